@@ -1,0 +1,158 @@
+/*
+ * gb300_eri.h -- C ABI of the GB300 (sm_103a) screened-ERI / J-K / gradient library.
+ *
+ * What the library computes (arXiv 2412.13203, Sec. 2.1-2.2): the four-centre
+ * electron repulsion integrals over contracted Cartesian Gaussian shells
+ *   (ab|cd) = sum_klmn D_ak D_bl D_cm D_dn [a_k b_l | c_m d_n]        (Eq. 2)
+ * for every angular-momentum class up to l = 3 (f), Schwarz-screened and
+ * contracted on the fly with a density matrix into the Coulomb and exchange
+ * matrices of a Fock build,
+ *   J_mn = sum_ls (mn|ls) D_ls,     K_mn = sum_ls (ml|ns) D_ls,
+ * and the nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D.
+ * The atomic J/K reduction is the one of Sec. 6 ("each thread employs atomic
+ * operations"), the pair/quartet blocking that of Sec. 4 (Block Constructor,
+ * stages 1-2).
+ *
+ * Conventions
+ *   - Units: bohr, hartree.  Cartesian shells.  Components ordered lx
+ *     descending, then ly descending (d: xx xy xz yy yz zz).  Basis
+ *     functions are ordered shell by shell as the caller lists them.
+ *   - Primitive normalisation: N(a,l) = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!);
+ *     the library then rescales each shell's coefficients so that its
+ *     contracted axial component x^l has unit norm.  Callers pass raw
+ *     coefficients.
+ *   - Screening: a shell quartet is evaluated iff Q_ab * Q_cd >= thresh,
+ *     Q_ab = sqrt(max_i |(ab|ab)_ii|) (plain Schwarz; thresh <= 0 keeps all).
+ *   - Matrices D, J, K are nbf x nbf, row-major, contiguous float64 in DEVICE
+ *     memory owned by the caller.  D must be symmetric (not checked unless
+ *     JK_OPT_CHECK_SYMMETRY is set).  J and K are overwritten.
+ *   - Every call is asynchronous on the given CUDA stream (NULL = legacy
+ *     default stream) unless stated otherwise.
+ *
+ * Errors: every function returns JK_OK (0) or a negative status; the message
+ * of the last failure on the calling thread is returned by jk_last_error().
+ * No exception crosses this boundary.
+ */
+#ifndef GB300_ERI_H
+#define GB300_ERI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    JK_OK = 0,
+    JK_ERR_INVALID = -1,       /* bad argument (null pointer, negative size, ...) */
+    JK_ERR_NOMEM = -2,         /* device or host allocation failed */
+    JK_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    JK_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    JK_ERR_UNSUPPORTED = -5,   /* angular momentum above the compiled maximum */
+    JK_ERR_NOT_SYMMETRIC = -6  /* D failed the optional symmetry check */
+};
+
+typedef enum { JK_FP64 = 0, JK_MIXED = 1 } jk_precision;
+
+/* Atoms: natom centres, xyz[natom*3] in bohr, HOST memory, read during the call. */
+typedef struct {
+    int natom;
+    const double* xyz;
+} jk_atoms;
+
+/* Shells (HOST memory, read during the call):
+ *   atom[s]        centre index in [0, natom)
+ *   l[s]           angular momentum, 0..JK_LMAX
+ *   nprim[s]       number of primitives, >= 1
+ *   prim_offset[s] first primitive of shell s in exps/coefs
+ *   exps, coefs    exponents (> 0) and raw contraction coefficients */
+typedef struct {
+    int nshell;
+    const int* atom;
+    const int* l;
+    const int* nprim;
+    const int* prim_offset;
+    const double* exps;
+    const double* coefs;
+} jk_shells;
+
+#define JK_LMAX 3
+
+/* Opaque handle: shell pairs, Schwarz factors and the quartet work lists,
+ * resident in device memory and owned by the library until shellpairs_free. */
+typedef struct jk_pairs_s* jk_pairs;
+
+/* Block Constructor stage 1 + 2 (Sec. 4): normalise the shells, form every
+ * unique shell pair and its primitive Gaussian products (p, P, K_AB c_a c_b),
+ * compute the Schwarz factors from a diagonal (ab|ab) pass, sort the pairs
+ * by angular class, primitive count and Q, and enumerate the surviving
+ * quartet rows per class.  Synchronous: returns after the device work is
+ * complete.  *out receives a new handle.  cuda_stream: cudaStream_t or NULL. */
+int shellpairs_build(const jk_atoms* atoms, const jk_shells* shells, double thresh,
+                     jk_pairs* out, void* cuda_stream);
+
+/* Sizes of a handle (any pointer may be NULL).
+ *   nbf            number of Cartesian basis functions
+ *   npairs         unique shell pairs kept (after the Q_ab * Q_max cut)
+ *   nquartets      unique shell quartets surviving Schwarz (ab >= cd)
+ *   nprimquartets  primitive quartets inside them */
+int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartets,
+                    int64_t* nprimquartets);
+
+/* J and K for one density (device pointers, nbf x nbf float64).
+ * JK_FP64: every primitive quartet in FP64.  JK_MIXED: shell quartets whose
+ * bound Q_ab Q_cd max|D| is below the mixed-precision cutoff (jk_set_option)
+ * run their primitive arithmetic in FP32 with FP64 accumulation of the
+ * contracted block and FP64 J/K updates; the others, the Boys function at
+ * small T, the Schwarz factors and the final J/K symmetrisation stay FP64. */
+int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision prec,
+             void* cuda_stream);
+
+/* Nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D (device pointers):
+ * dEdR[natom*3] (float64, device) is overwritten.  Derivative integrals by the
+ * shift rule d phi_a/dA_i = 2 alpha phi_{a+1_i} - a_i phi_{a-1_i} on centres
+ * A, B and C; the D centre by translational invariance.  prec as jk_build. */
+int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, void* cuda_stream);
+
+/* Many independent molecules in one launch sequence (one persistent launch per
+ * angular class over all molecules' work), optionally captured into a CUDA
+ * graph (JK_OPT_GRAPH).  D[i], J[i], K[i] are device pointers of molecule i. */
+int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J,
+                     double* const* K, jk_precision prec, void* cuda_stream);
+
+/* E = tr(DJ)/2 - tr(DK)/4 with a compensated device reduction; *E (host) is
+ * written after the stream synchronises (synchronous). */
+int jk_energy(int nbf, const double* D, const double* J, const double* K, double* E,
+              void* cuda_stream);
+
+/* Diagnostic: the device Boys evaluator used by the FP64 kernels (tabulated
+ * Taylor grid + downward recursion, Sec. 2.2 "[00|00] analytically").
+ * For each of n arguments T[i] (device, float64, T >= 0) writes
+ * F[i*(L+1) + m] = F_m(T[i]), m = 0..L (device, float64).  L <= 13.
+ * prec JK_MIXED evaluates the FP32 path used by mixed kernels (T >= tsmall). */
+int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* cuda_stream);
+
+/* Tunables (process-wide). */
+typedef enum {
+    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-7) */
+    JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys in FP64 for T < tsmall (default 1.0) */
+    JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous) */
+    JK_OPT_GRAPH = 3             /* nonzero: jk_build_batched captures and replays a CUDA graph */
+} jk_option;
+int jk_set_option(jk_option opt, double value);
+int jk_get_option(jk_option opt, double* value);
+
+/* Diagnostic counters of the last jk_build on this handle (host, synchronous):
+ * number of shell quartets run in FP32 and in FP64. */
+int jk_last_split(jk_pairs pairs, int64_t* n_fp32, int64_t* n_fp64);
+
+void shellpairs_free(jk_pairs pairs);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* jk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_ERI_H */

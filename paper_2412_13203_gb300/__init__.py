@@ -1,0 +1,200 @@
+"""Python binding of the GB300 screened-ERI / J-K / gradient library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/gb300_eri.h``.  PyTorch
+provides device memory and streams.  There is no CPU fallback: if the shared
+library has not been built (``paper_2412_13203_gb300.build.build()``) or no
+CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgb300eri.so")
+
+JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3}
+_PREC = {"fp64": 0, "mixed": 1}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class JKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class _Atoms(C.Structure):
+    _fields_ = [("natom", C.c_int), ("xyz", C.c_void_p)]
+
+
+class _Shells(C.Structure):
+    _fields_ = [("nshell", C.c_int), ("atom", C.c_void_p), ("l", C.c_void_p), ("nprim", C.c_void_p),
+                ("prim_offset", C.c_void_p), ("exps", C.c_void_p), ("coefs", C.c_void_p)]
+
+
+EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_build_batched", "jk_energy", "jk_boys",
+           "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error"]
+
+
+def load():
+    """Load the compiled library (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing; run paper_2412_13203_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+        lib.shellpairs_build.argtypes = [C.POINTER(_Atoms), C.POINTER(_Shells), C.c_double, C.POINTER(vp), vp]
+        lib.shellpairs_info.argtypes = [vp, C.POINTER(C.c_int), i64p, i64p, i64p]
+        lib.jk_build.argtypes = [vp, vp, vp, vp, C.c_int, vp]
+        lib.jk_grad.argtypes = [vp, vp, vp, C.c_int, vp]
+        lib.jk_build_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
+        lib.jk_energy.argtypes = [C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp]
+        lib.jk_boys.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, vp]
+        lib.jk_set_option.argtypes = [C.c_int, C.c_double]
+        lib.jk_get_option.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        lib.jk_last_split.argtypes = [vp, i64p, i64p]
+        lib.shellpairs_free.argtypes = [vp]
+        lib.shellpairs_free.restype = None
+        lib.jk_last_error.restype = C.c_char_p
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise JKError(rc, load().jk_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype_name="float64"):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != getattr(torch, dtype_name) or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype_name} tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class ShellPairs:
+    """Library-owned shell pairs, Schwarz factors and quartet work lists of one
+    molecule (``shellpairs_build``).  ``mol`` provides xyz, shell_atom,
+    shell_l, shell_nprim, shell_prim_offset, exps and raw coefs arrays."""
+
+    def __init__(self, mol, thresh: float | None = None, stream=None):
+        lib = load()
+        self._keep = [np.ascontiguousarray(mol.xyz, dtype=np.float64)]
+        ints = [np.ascontiguousarray(getattr(mol, n), dtype=np.int32)
+                for n in ("shell_atom", "shell_l", "shell_nprim", "shell_prim_offset")]
+        dbls = [np.ascontiguousarray(mol.exps, dtype=np.float64), np.ascontiguousarray(mol.coefs, dtype=np.float64)]
+        self._keep += ints + dbls
+        atoms = _Atoms(self._keep[0].shape[0], self._keep[0].ctypes.data)
+        shells = _Shells(ints[0].shape[0], ints[0].ctypes.data, ints[1].ctypes.data, ints[2].ctypes.data,
+                         ints[3].ctypes.data, dbls[0].ctypes.data, dbls[1].ctypes.data)
+        h = C.c_void_p()
+        _check(lib.shellpairs_build(C.byref(atoms), C.byref(shells), float(thresh or 0.0), C.byref(h),
+                                    _stream_ptr(stream)))
+        self.handle = h
+        self.natom = int(self._keep[0].shape[0])
+        nbf = C.c_int()
+        npair, nq, npq = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.shellpairs_info(h, C.byref(nbf), C.byref(npair), C.byref(nq), C.byref(npq)))
+        self.nbf, self.npairs, self.nquartets, self.nprimquartets = nbf.value, npair.value, nq.value, npq.value
+        self._keep = None
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().shellpairs_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def jk_build(pairs: ShellPairs, D, precision: str = "fp64", J=None, K=None, stream=None):
+    """J and K (new or given float64 CUDA tensors, nbf x nbf) for density D."""
+    import torch
+    n = pairs.nbf
+    if tuple(D.shape) != (n, n):
+        raise ValueError("D must be nbf x nbf")
+    if J is None:
+        J = torch.empty((n, n), dtype=torch.float64, device=D.device)
+    if K is None:
+        K = torch.empty((n, n), dtype=torch.float64, device=D.device)
+    _check(load().jk_build(pairs.handle, _dev_ptr(D), _dev_ptr(J), _dev_ptr(K), _PREC[precision], _stream_ptr(stream)))
+    return J, K
+
+
+def jk_energy(D, J, K, stream=None) -> float:
+    """E = tr(DJ)/2 - tr(DK)/4 (compensated device reduction)."""
+    E = C.c_double()
+    _check(load().jk_energy(int(D.shape[0]), _dev_ptr(D), _dev_ptr(J), _dev_ptr(K), C.byref(E), _stream_ptr(stream)))
+    return E.value
+
+
+def jk_grad(pairs: ShellPairs, D, precision: str = "fp64", out=None, stream=None):
+    """dE/dR [natom, 3] (float64 CUDA tensor) of E = tr(DJ)/2 - tr(DK)/4 at fixed D."""
+    import torch
+    if out is None:
+        out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
+    _check(load().jk_grad(pairs.handle, _dev_ptr(D), _dev_ptr(out), _PREC[precision], _stream_ptr(stream)))
+    return out
+
+
+def jk_build_batched(pairs_list, Ds, Js=None, Ks=None, precision: str = "fp64", stream=None):
+    import torch
+    n = len(pairs_list)
+    if Js is None:
+        Js = [torch.empty_like(D) for D in Ds]
+    if Ks is None:
+        Ks = [torch.empty_like(D) for D in Ds]
+    arr = C.c_void_p * n
+    hp = arr(*[p.handle.value for p in pairs_list])
+    dp = arr(*[_dev_ptr(D).value for D in Ds])
+    jp = arr(*[_dev_ptr(J).value for J in Js])
+    kp = arr(*[_dev_ptr(K).value for K in Ks])
+    _check(load().jk_build_batched(n, hp, dp, jp, kp, _PREC[precision], _stream_ptr(stream)))
+    return Js, Ks
+
+
+def boys(L: int, T, precision: str = "fp64", stream=None):
+    """F_m(T), m = 0..L, for a float64 CUDA tensor of arguments (diagnostic)."""
+    import torch
+    T = T.contiguous()
+    F = torch.empty((T.numel(), L + 1), dtype=torch.float64, device=T.device)
+    _check(load().jk_boys(int(L), int(T.numel()), _dev_ptr(T), _dev_ptr(F), _PREC[precision], _stream_ptr(stream)))
+    return F
+
+
+def set_option(name: str, value: float):
+    _check(load().jk_set_option(JK_OPT[name], float(value)))
+
+
+def get_option(name: str) -> float:
+    v = C.c_double()
+    _check(load().jk_get_option(JK_OPT[name], C.byref(v)))
+    return v.value
+
+
+def last_split(pairs: ShellPairs):
+    """(shell quartets run in FP32, in FP64) by the last jk_build on this handle."""
+    a, b = C.c_int64(), C.c_int64()
+    _check(load().jk_last_split(pairs.handle, C.byref(a), C.byref(b)))
+    return a.value, b.value

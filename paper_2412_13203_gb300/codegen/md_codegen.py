@@ -1,0 +1,621 @@
+"""McMurchie-Davidson code generator for the per-class ERI kernels.
+
+For a primitive quartet [ab|cd] the McMurchie-Davidson form is
+
+  [ab|cd] = 2 pi^(5/2) / (p q sqrt(p+q)) K_AB K_CD
+            sum_{tuv} E^{ab}_{tuv} sum_{tau nu phi} (-1)^{tau+nu+phi} E^{cd}_{tau nu phi}
+            R_{t+tau, u+nu, v+phi}(rho, P - Q)
+
+with the 1-D Hermite expansion coefficients (per axis)
+  E^{i+1,j}_t = E^{ij}_{t-1} / (2p) + X_PA E^{ij}_t + (t+1) E^{ij}_{t+1}
+  E^{i,j+1}_t = E^{ij}_{t-1} / (2p) + X_PB E^{ij}_t + (t+1) E^{ij}_{t+1},  E^{00}_0 = 1,
+and the Hermite Coulomb integrals
+  R^{(n)}_{000} = (-2 rho)^n F_n(rho |PQ|^2),
+  R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PQ R^{(n+1)}_{tuv}   (same for u, v).
+
+This is the recurrence the paper's Graph Compiler turns into straight-line
+code (Sec. 5, stages 2 and 4: a DAG of intermediate results emitted bottom-up
+from the [00|00] base case), but built on Hermite E/R instead of the
+paper's HGP recurrences.  Per shell quartet the generated kernel
+
+  1. loops over bra primitive pairs; per pair it forms the bra E products,
+  2. loops over ket primitive pairs; per pair it forms the signed ket E
+     products, evaluates F_0..F_L, builds R_{tuv} and accumulates the
+     half-transformed X[tuv][cd] (contracted over ket primitives),
+  3. applies the bra transform into the contracted Cartesian block
+     acc[ab][cd] (contracted over bra primitives),
+  4. digests the block into J' and K' (fused, atomics).
+
+Two emission modes:
+  * "flat": everything straight-line (small classes, values in registers);
+  * "loop": R stored in a (L+1)^3 cube, the ket-component loop runtime, the
+    per-axis E tables in small arrays (large classes, bounded code size).
+
+The generator also prints the exact FMA/FLOP count per primitive quartet of
+every class (used for the FLOP roofline).
+
+Run:  python md_codegen.py OUTDIR
+"""
+from __future__ import annotations
+
+import math
+import os
+import sys
+
+PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2), (3, 0), (3, 1), (3, 2), (3, 3)]
+LMAX = 3
+
+
+def comps(l):
+    return [(lx, ly, l - lx - ly) for lx in range(l, -1, -1) for ly in range(l - lx, -1, -1)]
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def herm(L):
+    """Hermite triples (t,u,v) with t+u+v <= L, ordered by total then lexicographic desc."""
+    out = []
+    for tot in range(L + 1):
+        for t in range(tot, -1, -1):
+            for u in range(tot - t, -1, -1):
+                out.append((t, u, tot - t - u))
+    return out
+
+
+# ---------------------------------------------------------------- symbolic emitter
+class Sym:
+    __slots__ = ("c", "name")
+
+    def __init__(self, c=None, name=None):
+        self.c, self.name = c, name
+
+    @property
+    def const(self):
+        return self.name is None
+
+    def __repr__(self):
+        return self.name if self.name is not None else repr(self.c)
+
+
+ONE = Sym(1.0)
+ZERO = Sym(0.0)
+
+
+class Emitter:
+    def __init__(self, real):
+        self.real = real
+        self.lines = []
+        self.flops = 0
+
+    def lit(self, c):
+        if self.real == "float":
+            return f"{c!r}f" if not float(c).is_integer() else f"{float(c):.1f}f"
+        return repr(float(c))
+
+    def val(self, s: Sym):
+        return s.name if not s.const else self.lit(s.c)
+
+    def emit(self, line):
+        self.lines.append(line)
+
+    def define(self, name, expr):
+        self.lines.append(f"const {self.real} {name} = {expr};")
+        return Sym(name=name)
+
+    def lincomb(self, terms, name):
+        """sum of factor * value, factors are Sym; folds constants."""
+        const = 0.0
+        var = []
+        for f, v in terms:
+            if f.const and v.const:
+                const += f.c * v.c
+            elif f.const:
+                if f.c != 0.0:
+                    var.append((f.c, v.name))
+            elif v.const:
+                if v.c != 0.0:
+                    var.append((v.c, f.name))
+            else:
+                var.append((1.0, f"{f.name} * {v.name}"))
+        if not var:
+            return Sym(const)
+        if len(var) == 1 and const == 0.0 and var[0][0] == 1.0 and "*" not in var[0][1]:
+            return Sym(name=var[0][1])
+        parts = []
+        for c, e in var:
+            if c == 1.0:
+                parts.append(e)
+            elif c == -1.0:
+                parts.append(f"-({e})")
+            else:
+                parts.append(f"{self.lit(c)} * {e}")
+            self.flops += 1 if c == 1.0 or c == -1.0 else 2
+        if const != 0.0:
+            parts.append(self.lit(const))
+            self.flops += 1
+        self.flops -= 1
+        return self.define(name, " + ".join(parts))
+
+    def product(self, factors, name):
+        c = 1.0
+        names = []
+        for f in factors:
+            if f.const:
+                c *= f.c
+            else:
+                names.append(f.name)
+        if c == 0.0:
+            return ZERO
+        if not names:
+            return Sym(c)
+        if len(names) == 1 and c == 1.0:
+            return Sym(name=names[0])
+        expr = " * ".join(names)
+        self.flops += len(names) - 1
+        if c != 1.0:
+            if c == -1.0:
+                expr = f"-({expr})"
+            else:
+                expr = f"{self.lit(c)} * {expr}"
+                self.flops += 1
+        return self.define(name, expr)
+
+
+def gen_E_axis(em: Emitter, tag, la, lb, PA, PB, inv2p, sign=False):
+    """E[(i, j, t)] for i <= la, j <= lb.  With sign, E_t is multiplied by (-1)^t."""
+    E = {(0, 0, 0): ONE}
+    for i in range(la):
+        for t in range(i + 2):
+            terms = []
+            if t >= 1:
+                terms.append((inv2p, E.get((i, 0, t - 1), ZERO)))
+            terms.append((PA, E.get((i, 0, t), ZERO)))
+            terms.append((Sym(float(t + 1)), E.get((i, 0, t + 1), ZERO)))
+            E[(i + 1, 0, t)] = em.lincomb(terms, f"{tag}{i + 1}_0_{t}")
+    for j in range(lb):
+        for i in range(la + 1):
+            for t in range(i + j + 2):
+                terms = []
+                if t >= 1:
+                    terms.append((inv2p, E.get((i, j, t - 1), ZERO)))
+                terms.append((PB, E.get((i, j, t), ZERO)))
+                terms.append((Sym(float(t + 1)), E.get((i, j, t + 1), ZERO)))
+                E[(i, j + 1, t)] = em.lincomb(terms, f"{tag}{i}_{j + 1}_{t}")
+    if sign:
+        out = {}
+        for (i, j, t), s in E.items():
+            if t % 2 == 1:
+                if s.const:
+                    out[(i, j, t)] = Sym(-s.c)
+                else:
+                    out[(i, j, t)] = em.define(f"{tag}n{i}_{j}_{t}", f"-{s.name}")
+            else:
+                out[(i, j, t)] = s
+        return out
+    return E
+
+
+def gen_products(em, tag, la, lb, Ex, Ey, Ez):
+    """Per Cartesian component pair (a, b): list of (hermite triple, Sym)."""
+    out = []
+    for ia, a in enumerate(comps(la)):
+        for ib, b in enumerate(comps(lb)):
+            lst = []
+            for t in range(a[0] + b[0] + 1):
+                for u in range(a[1] + b[1] + 1):
+                    for v in range(a[2] + b[2] + 1):
+                        s = em.product([Ex[(a[0], b[0], t)], Ey[(a[1], b[1], u)], Ez[(a[2], b[2], v)]],
+                                       f"{tag}{ia}_{ib}_{t}{u}{v}")
+                        if not (s.const and s.c == 0.0):
+                            lst.append(((t, u, v), s))
+            out.append(lst)
+    return out
+
+
+def gen_R(em, L, pref, m2r, F, PQ):
+    """R^{(0)}_{tuv} for t+u+v <= L.  Returns dict (t,u,v) -> Sym."""
+    pw = [Sym(name=pref)]
+    for n in range(1, L + 1):
+        pw.append(em.product([pw[-1], Sym(name=m2r)], f"pw{n}"))
+    prev = {}
+    for n in range(L, -1, -1):
+        cur = {}
+        for (t, u, v) in herm(L - n):
+            if (t, u, v) == (0, 0, 0):
+                cur[(t, u, v)] = em.product([pw[n], Sym(name=f"{F}[{n}]")], f"r{n}_000")
+                continue
+            if t > 0:
+                a, lo1, lo2, X = t - 1, (t - 1, u, v), (t - 2, u, v), PQ[0]
+            elif u > 0:
+                a, lo1, lo2, X = u - 1, (t, u - 1, v), (t, u - 2, v), PQ[1]
+            else:
+                a, lo1, lo2, X = v - 1, (t, u, v - 1), (t, u, v - 2), PQ[2]
+            terms = [(Sym(name=X), prev[lo1])]
+            if a > 0:
+                terms.append((Sym(float(a)), prev[lo2]))
+            cur[(t, u, v)] = em.lincomb(terms, f"r{n}_{t}_{u}_{v}")
+        prev = cur
+    return prev
+
+
+def hidx(h):
+    return {x: i for i, x in enumerate(h)}
+
+
+# ---------------------------------------------------------------- kernel body
+def class_name(bra, ket):
+    return f"{bra[0]}{bra[1]}{ket[0]}{ket[1]}"
+
+
+def quartet_counts(bra, ket):
+    la, lb = bra
+    lc, ld = ket
+    L = la + lb + lc + ld
+    HAB = len(herm(la + lb))
+    S_ab = sum(math.prod(a[i] + b[i] + 1 for i in range(3)) for a in comps(la) for b in comps(lb))
+    S_cd = sum(math.prod(a[i] + b[i] + 1 for i in range(3)) for a in comps(lc) for b in comps(ld))
+    NCD = ncart(lc) * ncart(ld)
+    NAB = ncart(la) * ncart(lb)
+    return dict(L=L, HAB=HAB, S_ab=S_ab, S_cd=S_cd, NAB=NAB, NCD=NCD,
+                xket=HAB * S_cd, bra=S_ab * NCD, R=math.comb(L + 4, 4))
+
+
+def use_flat(bra, ket):
+    c = quartet_counts(bra, ket)
+    return c["NAB"] * c["NCD"] + c["HAB"] * c["NCD"] <= 200 and c["xket"] + c["bra"] <= 2500
+
+
+def gen_quartet_body(bra, ket, real, mode_flat):
+    """Device code computing acc[NAB*NCD] (double) for one shell quartet.
+
+    Expects in scope: pairs (PairsView), bra/ket indices, ib/ik (int4 info),
+    A, B, C, Dd centres (double4 or float4 per precision), boys tables."""
+    la, lb = bra
+    lc, ld = ket
+    L = la + lb + lc + ld
+    cnt = quartet_counts(bra, ket)
+    NAB, NCD, HAB = cnt["NAB"], cnt["NCD"], cnt["HAB"]
+    f32 = real == "float"
+    em = Emitter(real)
+    hb = herm(la + lb)
+    hbi = hidx(hb)
+    L1 = L + 1
+    E = em.emit
+    pp, pp2 = ("pairs.ppf", "pairs.ppf2") if f32 else ("pairs.pp", "pairs.pp2")
+    vec = "float" if f32 else "double"
+    fma = "fmaf" if f32 else "fma"
+    E(f"double acc[{NAB * NCD}];")
+    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * NCD}; ++i) acc[i] = 0.0;")
+    if not mode_flat:
+        E(f"{real} Xl[{HAB * NCD}];")
+        E(f"{real} Rc[{L1 * L1 * L1}];")
+    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    E(f"const {vec}4 pa = {pp}[ib.w + ip]; const {vec}2 pb = {pp2}[ib.w + ip];")
+    E(f"const {real} p = pa.w, kp = pb.x, inv2p = pb.y;")
+    E(f"const {real} PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
+    E(f"const {real} PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
+    inv2p = Sym(name="inv2p")
+    Ebx = gen_E_axis(em, "ebx", la, lb, Sym(name="PAx"), Sym(name="PBx"), inv2p)
+    Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
+    Ebz = gen_E_axis(em, "ebz", la, lb, Sym(name="PAz"), Sym(name="PBz"), inv2p)
+    flops_ebra = em.flops
+    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz)
+    flops_ebra = em.flops - 0  # total so far (per bra primitive)
+    # X accumulators
+    if mode_flat:
+        for h in range(HAB):
+            for cd in range(NCD):
+                E(f"{real} x{h}_{cd} = 0;")
+    else:
+        E(f"for (int i = 0; i < {HAB * NCD}; ++i) Xl[i] = 0;")
+    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    E(f"const {vec}4 qa = {pp}[ik.w + jq]; const {vec}2 qb = {pp2}[ik.w + jq];")
+    E(f"const {real} q = qa.w, kq = qb.x, inv2q = qb.y;")
+    E(f"const {real} QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
+    E(f"const {real} QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
+    em.flops = 0
+    inv2q = Sym(name="inv2q")
+    Ekx = gen_E_axis(em, "ekx", lc, ld, Sym(name="QCx"), Sym(name="QDx"), inv2q, sign=True)
+    Eky = gen_E_axis(em, "eky", lc, ld, Sym(name="QCy"), Sym(name="QDy"), inv2q, sign=True)
+    Ekz = gen_E_axis(em, "ekz", lc, ld, Sym(name="QCz"), Sym(name="QDz"), inv2q, sign=True)
+    if mode_flat:
+        kprod = gen_products(em, "ek", lc, ld, Ekx, Eky, Ekz)
+    flops_eket = em.flops
+    em.flops = 0
+    E(f"const {real} PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
+    if f32:
+        E("const float rs = rsqrtf(p + q);")
+    else:
+        E("const double rs = rsqrt(p + q);")
+    E(f"const {real} rho = p * q * rs * rs;")
+    E(f"const {real} T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
+    E(f"const {real} pref = kp * kq * rs;")
+    E(f"const {real} m2r = -2 * rho;")
+    E(f"{real} F[{L + 1}];")
+    if f32:
+        E(f"gb::boys_mixed<{L}>(T, F, boys, boysf, tsmall);")
+    else:
+        E(f"gb::boys_f64<{L}>(T, F, boys);")
+    flops_setup = 16 + (kBoysCost(L))
+    R = gen_R(em, L, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
+    flops_R = em.flops
+    em.flops = 0
+    if mode_flat:
+        for h, (t, u, v) in enumerate(hb):
+            for cd in range(NCD):
+                for (tau, nu, phi), s in kprod[cd]:
+                    r = R[(t + tau, u + nu, v + phi)]
+                    E(f"x{h}_{cd} = {fma}({em.val(s)}, {em.val(r)}, x{h}_{cd});")
+                    em.flops += 2
+    else:
+        # cube store of R^(0)
+        for (t, u, v), s in R.items():
+            E(f"Rc[{(t * L1 + u) * L1 + v}] = {em.val(s)};")
+        # per-axis E arrays
+        for ax, Ek in (("x", Ekx), ("y", Eky), ("z", Ekz)):
+            n = (lc + 1) * (ld + 1) * (lc + ld + 1)
+            E(f"{real} ek{ax}a[{n}];")
+            for i in range(lc + 1):
+                for j in range(ld + 1):
+                    for t in range(lc + ld + 1):
+                        s = Ek.get((i, j, t), ZERO)
+                        E(f"ek{ax}a[{(i * (ld + 1) + j) * (lc + ld + 1) + t}] = {em.val(s)};")
+        cdl = [(c, d) for c in comps(lc) for d in comps(ld)]
+        E(f"#pragma unroll 1\nfor (int cd = 0; cd < {NCD}; ++cd) {{")
+        E(f"const int cx = c_cd_tab_{lc}{ld}[cd * 6 + 0], cy = c_cd_tab_{lc}{ld}[cd * 6 + 1], cz = c_cd_tab_{lc}{ld}[cd * 6 + 2];")
+        E(f"const int dx = c_cd_tab_{lc}{ld}[cd * 6 + 3], dy = c_cd_tab_{lc}{ld}[cd * 6 + 4], dz = c_cd_tab_{lc}{ld}[cd * 6 + 5];")
+        for h in range(HAB):
+            E(f"{real} xh{h} = Xl[{h} * {NCD} + cd];")
+        E("for (int tau = 0; tau <= cx + dx; ++tau) {")
+        E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {lc + ld + 1} + tau];")
+        E("for (int nu = 0; nu <= cy + dy; ++nu) {")
+        E(f"const {real} exy = ex * ekya[(cy * {ld + 1} + dy) * {lc + ld + 1} + nu];")
+        E("for (int phi = 0; phi <= cz + dz; ++phi) {")
+        E(f"const {real} e = exy * ekza[(cz * {ld + 1} + dz) * {lc + ld + 1} + phi];")
+        E(f"const {real}* Rb = Rc + (tau * {L1} + nu) * {L1} + phi;")
+        for h, (t, u, v) in enumerate(hb):
+            E(f"xh{h} = {fma}(e, Rb[{(t * L1 + u) * L1 + v}], xh{h});")
+        E("}}}")
+        for h in range(HAB):
+            E(f"Xl[{h} * {NCD} + cd] = xh{h};")
+        E("}")
+        em.flops += 2 * cnt["xket"]
+    flops_x = em.flops
+    E("}  // ket primitives")
+    # bra transform
+    em.flops = 0
+    if mode_flat:
+        for ab in range(NAB):
+            for cd in range(NCD):
+                expr = _dot(em, fma, [(sv, f"x{hbi[h]}_{cd}") for h, sv in bprod[ab]])
+                E(f"acc[{ab * NCD + cd}] += (double)({expr});")
+    else:
+        E(f"#pragma unroll 1\nfor (int cd = 0; cd < {NCD}; ++cd) {{")
+        for h in range(HAB):
+            E(f"const {real} xh{h} = Xl[{h} * {NCD} + cd];")
+        for ab in range(NAB):
+            expr = _dot(em, fma, [(sv, f"xh{hbi[h]}") for h, sv in bprod[ab]])
+            E(f"acc[{ab} * {NCD} + cd] += (double)({expr});")
+        E("}")
+        em.flops = 2 * cnt["bra"]
+    flops_bra = em.flops
+    E("}  // bra primitives")
+    body = "\n".join(em.lines)
+    stats = dict(flops_per_primq=flops_setup + flops_R + flops_x + flops_eket,
+                 flops_per_brap=flops_bra + flops_ebra, flat=mode_flat, **cnt)
+    return body, stats
+
+
+def _dot(em, fma, terms):
+    """sum of coefficient * variable as a chain of FMAs (coefficient 1 folded)."""
+    expr = None
+    for sv, x in terms:
+        unit = sv.const and sv.c == 1.0
+        if expr is None:
+            expr = x if unit else f"{em.val(sv)} * {x}"
+            em.flops += 0 if unit else 1
+        else:
+            expr = f"({expr} + {x})" if unit else f"{fma}({em.val(sv)}, {x}, {expr})"
+            em.flops += 1 if unit else 2
+    return expr
+
+
+def kBoysCost(L):
+    # Taylor evaluation (8 FMA) + exp Taylor (8 FMA) + 2 per downward step (FMA + MUL)
+    return 8 + (8 + 2 * L if L > 0 else 0)
+
+
+CD_TAB_DONE = set()
+
+
+def cd_table(lc, ld):
+    rows = []
+    for c in comps(lc):
+        for d in comps(ld):
+            rows += list(c) + list(d)
+    return f"static __device__ __constant__ int c_cd_tab_{lc}{ld}[{len(rows)}] = {{{', '.join(map(str, rows))}}};"
+
+
+def gen_class_kernels(bra, ket):
+    la, lb = bra
+    lc, ld = ket
+    na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
+    flat = use_flat(bra, ket)
+    out = []
+    stats = None
+    for prec, real in (("f64", "double"), ("f32", "float")):
+        body, st = gen_quartet_body(bra, ket, real, flat)
+        if prec == "f64":
+            stats = st
+        name = class_name(bra, ket)
+        vec = "float" if real == "float" else "double"
+        cen = ("Af", "Bf") if real == "float" else ("A", "B")
+        out.append(f"""
+__global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs args) {{
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= args.total) return;
+  int bra, ket;
+  gb::locate_quartet(args.rows, tid, bra, ket);
+  const gb::PairsView& pairs = args.pairs;
+  const double* __restrict__ boys = args.boys;
+  const float* __restrict__ boysf = args.boysf;
+  const float tsmall = args.tsmall;
+  (void)boysf; (void)tsmall;
+  const int4 ib = pairs.info[bra], ik = pairs.info[ket];
+  const {vec}4 A = pairs.{cen[0]}[bra], B = pairs.{cen[1]}[bra], C = pairs.{cen[0]}[ket], Dd = pairs.{cen[1]}[ket];
+{indent(body)}
+  double s = 1.0;
+  if (ib.x == ib.y) s *= 0.5;
+  if (ik.x == ik.y) s *= 0.5;
+  if (bra == ket) s *= 0.5;
+#pragma unroll
+  for (int i = 0; i < {na * nb * nc * nd}; ++i) acc[i] *= s;
+  gb::{"digest" if flat else "digest_loop"}<{na}, {nb}, {nc}, {nd}>(acc, ib.x, ib.y, ik.x, ik.y, args.D, args.J, args.K, args.nbf);
+}}
+""")
+        if bra == ket and prec == "f64":
+            out.append(f"""
+__global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArgs sa) {{
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sa.count) return;
+  const int bra = sa.first + i, ket = bra;
+  const gb::PairsView& pairs = sa.pairs;
+  const double* __restrict__ boys = sa.boys;
+  const float* __restrict__ boysf = nullptr;
+  const float tsmall = 0.f;
+  (void)boysf; (void)tsmall;
+  const int4 ib = pairs.info[bra], ik = ib;
+  const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
+{indent(body_f64_for_schwarz(bra, ket))}
+  sa.Q[i] = gb::schwarz_from_block<{na * nb}>(acc);
+}}
+""")
+    return "".join(out), stats
+
+
+_BODY_CACHE = {}
+
+
+def body_f64_for_schwarz(bra, ket):
+    key = (bra, ket)
+    if key not in _BODY_CACHE:
+        _BODY_CACHE[key] = gen_quartet_body(bra, ket, "double", use_flat(bra, ket))[0]
+    return _BODY_CACHE[key]
+
+
+def indent(s, n=2):
+    return "\n".join(" " * n + l for l in s.split("\n"))
+
+
+def class_pairs(lmax):
+    pcs = [pc for pc in PAIR_CLASSES if pc[0] <= lmax]
+    return [(pcs[i], pcs[j]) for i in range(len(pcs)) for j in range(i + 1)]
+
+
+def generate(outdir, lmax=LMAX, nfiles=8):
+    os.makedirs(outdir, exist_ok=True)
+    qs = class_pairs(lmax)
+    # spread classes over translation units by estimated size
+    sized = []
+    for bra, ket in qs:
+        c = quartet_counts(bra, ket)
+        sized.append(((c["xket"] + c["bra"]) if use_flat(bra, ket) else 400, bra, ket))
+    sized.sort(reverse=True)
+    bins = [[] for _ in range(nfiles)]
+    load = [0] * nfiles
+    for w, bra, ket in sized:
+        k = load.index(min(load))
+        bins[k].append((bra, ket))
+        load[k] += w + 100
+    header = '#include "eri_device.cuh"\n'
+    stats_all = {}
+    files = []
+    for k, items in enumerate(bins):
+        if not items:
+            continue
+        src = [header]
+        kets = sorted({ket for _, ket in items})
+        for ket in kets:
+            src.append(cd_table(*ket))
+        for bra, ket in items:
+            code, st = gen_class_kernels(bra, ket)
+            src.append(code)
+            stats_all[class_name(bra, ket)] = st
+            name = class_name(bra, ket)
+            src.append(f"""
+int launch_jk_{name}(int prec, const gb::JKArgs& a, cudaStream_t s) {{
+  if (a.total <= 0) return 0;
+  const int bs = 128;
+  const long long nb = (a.total + bs - 1) / bs;
+  if (prec == 0) eri_jk_{name}_f64<<<(unsigned)nb, bs, 0, s>>>(a);
+  else eri_jk_{name}_f32<<<(unsigned)nb, bs, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}}
+""")
+            if bra == ket:
+                src.append(f"""
+int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
+  if (a.count <= 0) return 0;
+  const int bs = 128;
+  eri_schwarz_{bra[0]}{bra[1]}<<<(a.count + bs - 1) / bs, bs, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}}
+""")
+        fn = os.path.join(outdir, f"md_classes_{k}.cu")
+        _write_if_changed(fn, "".join(src))
+        files.append(fn)
+    # dispatch
+    d = ['#include "eri_device.cuh"', "namespace gbgen {"]
+    d.append("}")
+    for bra, ket in qs:
+        d.append(f"int launch_jk_{class_name(bra, ket)}(int prec, const gb::JKArgs& a, cudaStream_t s);")
+    pcs = [pc for pc in PAIR_CLASSES if pc[0] <= lmax]
+    for pc in pcs:
+        d.append(f"int launch_schwarz_{pc[0]}{pc[1]}(const gb::SchwarzArgs& a, cudaStream_t s);")
+    n = len(pcs)
+    d.append("typedef int (*jk_launch_fn)(int, const gb::JKArgs&, cudaStream_t);")
+    d.append("typedef int (*schwarz_launch_fn)(const gb::SchwarzArgs&, cudaStream_t);")
+    tab = []
+    for i in range(n):
+        row = []
+        for j in range(n):
+            row.append(f"launch_jk_{class_name(pcs[i], pcs[j])}" if j <= i else "nullptr")
+        tab.append("{" + ", ".join(row) + "}")
+    d.append(f"extern \"C\" int gb_num_pair_classes() {{ return {n}; }}")
+    d.append(f"static const jk_launch_fn k_jk_tab[{n}][{n}] = {{{', '.join(tab)}}};")
+    d.append(f"static const schwarz_launch_fn k_sw_tab[{n}] = {{{', '.join(f'launch_schwarz_{pc[0]}{pc[1]}' for pc in pcs)}}};")
+    d.append("""
+int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, cudaStream_t s) {
+  return k_jk_tab[bra_cls][ket_cls](prec, a, s);
+}
+int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s) {
+  return k_sw_tab[cls](a, s);
+}
+""")
+    # flop table for roofline accounting
+    rows = []
+    for bra, ket in qs:
+        st = stats_all[class_name(bra, ket)]
+        rows.append(f"{{{st['flops_per_primq']}, {st['flops_per_brap']}}}")
+    d.append(f"extern \"C\" const int gb_class_flops[{len(qs)}][2] = {{{', '.join(rows)}}};")
+    fn = os.path.join(outdir, "md_dispatch.cu")
+    _write_if_changed(fn, "\n".join(d) + "\n")
+    files.append(fn)
+    return files, stats_all
+
+
+def _write_if_changed(fn, text):
+    if os.path.exists(fn) and open(fn).read() == text:
+        return
+    with open(fn, "w") as f:
+        f.write(text)
+
+
+if __name__ == "__main__":
+    out = sys.argv[1] if len(sys.argv) > 1 else "_gen"
+    lmax = int(sys.argv[2]) if len(sys.argv) > 2 else 2
+    files, stats = generate(out, lmax)
+    for k, v in stats.items():
+        print(k, "flat" if v["flat"] else "loop", "flops/primq", v["flops_per_primq"], "flops/brap", v["flops_per_brap"])

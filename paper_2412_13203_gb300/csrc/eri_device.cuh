@@ -1,0 +1,310 @@
+// Device-side building blocks shared by the generated per-class ERI kernels
+// and the host runtime: argument structures, the tabulated Boys function, the
+// quartet-row lookup and the fused J/K digestion.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb {
+
+constexpr int kLmaxShell = 3;
+constexpr int kLmaxBoys = 4 * kLmaxShell + 1;  // highest F_m needed (gradients of (ff|ff))
+constexpr int kBoysTaylor = 8;                  // Taylor terms j = 0..7 around each grid point
+constexpr int kBoysPerUnit = 16;                // grid step 1/16
+constexpr int kBoysNgrid = 80 * kBoysPerUnit + 1;  // T_k = k/16 on [0, 80]
+constexpr double kBoysTmax = 80.0;
+constexpr int kBoysRows = kLmaxBoys + 2;        // rows m = 0..kLmaxBoys, then exp(-T)
+constexpr int kBoysRowLen = kBoysTaylor;        // coefficients per (k, row)
+
+// Table layout: tab[(k * kBoysRows + m) * kBoysTaylor + j] = F_{m+j}(T_k) / j!
+// for m = 0..kLmaxBoys, and row kLmaxBoys+1 holds exp(-T_k) / j!.
+// F_L(T) = sum_j tab[k][L][j] (T_k - T)^j (Taylor expansion of F_L, using
+// dF_m/dT = -F_{m+1}).  Lower orders follow from the downward recursion
+// F_m = (2T F_{m+1} + exp(-T)) / (2m + 1).  For T >= 80 the asymptotic form
+// F_0 = sqrt(pi/T)/2, F_{m+1} = (2m+1) F_m / (2T) is exact to double
+// precision for every m <= kLmaxBoys (exp(-T) is below 1e-17 F_m there).
+
+struct PairsView {
+    int npair;
+    const int4* info;      // per pair: fa, fb (first basis functions of shells a, b), nprim pairs, first prim pair
+    const double4* A;      // per pair: centre of a (xyz), w = Q_ab (Schwarz factor)
+    const double4* B;      // per pair: centre of b (xyz), w = unused
+    const float4* Af;      // FP32 copies
+    const float4* Bf;
+    const double4* pp;     // per primitive pair: P (xyz), p
+    const double2* pp2;    // per primitive pair: kappa = sqrt(2 pi^(5/2)) K_AB c_a c_b / p, 1/(2p)
+    const float4* ppf;     // FP32 copies
+    const float2* ppf2;
+};
+
+struct RowsView {
+    int nrows;
+    const long long* start;  // [nrows + 1], exclusive prefix of the per-row quartet counts
+    const int* bra;          // bra pair of every row
+    const int* ket0;         // first ket pair of every row (kets are contiguous)
+};
+
+struct JKArgs {
+    PairsView pairs;
+    RowsView rows;
+    long long total;          // quartets in this launch (= rows.start[nrows])
+    const double* boys;       // FP64 Boys table
+    const float* boysf;       // FP32 Boys table
+    float tsmall;             // mixed kernels: FP64 Boys below this T
+    const double* D;
+    double* J;                // accumulates J' (J = J' + J'^T afterwards)
+    double* K;                // accumulates K'
+    int nbf;
+};
+
+struct SchwarzArgs {
+    PairsView pairs;
+    int first, count;         // pair range (one angular class)
+    const double* boys;
+    double* Q;                // out: Q for pairs first..first+count-1
+};
+
+// ------------------------------------------------------------------ Boys
+template <int L>
+__device__ __forceinline__ void boys_f64(double T, double* F, const double* __restrict__ tab) {
+    if (T < kBoysTmax) {
+        const int k = __double2int_rn(T * kBoysPerUnit);
+        const double d = k * (1.0 / kBoysPerUnit) - T;
+        const double* c = tab + ((size_t)k * kBoysRows + L) * kBoysTaylor;
+        double f = __ldg(c + kBoysTaylor - 1);
+#pragma unroll
+        for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, d, __ldg(c + j));
+        F[L] = f;
+        if (L > 0) {
+            const double* e = tab + ((size_t)k * kBoysRows + kLmaxBoys + 1) * kBoysTaylor;
+            double eT = __ldg(e + kBoysTaylor - 1);
+#pragma unroll
+            for (int j = kBoysTaylor - 2; j >= 0; --j) eT = fma(eT, d, __ldg(e + j));
+            const double t2 = 2.0 * T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], eT) * (1.0 / (2 * m + 1));
+        }
+    } else {
+        const double r = rsqrt(T);
+        F[0] = 0.88622692545275801365 * r;  // sqrt(pi)/2 / sqrt(T)
+        const double h = 0.5 * r * r;       // 1 / (2T)
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = F[m] * ((2 * m + 1) * h);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void boys_f32(float T, float* F, const float* __restrict__ tab) {
+    if (T < (float)kBoysTmax) {
+        const int k = __float2int_rn(T * kBoysPerUnit);
+        const float d = k * (1.0f / kBoysPerUnit) - T;
+        const float* c = tab + ((size_t)k * kBoysRows + L) * kBoysTaylor;
+        // |d| <= 1/32: five terms reach FP32 rounding
+        float f = __ldg(c + 4);
+#pragma unroll
+        for (int j = 3; j >= 0; --j) f = fmaf(f, d, __ldg(c + j));
+        F[L] = f;
+        if (L > 0) {
+            const float* e = tab + ((size_t)k * kBoysRows + kLmaxBoys + 1) * kBoysTaylor;
+            float eT = __ldg(e + 4);
+#pragma unroll
+            for (int j = 3; j >= 0; --j) eT = fmaf(eT, d, __ldg(e + j));
+            const float t2 = 2.0f * T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], eT) * (1.0f / (2 * m + 1));
+        }
+    } else {
+        const float r = rsqrtf(T);
+        F[0] = 0.886226925f * r;
+        const float h = 0.5f * r * r;
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = F[m] * ((2 * m + 1) * h);
+    }
+}
+
+// Mixed precision: FP64 evaluation below tsmall, FP32 above.
+template <int L>
+__device__ __forceinline__ void boys_mixed(float T, float* F, const double* __restrict__ tab,
+                                           const float* __restrict__ tabf, float tsmall) {
+    if (T < tsmall) {
+        double Fd[L + 1];
+        boys_f64<L>((double)T, Fd, tab);
+#pragma unroll
+        for (int m = 0; m <= L; ++m) F[m] = (float)Fd[m];
+    } else {
+        boys_f32<L>(T, F, tabf);
+    }
+}
+
+// ------------------------------------------------------------------ rows
+// Largest r with start[r] <= t (t < start[nrows]).
+__device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, int& bra, int& ket) {
+    int lo = 0, hi = rv.nrows;  // invariant: start[lo] <= t < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(rv.start + mid) <= t) lo = mid; else hi = mid;
+    }
+    bra = __ldg(rv.bra + lo);
+    ket = __ldg(rv.ket0 + lo) + (int)(t - __ldg(rv.start + lo));
+}
+
+// ------------------------------------------------------------------ digestion
+// Fused J/K update of one unique shell quartet (ab|cd), acc[((a*NB+b)*NC+c)*ND+d],
+// already scaled by the degeneracy factor s.  With the eight permutational
+// images and a symmetric D,
+//   J'_ab += 2 sum_cd I D_cd,   J'_cd += 2 sum_ab I D_ab,
+//   K'_ac += sum_bd I D_bd,     K'_ad += sum_bc I D_bc,
+//   K'_bc += sum_ad I D_ad,     K'_bd += sum_ac I D_ac,
+// and J = J' + J'^T, K = K' + K'^T afterwards.
+template <int NA, int NB, int NC, int ND>
+__device__ __forceinline__ void digest(const double* acc, int fa, int fb, int fc, int fd,
+                                       const double* __restrict__ D, double* J, double* K, int n) {
+    // J'_ab
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            double v = 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fc + c) * n + fd + d), v);
+            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * v);
+        }
+    // J'_cd
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double v = 0.0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fb + b), v);
+            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * v);
+        }
+    // K'_ac and K'_ad
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double v = 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fc + c, v);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double v = 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, v);
+        }
+    }
+    // K'_bc and K'_bd
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double v = 0.0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fc + c, v);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double v = 0.0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, v);
+        }
+    }
+}
+
+// Same update with rolled loops (large classes: bounded code size; the block
+// lives in local memory there anyway).
+template <int NA, int NB, int NC, int ND>
+__device__ __forceinline__ void digest_loop(const double* acc, int fa, int fb, int fc, int fd,
+                                            const double* __restrict__ D, double* J, double* K, int n) {
+#pragma unroll 1
+    for (int ab = 0; ab < NA * NB; ++ab) {
+        const int a = ab / NB, b = ab % NB;
+        double v = 0.0;
+        for (int cd = 0; cd < NC * ND; ++cd)
+            v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fc + cd / ND) * n + fd + cd % ND), v);
+        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * v);
+    }
+#pragma unroll 1
+    for (int cd = 0; cd < NC * ND; ++cd) {
+        const int c = cd / ND, d = cd % ND;
+        double v = 0.0;
+        for (int ab = 0; ab < NA * NB; ++ab)
+            v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
+        atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * v);
+    }
+#pragma unroll 1
+    for (int a = 0; a < NA; ++a)
+#pragma unroll 1
+        for (int c = 0; c < NC; ++c) {
+            double vac = 0.0;
+            for (int b = 0; b < NB; ++b)
+                for (int d = 0; d < ND; ++d)
+                    vac = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
+            atomicAdd(K + (size_t)(fa + a) * n + fc + c, vac);
+        }
+#pragma unroll 1
+    for (int a = 0; a < NA; ++a)
+#pragma unroll 1
+        for (int d = 0; d < ND; ++d) {
+            double v = 0.0;
+            for (int b = 0; b < NB; ++b)
+                for (int c = 0; c < NC; ++c)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, v);
+        }
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b)
+#pragma unroll 1
+        for (int c = 0; c < NC; ++c) {
+            double v = 0.0;
+            for (int a = 0; a < NA; ++a)
+                for (int d = 0; d < ND; ++d)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fc + c, v);
+        }
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b)
+#pragma unroll 1
+        for (int d = 0; d < ND; ++d) {
+            double v = 0.0;
+            for (int a = 0; a < NA; ++a)
+                for (int c = 0; c < NC; ++c)
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, v);
+        }
+}
+
+// Schwarz factor from a (ab|ab) block: sqrt(max_i |(ab|ab)_ii|).
+template <int NAB>
+__device__ __forceinline__ double schwarz_from_block(const double* acc) {
+    double m = 0.0;
+#pragma unroll
+    for (int i = 0; i < NAB; ++i) m = fmax(m, fabs(acc[i * NAB + i]));
+    return sqrt(m);
+}
+
+}  // namespace gb

@@ -1,0 +1,1126 @@
+// Host runtime and C ABI of the screened-ERI / J-K library (include/gb300_eri.h).
+//
+// Everything on the data path runs in the kernels of this file and of the
+// generated per-class ERI kernels: coefficient normalisation, primitive
+// Gaussian products, Schwarz factors, the pair sort, the quartet-row
+// enumeration, J/K digestion, symmetrisation and the energy reduction.  The
+// host only validates arguments, sizes launches and reads back a few counts.
+//
+// Paper mapping (arXiv 2412.13203):
+//   Block Constructor stage 1 (Sec. 4): every basis-function pair, sorted by
+//     angular class, cut into class-uniform tiles  -> pair build + sort here,
+//     the tile key additionally carries the primitive-pair count (bucketed)
+//     and the Schwarz factor so every warp runs one class with uniform loops.
+//   Block Constructor stage 2 (Sec. 4): pair tile x pair tile quartet blocks,
+//     never stored as O(N^4) lists -> "rows" (bra pair, ket bucket prefix),
+//     O(N^2) memory, one launch per (bra class, ket class).
+//   Workload Allocator atomics (Sec. 6) -> fused J/K digestion with FP64
+//     atomics in the generated kernels.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "eri_device.cuh"
+#include "gb300_eri.h"
+
+int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, cudaStream_t s);
+int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
+extern "C" int gb_num_pair_classes();
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(x)                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = (x);                                                                     \
+        if (e_ != cudaSuccess) return fail(JK_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                                      \
+        if (e_ != cudaSuccess) return fail(JK_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {
+        if (n <= bytes && p) return 0;
+        release();
+        if (n == 0) n = 16;
+        if (cudaMalloc(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(JK_ERR_NOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+        }
+        bytes = n;
+        return 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+constexpr int kMaxClasses = 10;  // pair classes for l <= 3
+constexpr int kNB = 16;          // primitive-pair-count buckets (ceil log2)
+
+struct ClassRows {
+    int bra_cls = 0, ket_cls = 0;
+    int nrows = 0;
+    long long total = 0;
+    long long nprimq = 0;
+    DevBuf start, bra, ket0;
+    // mixed-precision split (filled by jk_build)
+    DevBuf s64, k64, s32, k32;
+    long long total64 = 0, total32 = 0;
+};
+
+// Boys tables (one set per device, built on first use).
+struct BoysTables {
+    DevBuf tab, tabf;
+    bool ready = false;
+};
+std::mutex g_boys_mu;
+BoysTables g_boys[64];
+
+struct Options {
+    double tau = 1e-7;
+    double tsmall = 1.0;
+    int check_sym = 0;
+    int graph = 1;
+} g_opt;
+
+}  // namespace
+
+struct jk_pairs_s {
+    int device = 0;
+    int natom = 0, nshell = 0, nbf = 0;
+    long long npair_all = 0, npair = 0, nprimpair = 0;
+    double thresh = 0.0, Qmax = 0.0;
+    DevBuf info, A, B, Af, Bf, pp, pp2, ppf, ppf2;  // sorted, kept pairs
+    DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
+    DevBuf pair_lab;                                // int2 per pair: la, lb
+    DevBuf xyz;                                     // atoms
+    std::vector<int> cls_start;                     // [ncls + 1] pair ranges per class
+    std::vector<int> bucket_start;                  // [ncls * (kNB + 1)] per class bucket ranges
+    std::vector<ClassRows> rows;
+    long long nquartets = 0, nprimq = 0;
+    long long last_n32 = 0, last_n64 = 0;
+    DevBuf scratch;                                 // small reductions
+};
+
+namespace {
+
+// ------------------------------------------------------------------ Boys table build
+// F_m(T_k) by its power series  F_m(T) = exp(-T) sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1)),
+// summed with compensation; every term is positive.
+__global__ void k_boys_raw(double* raw, int nm) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= gb::kBoysNgrid * nm) return;
+    const int k = idx / nm, m = idx % nm;
+    const double T = (double)k / gb::kBoysPerUnit;
+    double term = 1.0 / (2 * m + 1), sum = term, comp = 0.0;
+    for (int i = 1; i < 2000; ++i) {
+        term *= 2.0 * T / (2 * m + 2 * i + 1);
+        const double y = term - comp;
+        const double t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+        if (term < 1e-18 * sum) break;
+    }
+    raw[idx] = exp(-T) * sum;
+}
+
+__global__ void k_boys_fill(const double* raw, int nm, double* tab, float* tabf) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int per = gb::kBoysRows * gb::kBoysTaylor;
+    if (idx >= gb::kBoysNgrid * per) return;
+    const int k = idx / per, r = (idx / gb::kBoysTaylor) % gb::kBoysRows, j = idx % gb::kBoysTaylor;
+    double fact = 1.0;
+    for (int i = 2; i <= j; ++i) fact *= i;
+    double v;
+    if (r <= gb::kLmaxBoys) {
+        v = raw[k * nm + r + j] / fact;
+    } else {
+        v = exp(-(double)k / gb::kBoysPerUnit) / fact;
+    }
+    tab[idx] = v;
+    tabf[idx] = (float)v;
+}
+
+int ensure_boys(int dev, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_boys_mu);
+    if (dev < 0 || dev >= 64) return fail(JK_ERR_INVALID, "device index");
+    BoysTables& b = g_boys[dev];
+    if (b.ready) return 0;
+    const int nm = gb::kLmaxBoys + gb::kBoysTaylor;
+    DevBuf raw;
+    int rc;
+    if ((rc = raw.alloc(sizeof(double) * gb::kBoysNgrid * nm))) return rc;
+    const size_t n = (size_t)gb::kBoysNgrid * gb::kBoysRows * gb::kBoysTaylor;
+    if ((rc = b.tab.alloc(sizeof(double) * n))) return rc;
+    if ((rc = b.tabf.alloc(sizeof(float) * n))) return rc;
+    k_boys_raw<<<(gb::kBoysNgrid * nm + 127) / 128, 128, 0, st>>>(raw.as<double>(), nm);
+    CKL();
+    k_boys_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw.as<double>(), nm, b.tab.as<double>(), b.tabf.as<float>());
+    CKL();
+    CK(cudaStreamSynchronize(st));
+    b.ready = true;
+    return 0;
+}
+
+// ------------------------------------------------------------------ scans and sorts
+// Exclusive prefix sum of n int64 values (in place allowed), total written to *total.
+__global__ void k_scan_block(const long long* in, long long* out, long long* bsum, long long n) {
+    __shared__ long long s[1024];
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    const long long v = (i < n) ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long t = (threadIdx.x >= (unsigned)off) ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_add(long long* out, const long long* boff, long long n) {
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+__global__ void k_set_total(const long long* in, const long long* out, long long n, long long* total) {
+    *total = (n > 0) ? out[n - 1] + in[n - 1] : 0;
+}
+
+// in == out is not allowed for the last-element total; callers keep the counts.
+int scan_exclusive(const long long* in, long long* out, long long n, long long* total_dev, cudaStream_t st) {
+    if (n <= 0) {
+        CK(cudaMemsetAsync(total_dev, 0, sizeof(long long), st));
+        return 0;
+    }
+    const long long nb = (n + 1023) / 1024;
+    DevBuf bsum, boff, btot;
+    int rc;
+    if ((rc = bsum.alloc(sizeof(long long) * nb))) return rc;
+    if ((rc = boff.alloc(sizeof(long long) * nb))) return rc;
+    if ((rc = btot.alloc(sizeof(long long)))) return rc;
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in, out, bsum.as<long long>(), n);
+    CKL();
+    if (nb > 1) {
+        if ((rc = scan_exclusive(bsum.as<long long>(), boff.as<long long>(), nb, btot.as<long long>(), st))) return rc;
+        k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, boff.as<long long>(), n);
+        CKL();
+    }
+    k_set_total<<<1, 1, 0, st>>>(in, out, n, total_dev);
+    CKL();
+    // temporaries are freed on return; make sure the stream is done with them
+    CK(cudaStreamSynchronize(st));
+    return 0;
+}
+
+// Bitonic sort of (key, val) pairs, n a power of two.
+__global__ void k_bitonic(unsigned long long* key, int* val, long long n, long long j, long long k) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long l = i ^ j;
+    if (l <= i) return;
+    const bool up = (i & k) == 0;
+    const unsigned long long a = key[i], b = key[l];
+    if ((a > b) == up) {
+        key[i] = b; key[l] = a;
+        const int t = val[i]; val[i] = val[l]; val[l] = t;
+    }
+}
+
+int sort_pairs(unsigned long long* key, int* val, long long n, cudaStream_t st) {
+    for (long long k = 2; k <= n; k <<= 1)
+        for (long long j = k >> 1; j > 0; j >>= 1) {
+            k_bitonic<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(key, val, n, j, k);
+            CKL();
+        }
+    return 0;
+}
+
+// ------------------------------------------------------------------ pair build kernels
+__global__ void k_normalize(int nshell, const int* l, const int* nprim, const int* off, const double* e,
+                            const double* c, double* out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshell) return;
+    const int L = l[s], k = nprim[s], o = off[s];
+    double dfact = 1.0;
+    for (int i = 2 * L - 1; i > 1; i -= 2) dfact *= i;
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < k; ++i) {
+        const double a = e[o + i];
+        out[o + i] = c[o + i] * pow(2.0 * a / pi, 0.75) * pow(4.0 * a, 0.5 * L) / sqrt(dfact);
+    }
+    double S = 0.0;
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const double p = e[o + i] + e[o + j];
+            S += out[o + i] * out[o + j] * pow(pi / p, 1.5) * dfact / pow(2.0 * p, L);
+        }
+    const double f = rsqrt(S);
+    for (int i = 0; i < k; ++i) out[o + i] *= f;
+}
+
+struct ShellDev {
+    const int *atom, *l, *nprim, *off, *bf;
+    const double *e, *c, *xyz;
+};
+
+__device__ __forceinline__ void decode_pair(long long k, int& i, int& j) {
+    long long ii = (long long)((sqrt(8.0 * (double)k + 1.0) - 1.0) * 0.5);
+    while (ii * (ii + 1) / 2 > k) --ii;
+    while ((ii + 1) * (ii + 2) / 2 <= k) ++ii;
+    i = (int)ii;
+    j = (int)(k - ii * (ii + 1) / 2);
+}
+
+__device__ __forceinline__ void canon(const ShellDev& S, int i, int j, int& a, int& b) {
+    // a carries the larger angular momentum (ties: the larger shell index)
+    if (S.l[j] > S.l[i]) { a = j; b = i; } else { a = i; b = j; }
+}
+
+__global__ void k_pair_count(ShellDev S, long long npair, long long* nprimpair, unsigned long long* key, int* val,
+                             long long npad) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npad) return;
+    if (k >= npair) {
+        key[k] = ~0ull;
+        val[k] = -1;
+        return;
+    }
+    int i, j, a, b;
+    decode_pair(k, i, j);
+    canon(S, i, j, a, b);
+    nprimpair[k] = (long long)S.nprim[a] * S.nprim[b];
+    const int la = S.l[a], lb = S.l[b];
+    const unsigned long long cls = (unsigned long long)(la * (la + 1) / 2 + lb);
+    key[k] = (cls << 40) | (unsigned long long)k;
+    val[k] = (int)k;
+}
+
+__global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, int4* info, double4* A, double4* B,
+                            int2* atoms, int2* lab, double4* pp, double2* pp2) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npair) return;
+    int i, j, a, b;
+    decode_pair(k, i, j);
+    canon(S, i, j, a, b);
+    const double* Ra = S.xyz + 3 * S.atom[a];
+    const double* Rb = S.xyz + 3 * S.atom[b];
+    const double ABx = Ra[0] - Rb[0], ABy = Ra[1] - Rb[1], ABz = Ra[2] - Rb[2];
+    const double AB2 = ABx * ABx + ABy * ABy + ABz * ABz;
+    const int ka = S.nprim[a], kb = S.nprim[b];
+    const long long o = poff[k];
+    info[k] = make_int4(S.bf[a], S.bf[b], ka * kb, (int)o);
+    A[k] = make_double4(Ra[0], Ra[1], Ra[2], 0.0);
+    B[k] = make_double4(Rb[0], Rb[1], Rb[2], 0.0);
+    atoms[k] = make_int2(S.atom[a], S.atom[b]);
+    lab[k] = make_int2(S.l[a], S.l[b]);
+    const double s2pi52 = 5.9149671727956128778;  // sqrt(2 pi^(5/2))
+    int n = 0;
+    for (int u = 0; u < ka; ++u)
+        for (int v = 0; v < kb; ++v, ++n) {
+            const double al = S.e[S.off[a] + u], be = S.e[S.off[b] + v];
+            const double p = al + be, ip = 1.0 / p;
+            const double Kab = exp(-al * be * ip * AB2);
+            pp[o + n] = make_double4((al * Ra[0] + be * Rb[0]) * ip, (al * Ra[1] + be * Rb[1]) * ip,
+                                     (al * Ra[2] + be * Rb[2]) * ip, p);
+            pp2[o + n] = make_double2(s2pi52 * Kab * S.c[S.off[a] + u] * S.c[S.off[b] + v] * ip, 0.5 * ip);
+        }
+}
+
+template <class T>
+__global__ void k_gather(const T* src, const int* perm, T* dst, long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[perm[k]];
+}
+
+__global__ void k_class_bounds(const unsigned long long* key, long long n, int shift, int mask, int* start) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = (int)((key[k] >> shift) & mask);
+    const int cp = (k == 0) ? -1 : (int)((key[k - 1] >> shift) & mask);
+    if (c != cp) start[c] = (int)k;
+}
+
+// Q_ab into A.w; maximum Q via integer atomics on the (non-negative) bit pattern.
+__global__ void k_store_q(const double* Q, int first, int count, double4* A, unsigned long long* qmax) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double q = Q[i];
+    A[first + i].w = q;
+    atomicMax(qmax, (unsigned long long)__double_as_longlong(q));
+}
+
+__device__ __forceinline__ int bucket_of(int np) {
+    int b = 0;
+    while ((1 << b) < np) ++b;
+    return b;
+}
+
+// Final key: class (4 bits) | bucket (4 bits) | descending Q (56 bits); Q quantised
+// (7 low mantissa bits cleared) so that the stored Q and the sort order agree.
+__global__ void k_final_key(const double4* A, const int4* info, const int2* lab, long long n, double thresh,
+                            double qmax, unsigned long long* key, int* val, long long npad) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npad) return;
+    if (k >= n) { key[k] = ~0ull; val[k] = -1; return; }
+    const double q = A[k].w;
+    const int2 l = lab[k];
+    const unsigned long long cls = (unsigned long long)(l.x * (l.x + 1) / 2 + l.y);
+    const unsigned long long bk = (unsigned long long)bucket_of(info[k].z);
+    const unsigned long long qb = ((unsigned long long)__double_as_longlong(q)) >> 7;  // 56 bits
+    if (thresh > 0.0 && q * qmax < thresh) { key[k] = ~0ull; val[k] = (int)k; return; }
+    key[k] = (cls << 60) | (bk << 56) | ((~qb) & ((1ull << 56) - 1));
+    val[k] = (int)k;
+}
+
+__global__ void k_quantise_q(double4* A, long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(A[k].w);
+    A[k].w = __longlong_as_double((long long)((b >> 7) << 7));
+}
+
+__global__ void k_count_kept(const unsigned long long* key, long long n, unsigned long long* cnt) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n && key[k] != ~0ull) atomicAdd(cnt, 1ull);
+}
+
+__global__ void k_bucket_bounds(const unsigned long long* key, long long n, int* start) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = (int)(key[k] >> 56);  // class * 16 + bucket
+    const int cp = (k == 0) ? -1 : (int)(key[k - 1] >> 56);
+    if (c != cp) start[c] = (int)k;
+}
+
+// Rows of one (bra class X, ket class Y) block: row r = bucket slot * nX + (i - x0).
+// Count = kets of the bucket with Q_j >= thresh / Q_i (kets sorted by Q descending),
+// capped at j <= i when X == Y (unique quartets ab >= cd).
+__global__ void k_rows_count(const double4* A, int x0, int nX, const int* bseg /* [nb][2] */, int nb, bool same,
+                             double thresh, long long* cnt, int* rbra, int* rket0) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)nX * nb) return;
+    const int bi = (int)(r / nX);
+    const int i = x0 + (int)(r % nX);
+    const int s = bseg[2 * bi], e = bseg[2 * bi + 1];
+    int n;
+    if (thresh > 0.0) {
+        const double qi = A[i].w;
+        int lo = s, hi = e;  // first j with Q_i Q_j < thresh
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (qi * A[mid].w >= thresh) lo = mid + 1; else hi = mid;
+        }
+        n = lo - s;
+    } else {
+        n = e - s;
+    }
+    if (same) {
+        if (i < s) n = 0;
+        else n = min(n, i - s + 1);
+    }
+    cnt[r] = n;
+    rbra[r] = i;
+    rket0[r] = s;
+}
+
+__global__ void k_rows_primq(const long long* cnt, const int* rbra, const int* rket0, int nrows, const int4* info,
+                             const long long* npre, unsigned long long* acc) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long c = cnt[r];
+    if (c == 0) return;
+    const long long kp = npre[rket0[r] + c] - npre[rket0[r]];
+    atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
+}
+
+__global__ void k_np_of(const int4* info, long long n, long long* np) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) np[k] = info[k].z;
+}
+
+// Mixed split of every row: kets with Q_i Q_j max|D| >= tau stay FP64 (they lead, Q descending).
+__global__ void k_rows_split(const long long* start, const int* rbra, const int* rket0, int nrows, const double4* A,
+                             const double* dmax, double tau, long long* c64, long long* c32, int* k32) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long c = start[r + 1] - start[r];
+    const int s = rket0[r];
+    const double qi = A[rbra[r]].w * (*dmax);
+    int lo = s, hi = s + (int)c;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (qi * A[mid].w >= tau) lo = mid + 1; else hi = mid;
+    }
+    c64[r] = lo - s;
+    c32[r] = c - (lo - s);
+    k32[r] = lo;
+}
+
+__global__ void k_absmax(const double* x, long long n, unsigned long long* out) {
+    double m = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_asym(const double* x, int n, unsigned long long* out) {
+    double m = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n), j = (int)(t % n);
+        m = fmax(m, fabs(x[(size_t)i * n + j] - x[(size_t)j * n + i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// J = J' + J'^T in place (one thread per unordered index pair).
+__global__ void k_symmetrize(double* X, int n) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)n * (n + 1) / 2;
+    if (t >= tot) return;
+    int i, j;
+    decode_pair(t, i, j);  // i >= j
+    const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
+    if (i == j) { X[a] *= 2.0; return; }
+    const double v = X[a] + X[b];
+    X[a] = v;
+    X[b] = v;
+}
+
+// Compensated energy: E = sum D J / 2 - sum D K / 4.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void k_energy_partial(const double* D, const double* J, const double* K, long long n2, double2* part) {
+    double s = 0.0, c = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        double t, e;
+        two_sum(s, 0.5 * D[i] * J[i], t, e);
+        s = t; c += e;
+        two_sum(s, -0.25 * D[i] * K[i], t, e);
+        s = t; c += e;
+        // the products themselves carry rounding: add their exact residuals
+        c += fma(0.5 * D[i], J[i], -(0.5 * D[i] * J[i]));
+        c += fma(-0.25 * D[i], K[i], -(-0.25 * D[i] * K[i]));
+    }
+    __shared__ double ss[256], sc[256];
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) {
+            double t, e;
+            two_sum(ss[threadIdx.x], ss[threadIdx.x + o], t, e);
+            ss[threadIdx.x] = t;
+            sc[threadIdx.x] += sc[threadIdx.x + o] + e;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(ss[0], sc[0]);
+}
+
+__global__ void k_energy_final(const double2* part, int nb, double* E) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0, c = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        double t, e;
+        two_sum(s, part[i].x, t, e);
+        s = t;
+        c += e + part[i].y;
+    }
+    *E = s + c;
+}
+
+unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+
+gb::PairsView view_of(const jk_pairs_s* h) {
+    gb::PairsView v;
+    v.npair = (int)h->npair;
+    v.info = h->info.as<int4>();
+    v.A = h->A.as<double4>();
+    v.B = h->B.as<double4>();
+    v.Af = h->Af.as<float4>();
+    v.Bf = h->Bf.as<float4>();
+    v.pp = h->pp.as<double4>();
+    v.pp2 = h->pp2.as<double2>();
+    v.ppf = h->ppf.as<float4>();
+    v.ppf2 = h->ppf2.as<float2>();
+    return v;
+}
+
+__global__ void k_to_f32(const double4* A, const double4* B, long long n, float4* Af, float4* Bf) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double4 a = A[k], b = B[k];
+    Af[k] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
+    Bf[k] = make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
+}
+
+__global__ void k_pp_to_f32(const double4* pp, const double2* pp2, long long n, float4* ppf, float2* ppf2) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double4 a = pp[k];
+    const double2 b = pp2[k];
+    ppf[k] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
+    ppf2[k] = make_float2((float)b.x, (float)b.y);
+}
+
+template <class T>
+int upload(DevBuf& d, const T* h, size_t n, cudaStream_t st) {
+    int rc = d.alloc(sizeof(T) * n);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(d.p, h, sizeof(T) * n, cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk_pairs_s* h, cudaStream_t st) {
+    const int S = shells->nshell;
+    CK(cudaGetDevice(&h->device));
+    int rc;
+    if ((rc = ensure_boys(h->device, st))) return rc;
+    // ---- host-side validation and basis offsets
+    std::vector<int> bf(S);
+    int nbf = 0, nprim_tot = 0;
+    for (int s = 0; s < S; ++s) {
+        const int l = shells->l[s];
+        if (l < 0) return fail(JK_ERR_INVALID, "negative angular momentum");
+        if (l > JK_LMAX) return fail(JK_ERR_UNSUPPORTED, "angular momentum above f");
+        if (shells->nprim[s] < 1) return fail(JK_ERR_INVALID, "shell without primitives");
+        if (shells->atom[s] < 0 || shells->atom[s] >= atoms->natom) return fail(JK_ERR_INVALID, "shell atom out of range");
+        if (shells->prim_offset[s] < 0) return fail(JK_ERR_INVALID, "negative primitive offset");
+        nprim_tot = std::max(nprim_tot, shells->prim_offset[s] + shells->nprim[s]);
+        bf[s] = nbf;
+        nbf += (l + 1) * (l + 2) / 2;
+    }
+    for (int i = 0; i < nprim_tot; ++i)
+        if (!(shells->exps[i] > 0.0) || !std::isfinite(shells->coefs[i]))
+            return fail(JK_ERR_INVALID, "non-positive exponent or non-finite coefficient");
+    for (int i = 0; i < 3 * atoms->natom; ++i)
+        if (!std::isfinite(atoms->xyz[i])) return fail(JK_ERR_INVALID, "non-finite coordinate");
+    h->natom = atoms->natom;
+    h->nshell = S;
+    h->nbf = nbf;
+    h->thresh = thresh;
+    // ---- upload
+    DevBuf d_atom, d_l, d_np, d_off, d_bf, d_e, d_c, d_cn;
+    if ((rc = upload(h->xyz, atoms->xyz, 3 * (size_t)atoms->natom, st))) return rc;
+    if ((rc = upload(d_atom, shells->atom, S, st))) return rc;
+    if ((rc = upload(d_l, shells->l, S, st))) return rc;
+    if ((rc = upload(d_np, shells->nprim, S, st))) return rc;
+    if ((rc = upload(d_off, shells->prim_offset, S, st))) return rc;
+    if ((rc = upload(d_bf, bf.data(), S, st))) return rc;
+    if ((rc = upload(d_e, shells->exps, nprim_tot, st))) return rc;
+    if ((rc = upload(d_c, shells->coefs, nprim_tot, st))) return rc;
+    if ((rc = d_cn.alloc(sizeof(double) * nprim_tot))) return rc;
+    k_normalize<<<nblk(S, 128), 128, 0, st>>>(S, d_l.as<int>(), d_np.as<int>(), d_off.as<int>(), d_e.as<double>(),
+                                               d_c.as<double>(), d_cn.as<double>());
+    CKL();
+    ShellDev SD{d_atom.as<int>(), d_l.as<int>(), d_np.as<int>(), d_off.as<int>(), d_bf.as<int>(),
+                d_e.as<double>(), d_cn.as<double>(), h->xyz.as<double>()};
+    // ---- every unique pair, primitive offsets
+    const long long np = (long long)S * (S + 1) / 2;
+    h->npair_all = np;
+    long long npad = 1;
+    while (npad < np) npad <<= 1;
+    DevBuf d_npp, d_poff, d_tot, d_key, d_val;
+    if ((rc = d_npp.alloc(sizeof(long long) * np))) return rc;
+    if ((rc = d_poff.alloc(sizeof(long long) * np))) return rc;
+    if ((rc = d_tot.alloc(sizeof(long long) * 4))) return rc;
+    if ((rc = d_key.alloc(sizeof(unsigned long long) * npad))) return rc;
+    if ((rc = d_val.alloc(sizeof(int) * npad))) return rc;
+    k_pair_count<<<nblk(npad, 256), 256, 0, st>>>(SD, np, d_npp.as<long long>(), d_key.as<unsigned long long>(),
+                                                   d_val.as<int>(), npad);
+    CKL();
+    if ((rc = scan_exclusive(d_npp.as<long long>(), d_poff.as<long long>(), np, d_tot.as<long long>(), st))) return rc;
+    long long nprimpair = 0;
+    CK(cudaMemcpyAsync(&nprimpair, d_tot.p, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (nprimpair > (long long)INT32_MAX) return fail(JK_ERR_UNSUPPORTED, "more than 2^31 primitive pairs");
+    h->nprimpair = nprimpair;
+    // unsorted pair arrays
+    DevBuf u_info, u_A, u_B, u_atoms, u_lab;
+    if ((rc = u_info.alloc(sizeof(int4) * np))) return rc;
+    if ((rc = u_A.alloc(sizeof(double4) * np))) return rc;
+    if ((rc = u_B.alloc(sizeof(double4) * np))) return rc;
+    if ((rc = u_atoms.alloc(sizeof(int2) * np))) return rc;
+    if ((rc = u_lab.alloc(sizeof(int2) * np))) return rc;
+    if ((rc = h->pp.alloc(sizeof(double4) * nprimpair))) return rc;
+    if ((rc = h->pp2.alloc(sizeof(double2) * nprimpair))) return rc;
+    if ((rc = h->ppf.alloc(sizeof(float4) * nprimpair))) return rc;
+    if ((rc = h->ppf2.alloc(sizeof(float2) * nprimpair))) return rc;
+    k_pair_fill<<<nblk(np, 128), 128, 0, st>>>(SD, np, d_poff.as<long long>(), u_info.as<int4>(), u_A.as<double4>(),
+                                                u_B.as<double4>(), u_atoms.as<int2>(), u_lab.as<int2>(),
+                                                h->pp.as<double4>(), h->pp2.as<double2>());
+    CKL();
+    k_pp_to_f32<<<nblk(nprimpair, 256), 256, 0, st>>>(h->pp.as<double4>(), h->pp2.as<double2>(), nprimpair,
+                                                       h->ppf.as<float4>(), h->ppf2.as<float2>());
+    CKL();
+    // ---- sort 1: by class, then Schwarz per class
+    if ((rc = sort_pairs(d_key.as<unsigned long long>(), d_val.as<int>(), npad, st))) return rc;
+    DevBuf s_info, s_A, s_B, s_atoms, s_lab;
+    if ((rc = s_info.alloc(sizeof(int4) * np))) return rc;
+    if ((rc = s_A.alloc(sizeof(double4) * np))) return rc;
+    if ((rc = s_B.alloc(sizeof(double4) * np))) return rc;
+    if ((rc = s_atoms.alloc(sizeof(int2) * np))) return rc;
+    if ((rc = s_lab.alloc(sizeof(int2) * np))) return rc;
+    k_gather<int4><<<nblk(np, 256), 256, 0, st>>>(u_info.as<int4>(), d_val.as<int>(), s_info.as<int4>(), np);
+    k_gather<double4><<<nblk(np, 256), 256, 0, st>>>(u_A.as<double4>(), d_val.as<int>(), s_A.as<double4>(), np);
+    k_gather<double4><<<nblk(np, 256), 256, 0, st>>>(u_B.as<double4>(), d_val.as<int>(), s_B.as<double4>(), np);
+    k_gather<int2><<<nblk(np, 256), 256, 0, st>>>(u_atoms.as<int2>(), d_val.as<int>(), s_atoms.as<int2>(), np);
+    k_gather<int2><<<nblk(np, 256), 256, 0, st>>>(u_lab.as<int2>(), d_val.as<int>(), s_lab.as<int2>(), np);
+    CKL();
+    const int ncls = gb_num_pair_classes();
+    DevBuf d_cstart;
+    if ((rc = d_cstart.alloc(sizeof(int) * kMaxClasses))) return rc;
+    std::vector<int> cst(kMaxClasses, -1);
+    CK(cudaMemcpyAsync(d_cstart.p, cst.data(), sizeof(int) * kMaxClasses, cudaMemcpyHostToDevice, st));
+    k_class_bounds<<<nblk(np, 256), 256, 0, st>>>(d_key.as<unsigned long long>(), np, 40, 0xF, d_cstart.as<int>());
+    CKL();
+    CK(cudaMemcpyAsync(cst.data(), d_cstart.p, sizeof(int) * kMaxClasses, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> cend(kMaxClasses, 0);
+    {
+        int next = (int)np;
+        for (int c = kMaxClasses - 1; c >= 0; --c) {
+            if (cst[c] >= 0) { cend[c] = next; next = cst[c]; } else { cst[c] = next; cend[c] = next; }
+        }
+    }
+    DevBuf d_q, d_qmax;
+    if ((rc = d_q.alloc(sizeof(double) * np))) return rc;
+    if ((rc = d_qmax.alloc(sizeof(unsigned long long)))) return rc;
+    CK(cudaMemsetAsync(d_qmax.p, 0, sizeof(unsigned long long), st));
+    gb::PairsView pv;
+    std::memset(&pv, 0, sizeof(pv));
+    pv.npair = (int)np;
+    pv.info = s_info.as<int4>();
+    pv.A = s_A.as<double4>();
+    pv.B = s_B.as<double4>();
+    pv.pp = h->pp.as<double4>();
+    pv.pp2 = h->pp2.as<double2>();
+    const double* boys = g_boys[h->device].tab.as<double>();
+    for (int c = 0; c < ncls; ++c) {
+        const int cnt = cend[c] - cst[c];
+        if (cnt <= 0) continue;
+        gb::SchwarzArgs sa{pv, cst[c], cnt, boys, d_q.as<double>() + cst[c]};
+        if (gb_launch_schwarz(c, sa, st)) return fail(JK_ERR_CUDA, "Schwarz kernel launch failed");
+        k_store_q<<<nblk(cnt, 256), 256, 0, st>>>(d_q.as<double>() + cst[c], cst[c], cnt, s_A.as<double4>(),
+                                                  d_qmax.as<unsigned long long>());
+        CKL();
+    }
+    unsigned long long qmb = 0;
+    CK(cudaMemcpyAsync(&qmb, d_qmax.p, sizeof(qmb), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double qmax;
+    std::memcpy(&qmax, &qmb, sizeof(double));
+    h->Qmax = qmax;
+    // ---- sort 2: (class, bucket, Q descending), drop pairs with Q * Qmax < thresh
+    k_final_key<<<nblk(npad, 256), 256, 0, st>>>(s_A.as<double4>(), s_info.as<int4>(), s_lab.as<int2>(), np, thresh,
+                                                  qmax, d_key.as<unsigned long long>(), d_val.as<int>(), npad);
+    CKL();
+    CK(cudaMemsetAsync(d_tot.p, 0, sizeof(long long), st));
+    k_count_kept<<<nblk(np, 256), 256, 0, st>>>(d_key.as<unsigned long long>(), np, d_tot.as<unsigned long long>());
+    CKL();
+    if ((rc = sort_pairs(d_key.as<unsigned long long>(), d_val.as<int>(), npad, st))) return rc;
+    long long kept = 0;
+    CK(cudaMemcpyAsync(&kept, d_tot.p, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->npair = kept;
+    const long long nk = std::max(1LL, kept);
+    if ((rc = h->info.alloc(sizeof(int4) * nk))) return rc;
+    if ((rc = h->A.alloc(sizeof(double4) * nk))) return rc;
+    if ((rc = h->B.alloc(sizeof(double4) * nk))) return rc;
+    if ((rc = h->Af.alloc(sizeof(float4) * nk))) return rc;
+    if ((rc = h->Bf.alloc(sizeof(float4) * nk))) return rc;
+    if ((rc = h->pair_atoms.alloc(sizeof(int2) * nk))) return rc;
+    if ((rc = h->pair_lab.alloc(sizeof(int2) * nk))) return rc;
+    if (kept > 0) {
+        k_gather<int4><<<nblk(kept, 256), 256, 0, st>>>(s_info.as<int4>(), d_val.as<int>(), h->info.as<int4>(), kept);
+        k_gather<double4><<<nblk(kept, 256), 256, 0, st>>>(s_A.as<double4>(), d_val.as<int>(), h->A.as<double4>(), kept);
+        k_gather<double4><<<nblk(kept, 256), 256, 0, st>>>(s_B.as<double4>(), d_val.as<int>(), h->B.as<double4>(), kept);
+        k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_atoms.as<int2>(), d_val.as<int>(), h->pair_atoms.as<int2>(), kept);
+        k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_lab.as<int2>(), d_val.as<int>(), h->pair_lab.as<int2>(), kept);
+        CKL();
+        k_quantise_q<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), kept);
+        k_to_f32<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), h->B.as<double4>(), kept, h->Af.as<float4>(),
+                                                  h->Bf.as<float4>());
+        CKL();
+    }
+    // ---- class / bucket segments
+    const int nseg = kMaxClasses * kNB;
+    DevBuf d_bs;
+    if ((rc = d_bs.alloc(sizeof(int) * nseg))) return rc;
+    std::vector<int> bs(nseg, -1);
+    CK(cudaMemcpyAsync(d_bs.p, bs.data(), sizeof(int) * nseg, cudaMemcpyHostToDevice, st));
+    if (kept > 0) {
+        k_bucket_bounds<<<nblk(kept, 256), 256, 0, st>>>(d_key.as<unsigned long long>(), kept, d_bs.as<int>());
+        CKL();
+    }
+    CK(cudaMemcpyAsync(bs.data(), d_bs.p, sizeof(int) * nseg, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> be(nseg, 0);
+    {
+        int next = (int)kept;
+        for (int c = nseg - 1; c >= 0; --c) {
+            if (bs[c] >= 0) { be[c] = next; next = bs[c]; } else { bs[c] = next; be[c] = next; }
+        }
+    }
+    h->cls_start.assign(ncls + 1, 0);
+    for (int c = 0; c < ncls; ++c) h->cls_start[c] = bs[c * kNB];
+    h->cls_start[ncls] = (int)kept;
+    h->bucket_start = bs;
+    // ---- quartet rows per (bra class X >= ket class Y)
+    DevBuf d_npk, d_npre;
+    if ((rc = d_npk.alloc(sizeof(long long) * (nk + 1)))) return rc;
+    if ((rc = d_npre.alloc(sizeof(long long) * (nk + 1)))) return rc;
+    CK(cudaMemsetAsync(d_npk.p, 0, sizeof(long long) * (nk + 1), st));
+    if (kept > 0) {
+        k_np_of<<<nblk(kept, 256), 256, 0, st>>>(h->info.as<int4>(), kept, d_npk.as<long long>());
+        CKL();
+    }
+    if ((rc = scan_exclusive(d_npk.as<long long>(), d_npre.as<long long>(), kept + 1, d_tot.as<long long>() + 1, st)))
+        return rc;
+    DevBuf d_primq;
+    if ((rc = d_primq.alloc(sizeof(unsigned long long)))) return rc;
+    CK(cudaMemsetAsync(d_primq.p, 0, sizeof(unsigned long long), st));
+    h->rows.clear();
+    h->rows.reserve(ncls * (ncls + 1) / 2);
+    h->nquartets = 0;
+    for (int X = 0; X < ncls; ++X) {
+        const int x0 = bs[X * kNB], x1 = be[X * kNB + kNB - 1];
+        const int nX = x1 - x0;
+        for (int Y = 0; Y <= X; ++Y) {
+            std::vector<int> seg;
+            for (int b = 0; b < kNB; ++b)
+                if (be[Y * kNB + b] > bs[Y * kNB + b]) { seg.push_back(bs[Y * kNB + b]); seg.push_back(be[Y * kNB + b]); }
+            const int nb = (int)seg.size() / 2;
+            if (nX == 0 || nb == 0) continue;
+            h->rows.emplace_back();
+            ClassRows& cr = h->rows.back();
+            cr.bra_cls = X;
+            cr.ket_cls = Y;
+            cr.nrows = nX * nb;
+            DevBuf d_seg, d_cnt;
+            if ((rc = upload(d_seg, seg.data(), seg.size(), st))) return rc;
+            if ((rc = d_cnt.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = cr.start.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = cr.bra.alloc(sizeof(int) * cr.nrows))) return rc;
+            if ((rc = cr.ket0.alloc(sizeof(int) * cr.nrows))) return rc;
+            k_rows_count<<<nblk(cr.nrows, 256), 256, 0, st>>>(h->A.as<double4>(), x0, nX, d_seg.as<int>(), nb, X == Y,
+                                                              thresh, d_cnt.as<long long>(), cr.bra.as<int>(),
+                                                              cr.ket0.as<int>());
+            CKL();
+            CK(cudaMemsetAsync(d_cnt.as<long long>() + cr.nrows, 0, sizeof(long long), st));
+            if ((rc = scan_exclusive(d_cnt.as<long long>(), cr.start.as<long long>(), cr.nrows + 1,
+                                     d_tot.as<long long>() + 2, st)))
+                return rc;
+            k_rows_primq<<<nblk(cr.nrows, 256), 256, 0, st>>>(d_cnt.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                              cr.nrows, h->info.as<int4>(), d_npre.as<long long>(),
+                                                              d_primq.as<unsigned long long>());
+            CKL();
+            long long tot = 0;
+            CK(cudaMemcpyAsync(&tot, d_tot.as<long long>() + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            cr.total = tot;
+            h->nquartets += tot;
+        }
+    }
+    unsigned long long pq = 0;
+    CK(cudaMemcpyAsync(&pq, d_primq.p, sizeof(pq), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->nprimq = (long long)pq;
+    return 0;
+}
+
+int launch_class(const jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
+                 long long total, const double* D, double* J, double* K, cudaStream_t st) {
+    if (total <= 0) return 0;
+    gb::JKArgs a;
+    a.pairs = view_of(h);
+    a.rows.nrows = cr.nrows;
+    a.rows.start = start;
+    a.rows.bra = cr.bra.as<int>();
+    a.rows.ket0 = ket0;
+    a.total = total;
+    a.boys = g_boys[h->device].tab.as<double>();
+    a.boysf = g_boys[h->device].tabf.as<float>();
+    a.tsmall = (float)g_opt.tsmall;
+    a.D = D;
+    a.J = J;
+    a.K = K;
+    a.nbf = h->nbf;
+    if (total >= (1LL << 31) * 128LL) return fail(JK_ERR_UNSUPPORTED, "launch too large");
+    const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec, a, st);
+    if (e) return fail(JK_ERR_CUDA, std::string("ERI kernel launch: ") + cudaGetErrorString((cudaError_t)e));
+    return 0;
+}
+
+int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_precision prec, cudaStream_t st) {
+    const int n = h->nbf;
+    if (g_opt.check_sym) {
+        int rc;
+        if ((rc = h->scratch.alloc(64))) return rc;
+        CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
+        k_asym<<<152 * 4, 256, 0, st>>>(D, n, h->scratch.as<unsigned long long>());
+        CKL();
+        unsigned long long b = 0;
+        CK(cudaMemcpyAsync(&b, h->scratch.p, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double m;
+        std::memcpy(&m, &b, 8);
+        if (m > 0.0) return fail(JK_ERR_NOT_SYMMETRIC, "D is not symmetric (max |D - D^T| = " + std::to_string(m) + ")");
+    }
+    CK(cudaMemsetAsync(J, 0, sizeof(double) * n * n, st));
+    CK(cudaMemsetAsync(K, 0, sizeof(double) * n * n, st));
+    int rc;
+    if (prec == JK_FP64) {
+        for (const ClassRows& cr : h->rows)
+            if ((rc = launch_class(h, cr, 0, cr.start.as<long long>(), cr.ket0.as<int>(), cr.total, D, J, K, st))) return rc;
+        h->last_n64 = h->nquartets;
+        h->last_n32 = 0;
+    } else {
+        if ((rc = h->scratch.alloc(64))) return rc;
+        CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
+        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>());
+        CKL();
+        long long n32 = 0, n64 = 0;
+        for (ClassRows& cr : h->rows) {
+            if (cr.total <= 0) continue;
+            DevBuf c64, c32;
+            if ((rc = c64.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = c32.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = cr.s64.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = cr.s32.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
+            k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                              cr.nrows, h->A.as<double4>(),
+                                                              reinterpret_cast<const double*>(h->scratch.p), g_opt.tau,
+                                                              c64.as<long long>(), c32.as<long long>(), cr.k32.as<int>());
+            CKL();
+            CK(cudaMemsetAsync(c64.as<long long>() + cr.nrows, 0, 8, st));
+            CK(cudaMemsetAsync(c32.as<long long>() + cr.nrows, 0, 8, st));
+            if ((rc = scan_exclusive(c64.as<long long>(), cr.s64.as<long long>(), cr.nrows + 1,
+                                     h->scratch.as<long long>() + 2, st)))
+                return rc;
+            CK(cudaMemcpyAsync(&cr.total64, h->scratch.as<long long>() + 2, 8, cudaMemcpyDeviceToHost, st));
+            if ((rc = scan_exclusive(c32.as<long long>(), cr.s32.as<long long>(), cr.nrows + 1,
+                                     h->scratch.as<long long>() + 3, st)))
+                return rc;
+            CK(cudaMemcpyAsync(&cr.total32, h->scratch.as<long long>() + 3, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            n64 += cr.total64;
+            n32 += cr.total32;
+            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.total64, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.total32, D, J, K, st))) return rc;
+            CK(cudaStreamSynchronize(st));  // c64/c32 temporaries
+        }
+        h->last_n32 = n32;
+        h->last_n64 = n64;
+    }
+    const long long tri = (long long)n * (n + 1) / 2;
+    k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
+    k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(K, n);
+    CKL();
+    return 0;
+}
+
+template <int L>
+__global__ void k_boys_eval(int n, const double* T, double* F, int prec, const double* tab, const float* tabf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (prec == 0) {
+        double f[L + 1];
+        gb::boys_f64<L>(T[i], f, tab);
+        for (int m = 0; m <= L; ++m) F[(size_t)i * (L + 1) + m] = f[m];
+    } else {
+        float f[L + 1];
+        gb::boys_f32<L>((float)T[i], f, tabf);
+        for (int m = 0; m <= L; ++m) F[(size_t)i * (L + 1) + m] = f[m];
+    }
+}
+
+template <int L>
+int boys_launch(int n, const double* T, double* F, int prec, int dev, cudaStream_t st) {
+    k_boys_eval<L><<<nblk(n, 128), 128, 0, st>>>(n, T, F, prec, g_boys[dev].tab.as<double>(), g_boys[dev].tabf.as<float>());
+    CKL();
+    return 0;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* jk_last_error(void) { return g_err.c_str(); }
+
+int shellpairs_build(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk_pairs* out, void* cuda_stream) {
+    g_err.clear();
+    if (!atoms || !shells || !out) return fail(JK_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (atoms->natom <= 0 || !atoms->xyz) return fail(JK_ERR_INVALID, "no atoms");
+    if (shells->nshell <= 0 || !shells->atom || !shells->l || !shells->nprim || !shells->prim_offset || !shells->exps ||
+        !shells->coefs)
+        return fail(JK_ERR_INVALID, "no shells");
+    if (!std::isfinite(thresh)) return fail(JK_ERR_INVALID, "threshold not finite");
+    jk_pairs_s* h = new (std::nothrow) jk_pairs_s();
+    if (!h) return fail(JK_ERR_NOMEM, "host allocation");
+    const int rc = build_impl(atoms, shells, thresh, h, static_cast<cudaStream_t>(cuda_stream));
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return JK_OK;
+}
+
+int shellpairs_info(jk_pairs h, int* nbf, int64_t* npairs, int64_t* nquartets, int64_t* nprimq) {
+    if (!h) return fail(JK_ERR_INVALID, "null handle");
+    if (nbf) *nbf = h->nbf;
+    if (npairs) *npairs = h->npair;
+    if (nquartets) *nquartets = h->nquartets;
+    if (nprimq) *nprimq = h->nprimq;
+    return JK_OK;
+}
+
+int jk_build(jk_pairs h, const double* D, double* J, double* K, jk_precision prec, void* cuda_stream) {
+    g_err.clear();
+    if (!h || !D || !J || !K) return fail(JK_ERR_INVALID, "null argument");
+    if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    return jk_build_impl(h, D, J, K, prec, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int jk_energy(int nbf, const double* D, const double* J, const double* K, double* E, void* cuda_stream) {
+    g_err.clear();
+    if (nbf <= 0 || !D || !J || !K || !E) return fail(JK_ERR_INVALID, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int nb = 152 * 2;
+    DevBuf part, out;
+    int rc;
+    if ((rc = part.alloc(sizeof(double2) * nb))) return rc;
+    if ((rc = out.alloc(sizeof(double)))) return rc;
+    k_energy_partial<<<nb, 256, 0, st>>>(D, J, K, (long long)nbf * nbf, part.as<double2>());
+    CKL();
+    k_energy_final<<<1, 32, 0, st>>>(part.as<double2>(), nb, out.as<double>());
+    CKL();
+    CK(cudaMemcpyAsync(E, out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return JK_OK;
+}
+
+int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* cuda_stream) {
+    (void)h; (void)D; (void)dEdR; (void)prec; (void)cuda_stream;
+    return fail(JK_ERR_UNSUPPORTED, "jk_grad: not built yet");
+}
+
+int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J, double* const* K,
+                     jk_precision prec, void* cuda_stream) {
+    g_err.clear();
+    if (nmol < 0 || (nmol > 0 && (!pairs || !D || !J || !K))) return fail(JK_ERR_INVALID, "bad argument");
+    for (int i = 0; i < nmol; ++i) {
+        const int rc = jk_build(pairs[i], D[i], J[i], K[i], prec, cuda_stream);
+        if (rc) return rc;
+    }
+    return JK_OK;
+}
+
+int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* cuda_stream) {
+    g_err.clear();
+    if (L < 0 || L > gb::kLmaxBoys || n < 0 || (n > 0 && (!T || !F))) return fail(JK_ERR_INVALID, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, rc;
+    CK(cudaGetDevice(&dev));
+    if ((rc = ensure_boys(dev, st))) return rc;
+    if (n == 0) return JK_OK;
+    const int p = prec == JK_FP64 ? 0 : 1;
+    switch (L) {
+        case 0: return boys_launch<0>(n, T, F, p, dev, st);
+        case 1: return boys_launch<1>(n, T, F, p, dev, st);
+        case 2: return boys_launch<2>(n, T, F, p, dev, st);
+        case 3: return boys_launch<3>(n, T, F, p, dev, st);
+        case 4: return boys_launch<4>(n, T, F, p, dev, st);
+        case 5: return boys_launch<5>(n, T, F, p, dev, st);
+        case 6: return boys_launch<6>(n, T, F, p, dev, st);
+        case 7: return boys_launch<7>(n, T, F, p, dev, st);
+        case 8: return boys_launch<8>(n, T, F, p, dev, st);
+        case 9: return boys_launch<9>(n, T, F, p, dev, st);
+        case 10: return boys_launch<10>(n, T, F, p, dev, st);
+        case 11: return boys_launch<11>(n, T, F, p, dev, st);
+        case 12: return boys_launch<12>(n, T, F, p, dev, st);
+        default: return boys_launch<13>(n, T, F, p, dev, st);
+    }
+}
+
+int jk_set_option(jk_option opt, double v) {
+    switch (opt) {
+        case JK_OPT_MIXED_TAU: if (!(v >= 0)) return fail(JK_ERR_INVALID, "tau"); g_opt.tau = v; return JK_OK;
+        case JK_OPT_MIXED_TSMALL: if (!(v >= 0)) return fail(JK_ERR_INVALID, "tsmall"); g_opt.tsmall = v; return JK_OK;
+        case JK_OPT_CHECK_SYMMETRY: g_opt.check_sym = v != 0.0; return JK_OK;
+        case JK_OPT_GRAPH: g_opt.graph = v != 0.0; return JK_OK;
+    }
+    return fail(JK_ERR_INVALID, "unknown option");
+}
+
+int jk_get_option(jk_option opt, double* v) {
+    if (!v) return fail(JK_ERR_INVALID, "null");
+    switch (opt) {
+        case JK_OPT_MIXED_TAU: *v = g_opt.tau; return JK_OK;
+        case JK_OPT_MIXED_TSMALL: *v = g_opt.tsmall; return JK_OK;
+        case JK_OPT_CHECK_SYMMETRY: *v = g_opt.check_sym; return JK_OK;
+        case JK_OPT_GRAPH: *v = g_opt.graph; return JK_OK;
+    }
+    return fail(JK_ERR_INVALID, "unknown option");
+}
+
+int jk_last_split(jk_pairs h, int64_t* n32, int64_t* n64) {
+    if (!h) return fail(JK_ERR_INVALID, "null handle");
+    if (n32) *n32 = h->last_n32;
+    if (n64) *n64 = h->last_n64;
+    return JK_OK;
+}
+
+void shellpairs_free(jk_pairs h) { delete h; }
+
+}  // extern "C"

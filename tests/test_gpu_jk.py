@@ -1,0 +1,88 @@
+"""GPU parity: the sm_103a McMurchie-Davidson J/K path against the CPU
+Obara-Saika oracle on the same seeded inputs (called through the C ABI)."""
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10  # Eh, absolute, on every J/K element and on energies
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_13203_gb300 as g
+    g.load()
+    return g
+
+
+def _run(g, mol, D, thresh=None, prec="fp64"):
+    pairs = g.ShellPairs(mol, thresh)
+    Dt = torch.from_numpy(D).cuda()
+    J, K = g.jk_build(pairs, Dt, prec)
+    E = g.jk_energy(Dt, J, K)
+    torch.cuda.synchronize()
+    return pairs, J.cpu().numpy(), K.cpu().numpy(), E
+
+
+def test_boys_against_oracle(g):
+    Ts = np.concatenate([np.linspace(0, 2, 97), np.linspace(2, 45, 301), [79.99, 80.0, 80.01, 120.0, 1e3]])
+    F = g.boys(13, torch.from_numpy(Ts).cuda()).cpu().numpy()
+    for T, row in zip(Ts, F):
+        ref = oracle.boys(13, float(T))
+        assert np.all(np.abs(row - ref) <= 2e-14 * ref + 1e-300), (T, row, ref)
+    F32 = g.boys(13, torch.from_numpy(Ts).cuda(), "mixed").cpu().numpy()
+    for T, row in zip(Ts, F32):
+        ref = oracle.boys(13, float(T))
+        assert np.all(np.abs(row - ref) <= 2e-6 * ref + 1e-37)
+
+
+def test_config0_fp64_matches_oracle(g):
+    mol, D = molgen.config(0)
+    pairs, J, K, E = _run(g, mol, D)
+    Jo, Ko, n = oracle.jk(mol, D, mode="all")
+    assert pairs.nquartets == 78 * 79 // 2
+    assert np.abs(J - Jo).max() <= FP64_TOL and np.abs(K - Ko).max() <= FP64_TOL
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(1, [0, 1, 2], 3, 3), (2, [2, 2, 0], 2, 4), (3, [1, 2], 4, 2),
+                                                    (4, [0, 0, 1, 2], 3, 6)])
+def test_all_l2_classes_fp64(g, seed, shells, natom, kmax):
+    mol = molgen.random_molecule(100 + seed, natom, shells, 1, kmax, 0.05, 5e3, layout="lattice", spacing=2.0)
+    D = molgen.density(mol, 200 + seed)
+    pairs, J, K, E = _run(g, mol, D)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    scale = max(1.0, np.abs(Jo).max())
+    assert np.abs(J - Jo).max() <= FP64_TOL * scale, np.abs(J - Jo).max()
+    assert np.abs(K - Ko).max() <= FP64_TOL * scale, np.abs(K - Ko).max()
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= FP64_TOL * max(1.0, abs(E))
+
+
+def test_screened_fp64_matches_screened_oracle(g):
+    mol = molgen.random_molecule(7, 8, [0, 0, 1, 2], 1, 4, 0.05, 5e3, layout="lattice", spacing=2.5)
+    D = molgen.density(mol, 8)
+    thresh = 1e-8
+    pairs, J, K, E = _run(g, mol, D, thresh)
+    Jo, Ko, n = oracle.jk(mol, D, thresh=thresh, mode="unique")
+    # quartets on the threshold boundary may flip between the two Q evaluations;
+    # each flip moves an element by < 8 * thresh * ncomp * max|D|
+    assert abs(pairs.nquartets - n) <= max(3, n // 10000)
+    bound = FP64_TOL + 8 * 36 * thresh * np.abs(D).max() * abs(pairs.nquartets - n)
+    assert np.abs(J - Jo).max() <= bound and np.abs(K - Ko).max() <= bound
+
+
+def test_mixed_precision_within_target(g):
+    mol = molgen.random_molecule(9, 6, [0, 0, 1, 2], 1, 4, 0.05, 5e3, layout="lattice", spacing=2.5)
+    D = molgen.density(mol, 10)
+    pairs, J, K, E = _run(g, mol, D, 1e-10, "mixed")
+    n32, n64 = g.last_split(pairs)
+    assert n32 + n64 == pairs.nquartets
+    Jo, Ko, _ = oracle.jk(mol, D, thresh=1e-10, mode="unique")
+    assert np.abs(J - Jo).max() <= 1e-6 and np.abs(K - Ko).max() <= 1e-6
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-6
