@@ -138,7 +138,8 @@ typedef enum {
     JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-7) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys in FP64 for T < tsmall (default 1.0) */
     JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous) */
-    JK_OPT_GRAPH = 3             /* nonzero: jk_build_batched captures and replays a CUDA graph */
+    JK_OPT_GRAPH = 3,            /* nonzero: jk_build_batched captures and replays a CUDA graph */
+    JK_OPT_PROFILE = 4           /* nonzero: jk_build records CUDA events around every class launch */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);
@@ -146,6 +147,28 @@ int jk_get_option(jk_option opt, double* value);
 /* Diagnostic counters of the last jk_build on this handle (host, synchronous):
  * number of shell quartets run in FP32 and in FP64. */
 int jk_last_split(jk_pairs pairs, int64_t* n_fp32, int64_t* n_fp64);
+
+/* Number of kernels the last jk_build / jk_grad on this handle launched. */
+int jk_last_launches(jk_pairs pairs, int64_t* nlaunch);
+
+/* Per (bra class, ket class) work of a handle (host, synchronous).  Writes up
+ * to max_rows rows of 6 int64: bra class, ket class (pair classes ordered
+ * ss ps pp ds dp dd fs fp fd ff), shell quartets, primitive quartets,
+ * (shell quartet x bra primitive pair) count, and the algorithmic FP64
+ * operation count of the generated McMurchie-Davidson code for the whole
+ * class.  *nrows receives the number of classes with work. */
+int jk_class_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
+
+/* Launch timings of the last jk_build with JK_OPT_PROFILE set (host,
+ * synchronous): up to max_rows rows of 5 doubles: bra class, ket class,
+ * precision (0 FP64, 1 FP32), shell quartets, milliseconds (CUDA events on
+ * the build's stream).  *nrows receives the number of launches. */
+int jk_profile(jk_pairs pairs, int max_rows, double* rows, int* nrows);
+
+/* Diagnostic microbenchmark: sustained FMA throughput of this GPU's SIMT
+ * pipes (prec JK_FP64: DFMA, JK_MIXED: FFMA), in FLOP/s (2 per FMA), timed
+ * with CUDA events over `iters` dependent-chain iterations per thread. */
+int jk_fma_peak(jk_precision prec, int iters, double* flops_per_s, void* cuda_stream);
 
 void shellpairs_free(jk_pairs pairs);
 

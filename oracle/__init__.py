@@ -63,6 +63,8 @@ def _load():
             lib.orc_jk.restype = C.c_longlong
             lib.orc_jk_rows.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, ip, dp, dp]
             lib.orc_jk_rows.restype = C.c_int
+            lib.orc_jk_quartets.argtypes = [C.POINTER(_Mol), dp, C.c_longlong, ip, dp, dp]
+            lib.orc_jk_quartets.restype = C.c_longlong
             lib.orc_energy.argtypes = [C.c_int, dp, dp, dp]
             lib.orc_energy.restype = C.c_double
             lib.orc_grad.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, dp]
@@ -165,6 +167,44 @@ def jk(mol, D, thresh: float | None = None, mode: str = "unique"):
     K = np.zeros_like(D)
     kept = _load().orc_jk(v.ref(), _dp(D), float(thresh or 0.0), 0 if mode == "all" else 1, _dp(J), _dp(K))
     return J, K, int(kept)
+
+
+def jk_quartets(mol, D, quartets):
+    """J/K contributions (all images) of an explicit list of unique shell
+    quartets, array [n, 4] of (a, b, c, d) with a>=b, c>=d, ab>=cd."""
+    v = _MolView(mol)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    q = np.ascontiguousarray(quartets, dtype=np.int32)
+    J = np.zeros_like(D)
+    K = np.zeros_like(D)
+    n = _load().orc_jk_quartets(v.ref(), _dp(D), int(q.shape[0]), _ip(q), _dp(J), _dp(K))
+    if n < 0:
+        raise ValueError("malformed quartet list")
+    return J, K
+
+
+def sample_unique_quartets(mol, n, seed, thresh=None, Q=None):
+    """n random unique shell quartets (a>=b, c>=d, ab>=cd) that pass the
+    Schwarz test, drawn uniformly (rejection) with numpy PCG64(seed)."""
+    S = mol.nshell
+    if thresh and Q is None:
+        Q = schwarz(mol)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = S * (S + 1) // 2
+    tri_a = np.floor((np.sqrt(8 * np.arange(P) + 1) - 1) / 2).astype(np.int64)
+    tri_b = np.arange(P) - tri_a * (tri_a + 1) // 2
+    out = []
+    while sum(len(o) for o in out) < n:
+        ab = rng.integers(0, P, size=4 * n)
+        cd = rng.integers(0, P, size=4 * n)
+        sw = cd > ab
+        ab, cd = np.where(sw, cd, ab), np.where(sw, ab, cd)
+        a, b, c, d = tri_a[ab], tri_b[ab], tri_a[cd], tri_b[cd]
+        if thresh:
+            keep = Q[a, b] * Q[c, d] >= thresh
+            a, b, c, d = a[keep], b[keep], c[keep], d[keep]
+        out.append(np.stack([a, b, c, d], axis=1))
+    return np.concatenate(out)[:n].astype(np.int32)
 
 
 def jk_rows(mol, D, shells, thresh: float | None = None):

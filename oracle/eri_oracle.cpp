@@ -436,6 +436,60 @@ long long orc_jk(const orc_mol* m, const double* D, double thresh, int mode, dou
     return kept;
 }
 
+// J/K contributions of an explicit list of unique shell quartets
+// quartets[4*i..4*i+3] = (a, b, c, d) with a >= b, c >= d, ab >= cd, each added
+// to all of its permutational images (used to time a bounded sample of a
+// workload).  Returns the number processed, or -1 for a malformed entry.
+long long orc_jk_quartets(const orc_mol* m, const double* D, long long nq, const int* quartets, double* J, double* K) {
+    const auto o = bf_offsets(*m);
+    const int S = m->nshell, N = o[S];
+    for (long long i = 0; i < nq; ++i) {
+        const int* q = quartets + 4 * i;
+        for (int k = 0; k < 4; ++k) if (q[k] < 0 || q[k] >= S) return -1;
+        const long ab = (long)q[0] * (q[0] + 1) / 2 + q[1], cd = (long)q[2] * (q[2] + 1) / 2 + q[3];
+        if (q[1] > q[0] || q[3] > q[2] || cd > ab) return -1;
+    }
+    CompArr Jt((size_t)N * N), Kt((size_t)N * N);
+#pragma omp parallel
+    {
+        Work w;
+        std::vector<double> blk;
+        CompArr Jl((size_t)N * N), Kl((size_t)N * N);
+#pragma omp for schedule(dynamic, 16)
+        for (long long i = 0; i < nq; ++i) {
+            const int a = quartets[4 * i], b = quartets[4 * i + 1], c = quartets[4 * i + 2], d = quartets[4 * i + 3];
+            Shell A = shell_of(*m, a), B = shell_of(*m, b), C = shell_of(*m, c), Dd = shell_of(*m, d);
+            const int na = ncart(A.l), nb = ncart(B.l), nc = ncart(C.l), nd = ncart(Dd.l);
+            blk.resize((size_t)na * nb * nc * nd);
+            eri_quartet(A, B, C, Dd, blk.data(), w);
+            const long ab = (long)a * (a + 1) / 2 + b, cd = (long)c * (c + 1) / 2 + d;
+            double s = 1.0;
+            if (a == b) s *= 0.5;
+            if (c == d) s *= 0.5;
+            if (ab == cd) s *= 0.5;
+            for (int ii = 0; ii < na; ++ii) for (int j = 0; j < nb; ++j)
+            for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
+                const double v = s * blk[((ii * nb + j) * nc + k) * nd + l];
+                const int p = o[a] + ii, q = o[b] + j, r = o[c] + k, t = o[d] + l;
+                const int img[8][4] = {{p, q, r, t}, {q, p, r, t}, {p, q, t, r}, {q, p, t, r},
+                                       {r, t, p, q}, {t, r, p, q}, {r, t, q, p}, {t, r, q, p}};
+                for (int g = 0; g < 8; ++g) {
+                    const int* x = img[g];
+                    Jl.add((size_t)x[0] * N + x[1], v * D[(size_t)x[2] * N + x[3]]);
+                    Kl.add((size_t)x[0] * N + x[2], v * D[(size_t)x[1] * N + x[3]]);
+                }
+            }
+        }
+#pragma omp critical
+        for (size_t i = 0; i < (size_t)N * N; ++i) {
+            Jt.add(i, Jl.s[i]); Jt.add(i, Jl.c[i]);
+            Kt.add(i, Kl.s[i]); Kt.add(i, Kl.c[i]);
+        }
+    }
+    for (size_t i = 0; i < (size_t)N * N; ++i) { J[i] = Jt.get(i); K[i] = Kt.get(i); }
+    return nq;
+}
+
 // Rows of J and K: for every shell in rows[], J[mu,:] and K[mu,:] for all mu
 // of that shell, over the full (screened) quartet list.  Jr/Kr are
 // [sum ncart(rows) x nbf].

@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgb300eri.so")
 
-JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3}
+JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3, "profile": 4}
 _PREC = {"fp64": 0, "mixed": 1}
 
 _lib = None
@@ -40,7 +40,8 @@ class _Shells(C.Structure):
 
 
 EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_build_batched", "jk_energy", "jk_boys",
-           "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error"]
+           "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
+           "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches"]
 
 
 def load():
@@ -63,6 +64,10 @@ def load():
         lib.jk_set_option.argtypes = [C.c_int, C.c_double]
         lib.jk_get_option.argtypes = [C.c_int, C.POINTER(C.c_double)]
         lib.jk_last_split.argtypes = [vp, i64p, i64p]
+        lib.jk_last_launches.argtypes = [vp, i64p]
+        lib.jk_class_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
+        lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
         lib.shellpairs_free.argtypes = [vp]
         lib.shellpairs_free.restype = None
         lib.jk_last_error.restype = C.c_char_p
@@ -193,8 +198,52 @@ def get_option(name: str) -> float:
     return v.value
 
 
+def last_launches(pairs: ShellPairs) -> int:
+    """Kernels launched by the last jk_build / jk_grad on this handle."""
+    n = C.c_int64()
+    _check(load().jk_last_launches(pairs.handle, C.byref(n)))
+    return n.value
+
+
 def last_split(pairs: ShellPairs):
     """(shell quartets run in FP32, in FP64) by the last jk_build on this handle."""
     a, b = C.c_int64(), C.c_int64()
     _check(load().jk_last_split(pairs.handle, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+PAIR_CLASS_NAMES = ["ss", "ps", "pp", "ds", "dp", "dd", "fs", "fp", "fd", "ff"]
+
+
+def class_stats(pairs: ShellPairs):
+    """Per (bra class, ket class): shell quartets, primitive quartets, bra
+    primitive-pair work units and algorithmic FP operation count."""
+    buf = (C.c_int64 * (6 * 64))()
+    n = C.c_int()
+    _check(load().jk_class_stats(pairs.handle, 64, buf, C.byref(n)))
+    out = []
+    for k in range(n.value):
+        r = buf[6 * k:6 * k + 6]
+        out.append(dict(cls=PAIR_CLASS_NAMES[r[0]] + "|" + PAIR_CLASS_NAMES[r[1]], bra=r[0], ket=r[1],
+                        nquartets=r[2], nprimq=r[3], nbrap=r[4], flops=r[5]))
+    return out
+
+
+def profile(pairs: ShellPairs):
+    """Per-launch event timings of the last jk_build (profile option set)."""
+    buf = (C.c_double * (5 * 256))()
+    n = C.c_int()
+    _check(load().jk_profile(pairs.handle, 256, buf, C.byref(n)))
+    out = []
+    for k in range(min(n.value, 256)):
+        r = buf[5 * k:5 * k + 5]
+        out.append(dict(cls=PAIR_CLASS_NAMES[int(r[0])] + "|" + PAIR_CLASS_NAMES[int(r[1])], bra=int(r[0]),
+                        ket=int(r[1]), prec="fp64" if r[2] == 0 else "fp32", nquartets=int(r[3]), ms=r[4]))
+    return out
+
+
+def fma_peak(precision: str = "fp64", iters: int = 20000, stream=None) -> float:
+    """Measured SIMT FMA throughput in FLOP/s (diagnostic microbenchmark)."""
+    v = C.c_double()
+    _check(load().jk_fma_peak(_PREC[precision], int(iters), C.byref(v), _stream_ptr(stream)))
+    return v.value

@@ -599,7 +599,18 @@ int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s) {
     for bra, ket in qs:
         st = stats_all[class_name(bra, ket)]
         rows.append(f"{{{st['flops_per_primq']}, {st['flops_per_brap']}}}")
-    d.append(f"extern \"C\" const int gb_class_flops[{len(qs)}][2] = {{{', '.join(rows)}}};")
+    d.append(f"static const int k_class_flops[{len(qs)}][2] = {{{', '.join(rows)}}};")
+    d.append("""
+// Algorithmic FP operations of the generated code: per primitive quartet and per
+// (shell quartet x bra primitive pair); -1 if the class is not compiled.
+int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap) {
+  if (bra_cls < 0 || ket_cls < 0 || ket_cls > bra_cls || bra_cls >= gb_num_pair_classes()) return -1;
+  const int idx = bra_cls * (bra_cls + 1) / 2 + ket_cls;
+  *per_primq = k_class_flops[idx][0];
+  *per_brap = k_class_flops[idx][1];
+  return 0;
+}
+""")
     fn = os.path.join(outdir, "md_dispatch.cu")
     _write_if_changed(fn, "\n".join(d) + "\n")
     files.append(fn)

@@ -30,6 +30,7 @@
 
 int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, cudaStream_t s);
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
+int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap);
 extern "C" int gb_num_pair_classes();
 
 namespace {
@@ -93,6 +94,7 @@ struct ClassRows {
     int nrows = 0;
     long long total = 0;
     long long nprimq = 0;
+    long long nbrap = 0;
     DevBuf start, bra, ket0;
     // mixed-precision split (filled by jk_build)
     DevBuf s64, k64, s32, k32;
@@ -112,7 +114,14 @@ struct Options {
     double tsmall = 1.0;
     int check_sym = 0;
     int graph = 1;
+    int profile = 0;
 } g_opt;
+
+struct ProfRec {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int bra = 0, ket = 0, prec = 0;
+    long long total = 0;
+};
 
 }  // namespace
 
@@ -130,7 +139,15 @@ struct jk_pairs_s {
     std::vector<ClassRows> rows;
     long long nquartets = 0, nprimq = 0;
     long long last_n32 = 0, last_n64 = 0;
+    long long launches = 0;
     DevBuf scratch;                                 // small reductions
+    std::vector<ProfRec> prof;
+    ~jk_pairs_s() {
+        for (auto& r : prof) {
+            if (r.e0) cudaEventDestroy(r.e0);
+            if (r.e1) cudaEventDestroy(r.e1);
+        }
+    }
 };
 
 namespace {
@@ -218,6 +235,13 @@ __global__ void k_scan_add(long long* out, const long long* boff, long long n) {
 
 __global__ void k_set_total(const long long* in, const long long* out, long long n, long long* total) {
     *total = (n > 0) ? out[n - 1] + in[n - 1] : 0;
+}
+
+// Kernel launches scan_exclusive issues for n elements.
+long long scan_launches(long long n) {
+    if (n <= 0) return 0;
+    const long long nb = (n + 1023) / 1024;
+    return 2 + (nb > 1 ? 1 + scan_launches(nb) : 0);
 }
 
 // in == out is not allowed for the last-element total; callers keep the counts.
@@ -465,6 +489,7 @@ __global__ void k_rows_primq(const long long* cnt, const int* rbra, const int* r
     if (c == 0) return;
     const long long kp = npre[rket0[r] + c] - npre[rket0[r]];
     atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
+    atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
 }
 
 __global__ void k_np_of(const int4* info, long long n, long long* np) {
@@ -821,11 +846,11 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = scan_exclusive(d_npk.as<long long>(), d_npre.as<long long>(), kept + 1, d_tot.as<long long>() + 1, st)))
         return rc;
     DevBuf d_primq;
-    if ((rc = d_primq.alloc(sizeof(unsigned long long)))) return rc;
-    CK(cudaMemsetAsync(d_primq.p, 0, sizeof(unsigned long long), st));
+    if ((rc = d_primq.alloc(2 * sizeof(unsigned long long)))) return rc;
     h->rows.clear();
     h->rows.reserve(ncls * (ncls + 1) / 2);
     h->nquartets = 0;
+    h->nprimq = 0;
     for (int X = 0; X < ncls; ++X) {
         const int x0 = bs[X * kNB], x1 = be[X * kNB + kNB - 1];
         const int nX = x1 - x0;
@@ -851,6 +876,7 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
                                                               cr.ket0.as<int>());
             CKL();
             CK(cudaMemsetAsync(d_cnt.as<long long>() + cr.nrows, 0, sizeof(long long), st));
+            CK(cudaMemsetAsync(d_primq.p, 0, 2 * sizeof(unsigned long long), st));
             if ((rc = scan_exclusive(d_cnt.as<long long>(), cr.start.as<long long>(), cr.nrows + 1,
                                      d_tot.as<long long>() + 2, st)))
                 return rc;
@@ -859,20 +885,21 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
                                                               d_primq.as<unsigned long long>());
             CKL();
             long long tot = 0;
+            unsigned long long pq2[2] = {0, 0};
             CK(cudaMemcpyAsync(&tot, d_tot.as<long long>() + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(pq2, d_primq.p, sizeof(pq2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             cr.total = tot;
+            cr.nprimq = (long long)pq2[0];
+            cr.nbrap = (long long)pq2[1];
             h->nquartets += tot;
+            h->nprimq += cr.nprimq;
         }
     }
-    unsigned long long pq = 0;
-    CK(cudaMemcpyAsync(&pq, d_primq.p, sizeof(pq), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    h->nprimq = (long long)pq;
     return 0;
 }
 
-int launch_class(const jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
+int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
                  long long total, const double* D, double* J, double* K, cudaStream_t st) {
     if (total <= 0) return 0;
     gb::JKArgs a;
@@ -890,8 +917,22 @@ int launch_class(const jk_pairs_s* h, const ClassRows& cr, int prec, const long 
     a.K = K;
     a.nbf = h->nbf;
     if (total >= (1LL << 31) * 128LL) return fail(JK_ERR_UNSUPPORTED, "launch too large");
+    ProfRec* pr = nullptr;
+    if (g_opt.profile) {
+        h->prof.emplace_back();
+        pr = &h->prof.back();
+        CK(cudaEventCreate(&pr->e0));
+        CK(cudaEventCreate(&pr->e1));
+        pr->bra = cr.bra_cls;
+        pr->ket = cr.ket_cls;
+        pr->prec = prec;
+        pr->total = total;
+        CK(cudaEventRecord(pr->e0, st));
+    }
     const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec, a, st);
     if (e) return fail(JK_ERR_CUDA, std::string("ERI kernel launch: ") + cudaGetErrorString((cudaError_t)e));
+    h->launches += 1;
+    if (pr) CK(cudaEventRecord(pr->e1, st));
     return 0;
 }
 
@@ -912,6 +953,12 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     }
     CK(cudaMemsetAsync(J, 0, sizeof(double) * n * n, st));
     CK(cudaMemsetAsync(K, 0, sizeof(double) * n * n, st));
+    for (auto& r : h->prof) {
+        if (r.e0) cudaEventDestroy(r.e0);
+        if (r.e1) cudaEventDestroy(r.e1);
+    }
+    h->prof.clear();
+    h->launches = 0;
     int rc;
     if (prec == JK_FP64) {
         for (const ClassRows& cr : h->rows)
@@ -923,6 +970,7 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
         k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>());
         CKL();
+        h->launches += 1;
         long long n32 = 0, n64 = 0;
         for (ClassRows& cr : h->rows) {
             if (cr.total <= 0) continue;
@@ -937,6 +985,7 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
                                                               reinterpret_cast<const double*>(h->scratch.p), g_opt.tau,
                                                               c64.as<long long>(), c32.as<long long>(), cr.k32.as<int>());
             CKL();
+            h->launches += 1 + 2 * scan_launches(cr.nrows + 1);
             CK(cudaMemsetAsync(c64.as<long long>() + cr.nrows, 0, 8, st));
             CK(cudaMemsetAsync(c32.as<long long>() + cr.nrows, 0, 8, st));
             if ((rc = scan_exclusive(c64.as<long long>(), cr.s64.as<long long>(), cr.nrows + 1,
@@ -961,6 +1010,7 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
     k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(K, n);
     CKL();
+    h->launches += 2;
     return 0;
 }
 
@@ -984,6 +1034,24 @@ int boys_launch(int n, const double* T, double* F, int prec, int dev, cudaStream
     k_boys_eval<L><<<nblk(n, 128), 128, 0, st>>>(n, T, F, prec, g_boys[dev].tab.as<double>(), g_boys[dev].tabf.as<float>());
     CKL();
     return 0;
+}
+
+// Dependent FMA chains: 8 independent accumulators per thread (enough to cover
+// the pipe latency), `iters` rounds each.
+template <class T>
+__global__ void k_fma_peak(int iters, T* sink) {
+    T a0 = (T)threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+    const T m = (T)0.999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
+            a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+        }
+    }
+    const T r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (r == (T)-12345) *sink = r;  // keeps the chains alive
 }
 
 }  // namespace
@@ -1099,6 +1167,7 @@ int jk_set_option(jk_option opt, double v) {
         case JK_OPT_MIXED_TSMALL: if (!(v >= 0)) return fail(JK_ERR_INVALID, "tsmall"); g_opt.tsmall = v; return JK_OK;
         case JK_OPT_CHECK_SYMMETRY: g_opt.check_sym = v != 0.0; return JK_OK;
         case JK_OPT_GRAPH: g_opt.graph = v != 0.0; return JK_OK;
+        case JK_OPT_PROFILE: g_opt.profile = v != 0.0; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -1110,6 +1179,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_MIXED_TSMALL: *v = g_opt.tsmall; return JK_OK;
         case JK_OPT_CHECK_SYMMETRY: *v = g_opt.check_sym; return JK_OK;
         case JK_OPT_GRAPH: *v = g_opt.graph; return JK_OK;
+        case JK_OPT_PROFILE: *v = g_opt.profile; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -1118,6 +1188,77 @@ int jk_last_split(jk_pairs h, int64_t* n32, int64_t* n64) {
     if (!h) return fail(JK_ERR_INVALID, "null handle");
     if (n32) *n32 = h->last_n32;
     if (n64) *n64 = h->last_n64;
+    return JK_OK;
+}
+
+int jk_last_launches(jk_pairs h, int64_t* n) {
+    if (!h || !n) return fail(JK_ERR_INVALID, "bad argument");
+    *n = h->launches;
+    return JK_OK;
+}
+
+int jk_class_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
+    if (!h || !nrows || (max_rows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    int k = 0;
+    for (const ClassRows& cr : h->rows) {
+        if (cr.total <= 0) continue;
+        if (k < max_rows) {
+            int fq = 0, fb = 0;
+            gb_class_flops(cr.bra_cls, cr.ket_cls, &fq, &fb);
+            int64_t* r = rows + 6 * k;
+            r[0] = cr.bra_cls; r[1] = cr.ket_cls; r[2] = cr.total; r[3] = cr.nprimq; r[4] = cr.nbrap;
+            r[5] = (int64_t)fq * cr.nprimq + (int64_t)fb * cr.nbrap;
+        }
+        ++k;
+    }
+    *nrows = k;
+    return JK_OK;
+}
+
+int jk_profile(jk_pairs h, int max_rows, double* rows, int* nrows) {
+    if (!h || !nrows || (max_rows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    int k = 0;
+    for (const ProfRec& r : h->prof) {
+        if (k < max_rows) {
+            CK(cudaEventSynchronize(r.e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+            double* o = rows + 5 * k;
+            o[0] = r.bra; o[1] = r.ket; o[2] = r.prec; o[3] = (double)r.total; o[4] = ms;
+        }
+        ++k;
+    }
+    *nrows = k;
+    return JK_OK;
+}
+
+int jk_fma_peak(jk_precision prec, int iters, double* flops, void* cuda_stream) {
+    if (!flops || iters <= 0) return fail(JK_ERR_INVALID, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf sink;
+    int rc;
+    if ((rc = sink.alloc(16))) return rc;
+    const int blocks = nsm * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    // warm-up, then the timed launch
+    for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, st));
+        if (prec == JK_FP64) k_fma_peak<double><<<blocks, threads, 0, st>>>(iters, sink.as<double>());
+        else k_fma_peak<float><<<blocks, threads, 0, st>>>(iters, sink.as<float>());
+        CKL();
+        CK(cudaEventRecord(e1, st));
+    }
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *flops = 2.0 * 8 * 16 * (double)iters * blocks * threads / (ms * 1e-3);
     return JK_OK;
 }
 
