@@ -148,6 +148,22 @@ int jk_get_option(jk_option opt, double* value);
  * number of shell quartets run in FP32 and in FP64. */
 int jk_last_split(jk_pairs pairs, int64_t* n_fp32, int64_t* n_fp64);
 
+/* Workload Allocator (Sec. 6, Algorithm 2): per angular class, start at one
+ * shell quartet per thread and keep doubling the quartets per thread
+ * ("Combine") while the class's kernel gets faster, reverting otherwise,
+ * until no class improves.  Timed with CUDA events on a prefix of each
+ * class's work; J and K (device, nbf x nbf) are used as scratch and hold
+ * meaningless values afterwards.  The chosen configuration is stored in the
+ * handle and used by later jk_build calls of that precision.  Synchronous. */
+int jk_autotune(jk_pairs pairs, const double* D, double* J, double* K, jk_precision prec, void* cuda_stream);
+
+/* Read / restore the per-class launch configuration (e.g. a tuner cache kept
+ * across runs): up to max_rows rows of 6 ints: bra class, ket class, FP64
+ * block size, FP64 quartets per thread, FP32 block size, FP32 quartets per
+ * thread.  Block sizes must be 32..128 in steps of 32. */
+int jk_tuning(jk_pairs pairs, int max_rows, int* rows, int* nrows);
+int jk_set_tuning(jk_pairs pairs, int nrows, const int* rows);
+
 /* Number of kernels the last jk_build / jk_grad on this handle launched. */
 int jk_last_launches(jk_pairs pairs, int64_t* nlaunch);
 

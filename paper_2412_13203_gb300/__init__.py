@@ -41,7 +41,8 @@ class _Shells(C.Structure):
 
 EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_build_batched", "jk_energy", "jk_boys",
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
-           "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches"]
+           "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
+           "jk_set_tuning"]
 
 
 def load():
@@ -65,6 +66,9 @@ def load():
         lib.jk_get_option.argtypes = [C.c_int, C.POINTER(C.c_double)]
         lib.jk_last_split.argtypes = [vp, i64p, i64p]
         lib.jk_last_launches.argtypes = [vp, i64p]
+        lib.jk_autotune.argtypes = [vp, vp, vp, vp, C.c_int, vp]
+        lib.jk_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.jk_set_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.jk_class_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
         lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
@@ -198,6 +202,39 @@ def get_option(name: str) -> float:
     return v.value
 
 
+def autotune(pairs: ShellPairs, D, precision: str = "fp64", stream=None):
+    """Per-class work-per-thread tuning (the paper's Algorithm 2); returns the
+    chosen configuration (see tuning())."""
+    import torch
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    _check(load().jk_autotune(pairs.handle, _dev_ptr(D), _dev_ptr(J), _dev_ptr(K), _PREC[precision],
+                              _stream_ptr(stream)))
+    return tuning(pairs)
+
+
+def tuning(pairs: ShellPairs):
+    """{class: (fp64 block, fp64 quartets/thread, fp32 block, fp32 quartets/thread)}."""
+    buf = (C.c_int * (6 * 64))()
+    n = C.c_int()
+    _check(load().jk_tuning(pairs.handle, 64, buf, C.byref(n)))
+    out = {}
+    for k in range(n.value):
+        r = buf[6 * k:6 * k + 6]
+        out[PAIR_CLASS_NAMES[r[0]] + "|" + PAIR_CLASS_NAMES[r[1]]] = tuple(r[2:])
+    return out
+
+
+def set_tuning(pairs: ShellPairs, cfg: dict):
+    """Restore a configuration returned by tuning() (a tuner cache)."""
+    rows = []
+    for k, v in cfg.items():
+        a, b = k.split("|")
+        rows += [PAIR_CLASS_NAMES.index(a), PAIR_CLASS_NAMES.index(b)] + [int(x) for x in v]
+    arr = (C.c_int * max(1, len(rows)))(*rows)
+    _check(load().jk_set_tuning(pairs.handle, len(rows) // 6, arr))
+
+
 def last_launches(pairs: ShellPairs) -> int:
     """Kernels launched by the last jk_build / jk_grad on this handle."""
     n = C.c_int64()
@@ -247,3 +284,48 @@ def fma_peak(precision: str = "fp64", iters: int = 20000, stream=None) -> float:
     v = C.c_double()
     _check(load().jk_fma_peak(_PREC[precision], int(iters), C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def _autograd():
+    import torch
+
+    class JKEnergy(torch.autograd.Function):
+        """E(xyz, D) = tr(D J[D])/2 - tr(D K[D])/4 for the molecule's shells
+        placed at the atom positions ``xyz`` (a [natom, 3] float64 tensor).
+
+        Forward: shellpairs_build at xyz + jk_build + jk_energy.  Backward:
+        dE/dxyz from jk_grad (the adjoint kernel), dE/dD = J - K/2."""
+
+        @staticmethod
+        def forward(ctx, xyz, D, mol, thresh=None, precision="fp64"):
+            import copy
+            m = copy.copy(mol)
+            m.xyz = xyz.detach().cpu().numpy().astype(np.float64)
+            pairs = ShellPairs(m, thresh)
+            Dc = D.detach().contiguous()
+            J, K = jk_build(pairs, Dc, precision)
+            E = jk_energy(Dc, J, K)
+            g = jk_grad(pairs, Dc, precision)
+            pairs.free()
+            ctx.save_for_backward(g, J, K)
+            return torch.tensor(E, dtype=torch.float64, device=xyz.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g, J, K = ctx.saved_tensors
+            gx = (gout * g).to(g.device)
+            gD = gout * (J - 0.5 * K)
+            return gx, gD, None, None, None
+
+    return JKEnergy
+
+
+_JKE = None
+
+
+def jk_energy_fn(xyz, D, mol, thresh=None, precision="fp64"):
+    """Differentiable E = tr(DJ)/2 - tr(DK)/4 (torch.autograd.Function)."""
+    global _JKE
+    if _JKE is None:
+        _JKE = _autograd()
+    return _JKE.apply(xyz, D, mol, thresh, precision)

@@ -197,8 +197,9 @@ def gen_E_axis(em: Emitter, tag, la, lb, PA, PB, inv2p, sign=False):
     return E
 
 
-def gen_products(em, tag, la, lb, Ex, Ey, Ez):
-    """Per Cartesian component pair (a, b): list of (hermite triple, Sym)."""
+def gen_products(em, tag, la, lb, Ex, Ey, Ez, extra=None):
+    """Per Cartesian component pair (a, b): list of (hermite triple, Sym).
+    ``extra`` (a Sym) multiplies every product (prefactor folding)."""
     out = []
     for ia, a in enumerate(comps(la)):
         for ib, b in enumerate(comps(lb)):
@@ -206,12 +207,43 @@ def gen_products(em, tag, la, lb, Ex, Ey, Ez):
             for t in range(a[0] + b[0] + 1):
                 for u in range(a[1] + b[1] + 1):
                     for v in range(a[2] + b[2] + 1):
-                        s = em.product([Ex[(a[0], b[0], t)], Ey[(a[1], b[1], u)], Ez[(a[2], b[2], v)]],
-                                       f"{tag}{ia}_{ib}_{t}{u}{v}")
+                        fac = [Ex[(a[0], b[0], t)], Ey[(a[1], b[1], u)], Ez[(a[2], b[2], v)]]
+                        if extra is not None:
+                            fac.append(extra)
+                        s = em.product(fac, f"{tag}{ia}_{ib}_{t}{u}{v}")
                         if not (s.const and s.c == 0.0):
                             lst.append(((t, u, v), s))
             out.append(lst)
     return out
+
+
+def gen_R_scaled(em, L, F, PQs, r2):
+    """R^{(0)}_{tuv} for t+u+v <= L by the scaled recursion (FP32 kernels).
+
+    With Rs^{(n)} = R^{(n)} / (2 rho)^n (prefactor left out, it is folded
+    into the E products):  Rs^{(n)}_{000} = (-1)^n F_n and
+    Rs^{(n)}_{t+1,u,v} = (2 rho t) Rs^{(n+1)}_{t-1,u,v} + (2 rho X_PQ) Rs^{(n+1)}_{tuv},
+    so Rs^{(0)} = R^{(0)} / pref while no intermediate grows like (2 rho)^L
+    (which overflows FP32 for tight exponents)."""
+    prev = {}
+    for n in range(L, -1, -1):
+        cur = {}
+        for (t, u, v) in herm(L - n):
+            if (t, u, v) == (0, 0, 0):
+                cur[(t, u, v)] = Sym(name=f"{F}[{n}]") if n % 2 == 0 else em.define(f"r{n}_000", f"-{F}[{n}]")
+                continue
+            if t > 0:
+                a, lo1, lo2, X = t - 1, (t - 1, u, v), (t - 2, u, v), PQs[0]
+            elif u > 0:
+                a, lo1, lo2, X = u - 1, (t, u - 1, v), (t, u - 2, v), PQs[1]
+            else:
+                a, lo1, lo2, X = v - 1, (t, u, v - 1), (t, u, v - 2), PQs[2]
+            terms = [(Sym(name=X), prev[lo1])]
+            if a > 0:
+                terms.append((Sym(name=f"{r2}{a}"), prev[lo2]))
+            cur[(t, u, v)] = em.lincomb(terms, f"r{n}_{t}_{u}_{v}")
+        prev = cur
+    return prev
 
 
 def gen_R(em, L, pref, m2r, F, PQ):
@@ -301,7 +333,7 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
     Ebz = gen_E_axis(em, "ebz", la, lb, Sym(name="PAz"), Sym(name="PBz"), inv2p)
     flops_ebra = em.flops
-    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz)
+    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz, Sym(name="kp") if f32 else None)
     flops_ebra = em.flops - 0  # total so far (per bra primitive)
     # X accumulators
     if mode_flat:
@@ -320,26 +352,36 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     Ekx = gen_E_axis(em, "ekx", lc, ld, Sym(name="QCx"), Sym(name="QDx"), inv2q, sign=True)
     Eky = gen_E_axis(em, "eky", lc, ld, Sym(name="QCy"), Sym(name="QDy"), inv2q, sign=True)
     Ekz = gen_E_axis(em, "ekz", lc, ld, Sym(name="QCz"), Sym(name="QDz"), inv2q, sign=True)
-    if mode_flat:
-        kprod = gen_products(em, "ek", lc, ld, Ekx, Eky, Ekz)
-    flops_eket = em.flops
-    em.flops = 0
     E(f"const {real} PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
     if f32:
         E("const float rs = rsqrtf(p + q);")
+        E("const float kqrs = kq * rs;")
     else:
         E("const double rs = rsqrt(p + q);")
+    if mode_flat:
+        kprod = gen_products(em, "ek", lc, ld, Ekx, Eky, Ekz, Sym(name="kqrs") if f32 else None)
+    flops_eket = em.flops
+    em.flops = 0
     E(f"const {real} rho = p * q * rs * rs;")
     E(f"const {real} T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
-    E(f"const {real} pref = kp * kq * rs;")
-    E(f"const {real} m2r = -2 * rho;")
+    if f32:
+        E("const float r2 = 2.0f * rho;")
+        E("const float PQsx = r2 * PQx, PQsy = r2 * PQy, PQsz = r2 * PQz;")
+        for a in range(1, L):
+            E(f"const float r2k{a} = {float(a)!r}f * r2;")
+    else:
+        E(f"const {real} pref = kp * kq * rs;")
+        E(f"const {real} m2r = -2 * rho;")
     E(f"{real} F[{L + 1}];")
     if f32:
         E(f"gb::boys_mixed<{L}>(T, F, boys, boysf, tsmall);")
     else:
         E(f"gb::boys_f64<{L}>(T, F, boys);")
     flops_setup = 16 + (kBoysCost(L))
-    R = gen_R(em, L, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
+    if f32:
+        R = gen_R_scaled(em, L, "F", ("PQsx", "PQsy", "PQsz"), "r2k")
+    else:
+        R = gen_R(em, L, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
     flops_R = em.flops
     em.flops = 0
     if mode_flat:
@@ -369,7 +411,7 @@ def gen_quartet_body(bra, ket, real, mode_flat):
         for h in range(HAB):
             E(f"{real} xh{h} = Xl[{h} * {NCD} + cd];")
         E("for (int tau = 0; tau <= cx + dx; ++tau) {")
-        E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {lc + ld + 1} + tau];")
+        E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {lc + ld + 1} + tau]{' * kqrs' if f32 else ''};")
         E("for (int nu = 0; nu <= cy + dy; ++nu) {")
         E(f"const {real} exy = ex * ekya[(cy * {ld + 1} + dy) * {lc + ld + 1} + nu];")
         E("for (int phi = 0; phi <= cz + dz; ++phi) {")
@@ -454,15 +496,26 @@ def gen_class_kernels(bra, ket):
         cen = ("Af", "Bf") if real == "float" else ("A", "B")
         out.append(f"""
 __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs args) {{
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= args.total) return;
-  int bra, ket;
-  gb::locate_quartet(args.rows, tid, bra, ket);
-  const gb::PairsView& pairs = args.pairs;
+  // persistent grid-stride loop over the quartets of this launch; the total is
+  // read on the device (last entry of the row prefix) so launches need no host sync
+  const long long total = args.rows.start[args.rows.nrows];
   const double* __restrict__ boys = args.boys;
   const float* __restrict__ boysf = args.boysf;
   const float tsmall = args.tsmall;
   (void)boysf; (void)tsmall;
+  for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
+       tid += (long long)gridDim.x * blockDim.x) {{
+  int bra, ket, row;
+  gb::locate_quartet(args.rows, tid, bra, ket, row);
+  gb::PairsView pairs = args.pairs;
+  const double* Dm = args.D;
+  double* Jm = args.J;
+  double* Km = args.K;
+  int nbf = args.nbf;
+  if (args.mols) {{
+    const gb::BatchMol& bm = args.mols[args.row_mol[row]];
+    pairs = bm.pairs; Dm = bm.D; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
+  }}
   const int4 ib = pairs.info[bra], ik = pairs.info[ket];
   const {vec}4 A = pairs.{cen[0]}[bra], B = pairs.{cen[1]}[bra], C = pairs.{cen[0]}[ket], Dd = pairs.{cen[1]}[ket];
 {indent(body)}
@@ -472,7 +525,8 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs arg
   if (bra == ket) s *= 0.5;
 #pragma unroll
   for (int i = 0; i < {na * nb * nc * nd}; ++i) acc[i] *= s;
-  gb::{"digest" if flat else "digest_loop"}<{na}, {nb}, {nc}, {nd}>(acc, ib.x, ib.y, ik.x, ik.y, args.D, args.J, args.K, args.nbf);
+  gb::{"digest" if flat else "digest_loop"}<{na}, {nb}, {nc}, {nd}>(acc, ib.x, ib.y, ik.x, ik.y, Dm, Jm, Km, nbf);
+  }}
 }}
 """)
         if bra == ket and prec == "f64":
@@ -503,6 +557,224 @@ def body_f64_for_schwarz(bra, ket):
     if key not in _BODY_CACHE:
         _BODY_CACHE[key] = gen_quartet_body(bra, ket, "double", use_flat(bra, ket))[0]
     return _BODY_CACHE[key]
+
+
+# ---------------------------------------------------------------- gradient kernels
+def comp_table(l):
+    rows = []
+    for c in comps(l):
+        rows += list(c)
+    return f"static __device__ __constant__ int c_comp_{l}[{len(rows)}] = {{{', '.join(map(str, rows))}}};"
+
+
+def _store_axis_array(E, em, name, li, lj, E_axis):
+    """Write per-axis E[(i,j,t)] (i <= li, j <= lj) into a flat local array."""
+    T = li + lj + 1
+    E(f"double {name}[{(li + 1) * (lj + 1) * T}];")
+    for i in range(li + 1):
+        for j in range(lj + 1):
+            for t in range(T):
+                sv = E_axis.get((i, j, t), ZERO)
+                E(f"{name}[{(i * (lj + 1) + j) * T + t}] = {em.val(sv)};")
+
+
+def gen_grad_kernel(bra, ket):
+    """FP64 nuclear-gradient kernel of one class.
+
+    Per unique shell quartet: Gamma_abcd = s (4 D_ab D_cd - D_ac D_bd - D_ad D_bc)
+    (the weight of (ab|cd) in E = tr(DJ)/2 - tr(DK)/4 summed over its eight
+    images, s the degeneracy factor); derivative integrals by the shift rule
+    d/dA_x phi_a = 2 alpha phi_{a+1x} - a_x phi_{a-1x}, which in the Hermite
+    expansion only changes the x-axis coefficient:
+      E'^{ab}_t = 2 alpha E^{a_x+1, b_x}_t - a_x E^{a_x-1, b_x}_t  (centre A),
+      E'^{ab}_t = 2 beta  E^{a_x, b_x+1}_t - b_x E^{a_x, b_x-1}_t  (centre B),
+    the same on the ket for centre C, and dI/dD = -(dI/dA + dI/dB + dI/dC)
+    (translational invariance)."""
+    la, lb = bra
+    lc, ld = ket
+    L = la + lb + lc + ld
+    L1 = L + 1            # highest Hermite order needed
+    S = L1 + 1            # cube side of R
+    na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
+    NAB, NCD = na * nb, nc * nd
+    h1 = herm(la + lb + 1)
+    h0 = herm(la + lb)
+    H1, H0 = len(h1), len(h0)
+    em = Emitter("double")
+    E = em.emit
+    name = class_name(bra, ket)
+    TB = la + lb + 3      # t range of the bra arrays (i <= la+1, j <= lb+1)
+    TK = lc + ld + 2      # t range of the ket arrays (i <= lc+1, j <= ld)
+    E(f"__global__ void __launch_bounds__(128) eri_grad_{name}_f64(const gb::GradArgs args) {{")
+    E("const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
+    E("if (tid >= args.total) return;")
+    E("int bra, ket, row;")
+    E("gb::locate_quartet(args.rows, tid, bra, ket, row);")
+    E("const gb::PairsView& pairs = args.pairs;")
+    E("const double* __restrict__ boys = args.boys;")
+    E("const double* __restrict__ Dm = args.D;")
+    E("const int n = args.nbf;")
+    E("const int4 ib = pairs.info[bra], ik = pairs.info[ket];")
+    E("const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];")
+    E("double s = 1.0;")
+    E("if (ib.x == ib.y) s *= 0.5;")
+    E("if (ik.x == ik.y) s *= 0.5;")
+    E("if (bra == ket) s *= 0.5;")
+    E(f"double G[{NAB * NCD}];")
+    E(f"for (int ab = 0; ab < {NAB}; ++ab) {{")
+    E(f"  const int a = ib.x + ab / {nb}, b = ib.y + ab % {nb};")
+    E(f"  for (int cd = 0; cd < {NCD}; ++cd) {{")
+    E(f"    const int c = ik.x + cd / {nd}, d = ik.y + cd % {nd};")
+    E("    G[ab * %d + cd] = s * (4.0 * Dm[(size_t)a * n + b] * Dm[(size_t)c * n + d] - Dm[(size_t)a * n + c] * Dm[(size_t)b * n + d] - Dm[(size_t)a * n + d] * Dm[(size_t)b * n + c]);" % NCD)
+    E("  }")
+    E("}")
+    E("double gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gC[3] = {0, 0, 0};")
+    E(f"double X[{H1 * NCD}];")
+    E(f"double XC[{3 * H0 * NCD}];")
+    E(f"double Rc[{S * S * S}];")
+    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
+    E("const double p = pa.w, kp = pb.x, inv2p = pb.y, alpha = pairs.alpha[ib.w + ip], beta = p - alpha;")
+    E("const double PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
+    E("const double PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
+    inv2p = Sym(name="inv2p")
+    for ax in "xyz":
+        Eb = gen_E_axis(em, f"gb{ax}", la + 1, lb + 1, Sym(name=f"PA{ax}"), Sym(name=f"PB{ax}"), inv2p)
+        _store_axis_array(E, em, f"eb{ax}", la + 1, lb + 1, Eb)
+    E(f"for (int i = 0; i < {H1 * NCD}; ++i) X[i] = 0.0;")
+    E(f"for (int i = 0; i < {3 * H0 * NCD}; ++i) XC[i] = 0.0;")
+    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    E("const double4 qa = pairs.pp[ik.w + jq]; const double2 qb = pairs.pp2[ik.w + jq];")
+    E("const double q = qa.w, kq = qb.x, inv2q = qb.y, gam2 = 2.0 * pairs.alpha[ik.w + jq];")
+    E("const double QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
+    E("const double QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
+    inv2q = Sym(name="inv2q")
+    for ax in "xyz":
+        Ek = gen_E_axis(em, f"gk{ax}", lc + 1, ld, Sym(name=f"QC{ax}"), Sym(name=f"QD{ax}"), inv2q, sign=True)
+        _store_axis_array(E, em, f"ek{ax}", lc + 1, ld, Ek)
+    E("const double PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
+    E("const double rs = rsqrt(p + q);")
+    E("const double rho = p * q * rs * rs;")
+    E("const double T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
+    E("const double pref = kp * kq * rs;")
+    E("const double m2r = -2 * rho;")
+    E(f"double F[{L1 + 1}];")
+    E(f"gb::boys_f64<{L1}>(T, F, boys);")
+    R = gen_R(em, L1, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
+    for (t, u, v), sv in R.items():
+        E(f"Rc[{(t * S + u) * S + v}] = {em.val(sv)};")
+    E(f"for (int cd = 0; cd < {NCD}; ++cd) {{")
+    E(f"  const int c = cd / {nd}, d = cd % {nd};")
+    E(f"  const int cx = c_comp_{lc}[3 * c], cy = c_comp_{lc}[3 * c + 1], cz = c_comp_{lc}[3 * c + 2];")
+    E(f"  const int dx = c_comp_{ld}[3 * d], dy = c_comp_{ld}[3 * d + 1], dz = c_comp_{ld}[3 * d + 2];")
+    # X over H1
+    for k in range(H1):
+        E(f"  double xh{k} = X[{k * NCD} + cd];")
+    E("  for (int tau = 0; tau <= cx + dx; ++tau) {")
+    E(f"    const double ex = ekx[(cx * {ld + 1} + dx) * {TK} + tau];")
+    E("    for (int nu = 0; nu <= cy + dy; ++nu) {")
+    E(f"      const double exy = ex * eky[(cy * {ld + 1} + dy) * {TK} + nu];")
+    E("      for (int phi = 0; phi <= cz + dz; ++phi) {")
+    E(f"        const double e = exy * ekz[(cz * {ld + 1} + dz) * {TK} + phi];")
+    E(f"        const double* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
+    for k, (t, u, v) in enumerate(h1):
+        E(f"        xh{k} = fma(e, Rb[{(t * S + u) * S + v}], xh{k});")
+    E("  }}}")
+    for k in range(H1):
+        E(f"  X[{k * NCD} + cd] = xh{k};")
+    # XC for the three directions
+    for di, ax in enumerate("xyz"):
+        cc = {"x": ("cx", "dx"), "y": ("cy", "dy"), "z": ("cz", "dz")}
+        E("  {")
+        for k in range(H0):
+            E(f"  double xc{k} = XC[{(di * H0 + k) * NCD} + cd];")
+        rng = {a: (f"{cc[a][0]} + {cc[a][1]}" + (" + 1" if a == ax else "")) for a in "xyz"}
+        idx = {"x": "tau", "y": "nu", "z": "phi"}
+
+        def coef(a):
+            c, d = cc[a]
+            v = idx[a]
+            if a != ax:
+                return f"ek{a}[({c} * {ld + 1} + {d}) * {TK} + {v}]"
+            return (f"(gam2 * ek{a}[(({c} + 1) * {ld + 1} + {d}) * {TK} + {v}]"
+                    f" - ({c} > 0 ? {c} * ek{a}[(({c} - 1) * {ld + 1} + {d}) * {TK} + {v}] : 0.0))")
+        E(f"  for (int tau = 0; tau <= {rng['x']}; ++tau) {{")
+        E(f"    const double ex = {coef('x')};")
+        E(f"    for (int nu = 0; nu <= {rng['y']}; ++nu) {{")
+        E(f"      const double exy = ex * {coef('y')};")
+        E(f"      for (int phi = 0; phi <= {rng['z']}; ++phi) {{")
+        E(f"        const double e = exy * {coef('z')};")
+        E(f"        const double* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
+        for k, (t, u, v) in enumerate(h0):
+            E(f"        xc{k} = fma(e, Rb[{(t * S + u) * S + v}], xc{k});")
+        E("  }}}")
+        for k in range(H0):
+            E(f"  XC[{(di * H0 + k) * NCD} + cd] = xc{k};")
+        E("  }")
+    E("}")  # cd
+    E("}  // ket primitives")
+    # contraction with Gamma
+    TBs = TB
+    E(f"for (int ab = 0; ab < {NAB}; ++ab) {{")
+    E(f"  const int a = ab / {nb}, b = ab % {nb};")
+    E(f"  const int ax_ = c_comp_{la}[3 * a], ay_ = c_comp_{la}[3 * a + 1], az_ = c_comp_{la}[3 * a + 2];")
+    E(f"  const int bx_ = c_comp_{lb}[3 * b], by_ = c_comp_{lb}[3 * b + 1], bz_ = c_comp_{lb}[3 * b + 2];")
+    E("  const int ai[3] = {ax_, ay_, az_}, bi[3] = {bx_, by_, bz_};")
+    E("  const double* ebv[3] = {ebx, eby, ebz};")
+    E(f"  for (int cd = 0; cd < {NCD}; ++cd) {{")
+    E(f"    const double g = G[ab * {NCD} + cd];")
+    E("    if (g == 0.0) continue;")
+    # plain bra E over H0 for the C derivative; derivative bra E over H1 for A and B
+    E("    for (int dir = 0; dir < 3; ++dir) {")
+    E("      double vA = 0.0, vB = 0.0, vC = 0.0;")
+    E("      const int rx = ai[0] + bi[0] + (dir == 0), ry = ai[1] + bi[1] + (dir == 1), rz = ai[2] + bi[2] + (dir == 2);")
+    E("      for (int t = 0; t <= rx; ++t) for (int u = 0; u <= ry; ++u) for (int v = 0; v <= rz; ++v) {")
+    E("        const int tt[3] = {t, u, v};")
+    E("        double fA = 1.0, fB = 1.0, f0 = 1.0;")
+    E("        for (int k = 0; k < 3; ++k) {")
+    E(f"          const double* e = ebv[k];")
+    E(f"          const double base = e[(ai[k] * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
+    E("          if (k == dir) {")
+    E(f"            const double up_a = e[((ai[k] + 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
+    E(f"            const double dn_a = ai[k] > 0 ? e[((ai[k] - 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]] : 0.0;")
+    E(f"            const double up_b = e[(ai[k] * {lb + 2} + bi[k] + 1) * {TBs} + tt[k]];")
+    E(f"            const double dn_b = bi[k] > 0 ? e[(ai[k] * {lb + 2} + bi[k] - 1) * {TBs} + tt[k]] : 0.0;")
+    E("            fA *= 2.0 * alpha * up_a - ai[k] * dn_a;")
+    E("            fB *= 2.0 * beta * up_b - bi[k] * dn_b;")
+    E("            f0 *= base;")
+    E("          } else { fA *= base; fB *= base; f0 *= base; }")
+    E("        }")
+    E("        const int tot = t + u + v;")
+    E("        const int h = tot * (tot + 1) * (tot + 2) / 6 + (tot - t) * (tot - t + 1) / 2 + (tot - t - u);")
+    E(f"        const double xv = X[h * {NCD} + cd];")
+    E("        vA = fma(fA, xv, vA);")
+    E("        vB = fma(fB, xv, vB);")
+    E(f"        if (tot <= {la + lb} && t <= ai[0] + bi[0] && u <= ai[1] + bi[1] && v <= ai[2] + bi[2])")
+    E(f"          vC = fma(f0, XC[(dir * {H0} + h) * {NCD} + cd], vC);")
+    E("      }")
+    E("      gA[dir] = fma(g, vA, gA[dir]);")
+    E("      gB[dir] = fma(g, vB, gB[dir]);")
+    E("      gC[dir] = fma(g, vC, gC[dir]);")
+    E("    }")
+    E("  }")
+    E("}")
+    E("}  // bra primitives")
+    E("const int2 atb = args.atoms[bra], atk = args.atoms[ket];")
+    E("for (int k = 0; k < 3; ++k) {")
+    E("  atomicAdd(args.grad + 3 * atb.x + k, gA[k]);")
+    E("  atomicAdd(args.grad + 3 * atb.y + k, gB[k]);")
+    E("  atomicAdd(args.grad + 3 * atk.x + k, gC[k]);")
+    E("  atomicAdd(args.grad + 3 * atk.y + k, -(gA[k] + gB[k] + gC[k]));")
+    E("}")
+    E("}")
+    E(f"""
+int launch_grad_{name}(const gb::GradArgs& a, cudaStream_t s) {{
+  if (a.total <= 0) return 0;
+  const int bs = 128;
+  eri_grad_{name}_f64<<<(unsigned)((a.total + bs - 1) / bs), bs, 0, s>>>(a);
+  return (int)cudaGetLastError();
+}}""")
+    return "\n".join(em.lines) + "\n"
 
 
 def indent(s, n=2):
@@ -545,12 +817,10 @@ def generate(outdir, lmax=LMAX, nfiles=8):
             stats_all[class_name(bra, ket)] = st
             name = class_name(bra, ket)
             src.append(f"""
-int launch_jk_{name}(int prec, const gb::JKArgs& a, cudaStream_t s) {{
-  if (a.total <= 0) return 0;
-  const int bs = 128;
-  const long long nb = (a.total + bs - 1) / bs;
-  if (prec == 0) eri_jk_{name}_f64<<<(unsigned)nb, bs, 0, s>>>(a);
-  else eri_jk_{name}_f32<<<(unsigned)nb, bs, 0, s>>>(a);
+int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s) {{
+  if (grid <= 0) return 0;
+  if (prec == 0) eri_jk_{name}_f64<<<grid, block, 0, s>>>(a);
+  else eri_jk_{name}_f32<<<grid, block, 0, s>>>(a);
   return (int)cudaGetLastError();
 }}
 """)
@@ -566,16 +836,32 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
         fn = os.path.join(outdir, f"md_classes_{k}.cu")
         _write_if_changed(fn, "".join(src))
         files.append(fn)
+    # gradient kernels (rolled loops, compact), spread over a few TUs
+    ngf = 4
+    gbins = [[] for _ in range(ngf)]
+    for i, (bra, ket) in enumerate(sorted(qs, key=lambda x: -sum(x[0] + x[1]))):
+        gbins[i % ngf].append((bra, ket))
+    for k, items in enumerate(gbins):
+        if not items:
+            continue
+        src = [header] + [comp_table(l) for l in range(lmax + 1)]
+        for bra, ket in items:
+            src.append(gen_grad_kernel(bra, ket))
+        fn = os.path.join(outdir, f"md_grad_{k}.cu")
+        _write_if_changed(fn, "".join(src))
+        files.append(fn)
     # dispatch
     d = ['#include "eri_device.cuh"', "namespace gbgen {"]
     d.append("}")
     for bra, ket in qs:
-        d.append(f"int launch_jk_{class_name(bra, ket)}(int prec, const gb::JKArgs& a, cudaStream_t s);")
+        d.append(f"int launch_jk_{class_name(bra, ket)}(int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s);")
     pcs = [pc for pc in PAIR_CLASSES if pc[0] <= lmax]
     for pc in pcs:
         d.append(f"int launch_schwarz_{pc[0]}{pc[1]}(const gb::SchwarzArgs& a, cudaStream_t s);")
+    for bra, ket in qs:
+        d.append(f"int launch_grad_{class_name(bra, ket)}(const gb::GradArgs& a, cudaStream_t s);")
     n = len(pcs)
-    d.append("typedef int (*jk_launch_fn)(int, const gb::JKArgs&, cudaStream_t);")
+    d.append("typedef int (*jk_launch_fn)(int, const gb::JKArgs&, int, int, cudaStream_t);")
     d.append("typedef int (*schwarz_launch_fn)(const gb::SchwarzArgs&, cudaStream_t);")
     tab = []
     for i in range(n):
@@ -584,11 +870,18 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
             row.append(f"launch_jk_{class_name(pcs[i], pcs[j])}" if j <= i else "nullptr")
         tab.append("{" + ", ".join(row) + "}")
     d.append(f"extern \"C\" int gb_num_pair_classes() {{ return {n}; }}")
+    d.append("typedef int (*grad_launch_fn)(const gb::GradArgs&, cudaStream_t);")
+    gtab = []
+    for i in range(n):
+        row = [f"launch_grad_{class_name(pcs[i], pcs[j])}" if j <= i else "nullptr" for j in range(n)]
+        gtab.append("{" + ", ".join(row) + "}")
+    d.append(f"static const grad_launch_fn k_grad_tab[{n}][{n}] = {{{', '.join(gtab)}}};")
+    d.append("int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s) { return k_grad_tab[bra_cls][ket_cls](a, s); }")
     d.append(f"static const jk_launch_fn k_jk_tab[{n}][{n}] = {{{', '.join(tab)}}};")
     d.append(f"static const schwarz_launch_fn k_sw_tab[{n}] = {{{', '.join(f'launch_schwarz_{pc[0]}{pc[1]}' for pc in pcs)}}};")
     d.append("""
-int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, cudaStream_t s) {
-  return k_jk_tab[bra_cls][ket_cls](prec, a, s);
+int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s) {
+  return k_jk_tab[bra_cls][ket_cls](prec, a, grid, block, s);
 }
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s) {
   return k_sw_tab[cls](a, s);

@@ -35,6 +35,7 @@ struct PairsView {
     const double2* pp2;    // per primitive pair: kappa = sqrt(2 pi^(5/2)) K_AB c_a c_b / p, 1/(2p)
     const float4* ppf;     // FP32 copies
     const float2* ppf2;
+    const double* alpha;   // per primitive pair: exponent of the shell-a primitive (gradients)
 };
 
 struct RowsView {
@@ -44,10 +45,18 @@ struct RowsView {
     const int* ket0;         // first ket pair of every row (kets are contiguous)
 };
 
+// One molecule of a batched launch.
+struct BatchMol {
+    PairsView pairs;
+    const double* D;
+    double* J;
+    double* K;
+    int nbf;
+};
+
 struct JKArgs {
     PairsView pairs;
-    RowsView rows;
-    long long total;          // quartets in this launch (= rows.start[nrows])
+    RowsView rows;            // quartets of this launch: rows.start[rows.nrows] (read on the device)
     const double* boys;       // FP64 Boys table
     const float* boysf;       // FP32 Boys table
     float tsmall;             // mixed kernels: FP64 Boys below this T
@@ -55,6 +64,19 @@ struct JKArgs {
     double* J;                // accumulates J' (J = J' + J'^T afterwards)
     double* K;                // accumulates K'
     int nbf;
+    const BatchMol* mols;     // batched launches: per-molecule data (nullptr: single molecule above)
+    const int* row_mol;       // batched launches: molecule of every row
+};
+
+struct GradArgs {
+    PairsView pairs;
+    RowsView rows;
+    long long total;
+    const double* boys;
+    const double* D;
+    int nbf;
+    const int2* atoms;        // per pair: atoms of shells a and b
+    double* grad;             // [natom * 3], accumulated
 };
 
 struct SchwarzArgs {
@@ -138,7 +160,7 @@ __device__ __forceinline__ void boys_mixed(float T, float* F, const double* __re
 
 // ------------------------------------------------------------------ rows
 // Largest r with start[r] <= t (t < start[nrows]).
-__device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, int& bra, int& ket) {
+__device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, int& bra, int& ket, int& row) {
     int lo = 0, hi = rv.nrows;  // invariant: start[lo] <= t < start[hi]
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -146,6 +168,7 @@ __device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, 
     }
     bra = __ldg(rv.bra + lo);
     ket = __ldg(rv.ket0 + lo) + (int)(t - __ldg(rv.start + lo));
+    row = lo;
 }
 
 // ------------------------------------------------------------------ digestion

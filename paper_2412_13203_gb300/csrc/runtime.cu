@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -28,9 +29,10 @@
 #include "eri_device.cuh"
 #include "gb300_eri.h"
 
-int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, cudaStream_t s);
+int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s);
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
 int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap);
+int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s);
 extern "C" int gb_num_pair_classes();
 
 namespace {
@@ -89,6 +91,11 @@ struct DevBuf {
 constexpr int kMaxClasses = 10;  // pair classes for l <= 3
 constexpr int kNB = 16;          // primitive-pair-count buckets (ceil log2)
 
+struct TuneCfg {
+    int block = 128;  // threads per block (kernels are compiled for <= 128)
+    int qpt = 1;      // quartets per thread
+};
+
 struct ClassRows {
     int bra_cls = 0, ket_cls = 0;
     int nrows = 0;
@@ -96,9 +103,9 @@ struct ClassRows {
     long long nprimq = 0;
     long long nbrap = 0;
     DevBuf start, bra, ket0;
-    // mixed-precision split (filled by jk_build)
-    DevBuf s64, k64, s32, k32;
-    long long total64 = 0, total32 = 0;
+    // mixed-precision split (filled on the device by jk_build)
+    DevBuf s64, s32, k32, c64, c32, scr;
+    TuneCfg tune[2];  // per precision (0 FP64 kernels, 1 FP32 kernels)
 };
 
 // Boys tables (one set per device, built on first use).
@@ -131,6 +138,7 @@ struct jk_pairs_s {
     long long npair_all = 0, npair = 0, nprimpair = 0;
     double thresh = 0.0, Qmax = 0.0;
     DevBuf info, A, B, Af, Bf, pp, pp2, ppf, ppf2;  // sorted, kept pairs
+    DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
     DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
     DevBuf pair_lab;                                // int2 per pair: la, lb
     DevBuf xyz;                                     // atoms
@@ -140,6 +148,10 @@ struct jk_pairs_s {
     long long nquartets = 0, nprimq = 0;
     long long last_n32 = 0, last_n64 = 0;
     long long launches = 0;
+    int nsm = 152;
+    int last_prec = 0;
+    int tuned[2] = {0, 0};
+    DevBuf split_tot;                               // per class: FP32 and FP64 quartets of the last mixed build
     DevBuf scratch;                                 // small reductions
     std::vector<ProfRec> prof;
     ~jk_pairs_s() {
@@ -245,27 +257,47 @@ long long scan_launches(long long n) {
 }
 
 // in == out is not allowed for the last-element total; callers keep the counts.
-int scan_exclusive(const long long* in, long long* out, long long n, long long* total_dev, cudaStream_t st) {
+// long longs of scratch scan_into needs for n elements.
+long long scan_scratch_len(long long n) {
+    if (n <= 1024) return 0;
+    const long long nb = (n + 1023) / 1024;
+    return 2 * nb + 1 + scan_scratch_len(nb);
+}
+
+// Exclusive scan with caller-provided scratch (no allocation, no host sync).
+int scan_into(const long long* in, long long* out, long long n, long long* total_dev, long long* scratch,
+              cudaStream_t st) {
     if (n <= 0) {
         CK(cudaMemsetAsync(total_dev, 0, sizeof(long long), st));
         return 0;
     }
     const long long nb = (n + 1023) / 1024;
-    DevBuf bsum, boff, btot;
-    int rc;
-    if ((rc = bsum.alloc(sizeof(long long) * nb))) return rc;
-    if ((rc = boff.alloc(sizeof(long long) * nb))) return rc;
-    if ((rc = btot.alloc(sizeof(long long)))) return rc;
-    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in, out, bsum.as<long long>(), n);
-    CKL();
-    if (nb > 1) {
-        if ((rc = scan_exclusive(bsum.as<long long>(), boff.as<long long>(), nb, btot.as<long long>(), st))) return rc;
-        k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, boff.as<long long>(), n);
+    long long* bsum = scratch;
+    long long* boff = scratch + nb;
+    long long* btot = scratch + 2 * nb;
+    if (nb == 1) {
+        // single block: its block sum slot is unused, use the total slot directly
+        k_scan_block<<<1, 1024, 0, st>>>(in, out, total_dev, n);
+        CKL();
+    } else {
+        k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(in, out, bsum, n);
+        CKL();
+        int rc;
+        if ((rc = scan_into(bsum, boff, nb, btot, scratch + 2 * nb + 1, st))) return rc;
+        k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, boff, n);
         CKL();
     }
     k_set_total<<<1, 1, 0, st>>>(in, out, n, total_dev);
     CKL();
-    // temporaries are freed on return; make sure the stream is done with them
+    return 0;
+}
+
+// Exclusive scan with temporary scratch (synchronises before freeing it).
+int scan_exclusive(const long long* in, long long* out, long long n, long long* total_dev, cudaStream_t st) {
+    DevBuf tmp;
+    int rc;
+    if ((rc = tmp.alloc(sizeof(long long) * (scan_scratch_len(n) + 1)))) return rc;
+    if ((rc = scan_into(in, out, n, total_dev, tmp.as<long long>(), st))) return rc;
     CK(cudaStreamSynchronize(st));
     return 0;
 }
@@ -354,7 +386,7 @@ __global__ void k_pair_count(ShellDev S, long long npair, long long* nprimpair, 
 }
 
 __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, int4* info, double4* A, double4* B,
-                            int2* atoms, int2* lab, double4* pp, double2* pp2) {
+                            int2* atoms, int2* lab, double4* pp, double2* pp2, double* alpha) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair) return;
     int i, j, a, b;
@@ -381,6 +413,7 @@ __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, 
             pp[o + n] = make_double4((al * Ra[0] + be * Rb[0]) * ip, (al * Ra[1] + be * Rb[1]) * ip,
                                      (al * Ra[2] + be * Rb[2]) * ip, p);
             pp2[o + n] = make_double2(s2pi52 * Kab * S.c[S.off[a] + u] * S.c[S.off[b] + v] * ip, 0.5 * ip);
+            alpha[o + n] = al;
         }
 }
 
@@ -597,6 +630,7 @@ __global__ void k_energy_final(const double2* part, int nb, double* E) {
 
 unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+
 int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
 
 gb::PairsView view_of(const jk_pairs_s* h) {
@@ -611,6 +645,7 @@ gb::PairsView view_of(const jk_pairs_s* h) {
     v.pp2 = h->pp2.as<double2>();
     v.ppf = h->ppf.as<float4>();
     v.ppf2 = h->ppf2.as<float2>();
+    v.alpha = h->alpha.as<double>();
     return v;
 }
 
@@ -642,6 +677,7 @@ int upload(DevBuf& d, const T* h, size_t n, cudaStream_t st) {
 int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk_pairs_s* h, cudaStream_t st) {
     const int S = shells->nshell;
     CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
     int rc;
     if ((rc = ensure_boys(h->device, st))) return rc;
     // ---- host-side validation and basis offsets
@@ -714,9 +750,10 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = h->pp2.alloc(sizeof(double2) * nprimpair))) return rc;
     if ((rc = h->ppf.alloc(sizeof(float4) * nprimpair))) return rc;
     if ((rc = h->ppf2.alloc(sizeof(float2) * nprimpair))) return rc;
+    if ((rc = h->alpha.alloc(sizeof(double) * nprimpair))) return rc;
     k_pair_fill<<<nblk(np, 128), 128, 0, st>>>(SD, np, d_poff.as<long long>(), u_info.as<int4>(), u_A.as<double4>(),
                                                 u_B.as<double4>(), u_atoms.as<int2>(), u_lab.as<int2>(),
-                                                h->pp.as<double4>(), h->pp2.as<double2>());
+                                                h->pp.as<double4>(), h->pp2.as<double2>(), h->alpha.as<double>());
     CKL();
     k_pp_to_f32<<<nblk(nprimpair, 256), 256, 0, st>>>(h->pp.as<double4>(), h->pp2.as<double2>(), nprimpair,
                                                        h->ppf.as<float4>(), h->ppf2.as<float2>());
@@ -899,16 +936,27 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     return 0;
 }
 
+// Grid of a persistent class launch: `qpt` quartets per thread (the Workload
+// Allocator's unit of work, Algorithm 2 "Combine" doubles it), at least one
+// wave of one block per SM, at most 64 blocks per SM.
+int grid_for(long long total, int block, int qpt, int nsm) {
+    long long g = (total + (long long)block * qpt - 1) / ((long long)block * qpt);
+    g = std::max<long long>(g, 1);
+    g = std::min<long long>(g, (long long)nsm * 64);
+    return (int)g;
+}
+
 int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
-                 long long total, const double* D, double* J, double* K, cudaStream_t st) {
-    if (total <= 0) return 0;
+                 long long total_hint, const double* D, double* J, double* K, cudaStream_t st,
+                 const gb::BatchMol* mols = nullptr, const int* row_mol = nullptr, int nrows_override = -1) {
+    if (total_hint <= 0) return 0;
     gb::JKArgs a;
+    std::memset(&a, 0, sizeof(a));
     a.pairs = view_of(h);
-    a.rows.nrows = cr.nrows;
+    a.rows.nrows = nrows_override >= 0 ? nrows_override : cr.nrows;
     a.rows.start = start;
     a.rows.bra = cr.bra.as<int>();
     a.rows.ket0 = ket0;
-    a.total = total;
     a.boys = g_boys[h->device].tab.as<double>();
     a.boysf = g_boys[h->device].tabf.as<float>();
     a.tsmall = (float)g_opt.tsmall;
@@ -916,7 +964,10 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.J = J;
     a.K = K;
     a.nbf = h->nbf;
-    if (total >= (1LL << 31) * 128LL) return fail(JK_ERR_UNSUPPORTED, "launch too large");
+    a.mols = mols;
+    a.row_mol = row_mol;
+    const TuneCfg& tc = cr.tune[prec];
+    const int grid = grid_for(total_hint, tc.block, tc.qpt, h->nsm);
     ProfRec* pr = nullptr;
     if (g_opt.profile) {
         h->prof.emplace_back();
@@ -926,21 +977,46 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
         pr->bra = cr.bra_cls;
         pr->ket = cr.ket_cls;
         pr->prec = prec;
-        pr->total = total;
+        pr->total = total_hint;
         CK(cudaEventRecord(pr->e0, st));
     }
-    const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec, a, st);
+    const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec, a, grid, tc.block, st);
     if (e) return fail(JK_ERR_CUDA, std::string("ERI kernel launch: ") + cudaGetErrorString((cudaError_t)e));
     h->launches += 1;
     if (pr) CK(cudaEventRecord(pr->e1, st));
     return 0;
 }
 
+// Mixed split of one class: FP64 rows (s64, ket0) and FP32 rows (s32, k32),
+// computed on the device; the split totals land in split_tot[0..1].
+int split_class(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* split_tot, cudaStream_t st) {
+    int rc;
+    const long long n1 = cr.nrows + 1;
+    if ((rc = cr.c64.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.c32.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.s64.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.s32.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
+    if ((rc = cr.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
+    k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                      cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
+                                                      cr.c64.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>());
+    CKL();
+    CK(cudaMemsetAsync(cr.c64.as<long long>() + cr.nrows, 0, 8, st));
+    CK(cudaMemsetAsync(cr.c32.as<long long>() + cr.nrows, 0, 8, st));
+    if ((rc = scan_into(cr.c64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 1, cr.scr.as<long long>(), st)))
+        return rc;
+    if ((rc = scan_into(cr.c32.as<long long>(), cr.s32.as<long long>(), n1, split_tot, cr.scr.as<long long>(), st)))
+        return rc;
+    h->launches += 1 + 2 * scan_launches(n1);
+    return 0;
+}
+
 int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_precision prec, cudaStream_t st) {
     const int n = h->nbf;
+    int rc;
+    if ((rc = h->scratch.alloc(64))) return rc;
     if (g_opt.check_sym) {
-        int rc;
-        if ((rc = h->scratch.alloc(64))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
         k_asym<<<152 * 4, 256, 0, st>>>(D, n, h->scratch.as<unsigned long long>());
         CKL();
@@ -959,58 +1035,400 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     }
     h->prof.clear();
     h->launches = 0;
-    int rc;
+    h->last_prec = prec;
     if (prec == JK_FP64) {
         for (const ClassRows& cr : h->rows)
             if ((rc = launch_class(h, cr, 0, cr.start.as<long long>(), cr.ket0.as<int>(), cr.total, D, J, K, st))) return rc;
-        h->last_n64 = h->nquartets;
-        h->last_n32 = 0;
     } else {
-        if ((rc = h->scratch.alloc(64))) return rc;
+        const int ncr = (int)h->rows.size();
+        if ((rc = h->split_tot.alloc(sizeof(long long) * 2 * std::max(1, ncr)))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
         k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>());
         CKL();
         h->launches += 1;
-        long long n32 = 0, n64 = 0;
-        for (ClassRows& cr : h->rows) {
+        for (int k = 0; k < ncr; ++k) {
+            ClassRows& cr = h->rows[k];
             if (cr.total <= 0) continue;
-            DevBuf c64, c32;
-            if ((rc = c64.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = c32.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = cr.s64.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = cr.s32.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
-            k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
-                                                              cr.nrows, h->A.as<double4>(),
-                                                              reinterpret_cast<const double*>(h->scratch.p), g_opt.tau,
-                                                              c64.as<long long>(), c32.as<long long>(), cr.k32.as<int>());
-            CKL();
-            h->launches += 1 + 2 * scan_launches(cr.nrows + 1);
-            CK(cudaMemsetAsync(c64.as<long long>() + cr.nrows, 0, 8, st));
-            CK(cudaMemsetAsync(c32.as<long long>() + cr.nrows, 0, 8, st));
-            if ((rc = scan_exclusive(c64.as<long long>(), cr.s64.as<long long>(), cr.nrows + 1,
-                                     h->scratch.as<long long>() + 2, st)))
+            if ((rc = split_class(h, cr, reinterpret_cast<const double*>(h->scratch.p),
+                                  h->split_tot.as<long long>() + 2 * k, st)))
                 return rc;
-            CK(cudaMemcpyAsync(&cr.total64, h->scratch.as<long long>() + 2, 8, cudaMemcpyDeviceToHost, st));
-            if ((rc = scan_exclusive(c32.as<long long>(), cr.s32.as<long long>(), cr.nrows + 1,
-                                     h->scratch.as<long long>() + 3, st)))
-                return rc;
-            CK(cudaMemcpyAsync(&cr.total32, h->scratch.as<long long>() + 3, 8, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            n64 += cr.total64;
-            n32 += cr.total32;
-            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.total64, D, J, K, st))) return rc;
-            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.total32, D, J, K, st))) return rc;
-            CK(cudaStreamSynchronize(st));  // c64/c32 temporaries
+            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.total, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.total, D, J, K, st))) return rc;
         }
-        h->last_n32 = n32;
-        h->last_n64 = n64;
     }
     const long long tri = (long long)n * (n + 1) / 2;
     k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
     k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(K, n);
     CKL();
     h->launches += 2;
+    return 0;
+}
+
+
+// ------------------------------------------------------------------ batched launches
+// Many molecules in one launch per (bra class, ket class): the rows of every
+// molecule are concatenated, each row carries its molecule index, and the
+// kernels read that molecule's pairs / D / J / K from a device table.  The
+// whole sequence (zeroing, optional mixed split, class launches on four
+// forked streams, symmetrisation) is captured once into a CUDA graph and
+// replayed while the molecule list, the matrices and the options are unchanged.
+struct BatchClass {
+    int X = 0, Y = 0, nrows = 0;
+    long long total = 0;
+    DevBuf start, bra, ket0, rowmol;
+    DevBuf s64, s32, k32, c64, c32, scr;
+    TuneCfg tune[2];
+};
+
+struct BatchPlan {
+    std::vector<jk_pairs> mols;
+    std::vector<const double*> D;
+    std::vector<double*> J, K;
+    int prec = 0, device = 0, max_n = 0, graph = 0;
+    double tau = 0.0, tsmall = 0.0;
+    long long nquartets = 0;
+    DevBuf bm, dmax, split_tot;
+    std::vector<BatchClass> cls;
+    cudaStream_t cs = nullptr, ps[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr}, done = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    ~BatchPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (auto& x : ps) if (x) cudaStreamDestroy(x);
+        if (cs) cudaStreamDestroy(cs);
+        if (fork) cudaEventDestroy(fork);
+        for (auto& e : join) if (e) cudaEventDestroy(e);
+        if (done) cudaEventDestroy(done);
+    }
+};
+std::mutex g_batch_mu;
+std::unique_ptr<BatchPlan> g_plan;
+
+__global__ void k_offset_copy(const long long* src, int n, long long off, long long* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] + off;
+}
+__global__ void k_fill_int(int* dst, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = v;
+}
+__global__ void k_set_ll(long long* dst, long long v) { *dst = v; }
+
+__global__ void k_zero_batched(const gb::BatchMol* bm) {
+    const gb::BatchMol& m = bm[blockIdx.y];
+    const long long n2 = (long long)m.nbf * m.nbf;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        m.J[i] = 0.0;
+        m.K[i] = 0.0;
+    }
+}
+
+__global__ void k_sym_batched(const gb::BatchMol* bm) {
+    const gb::BatchMol& m = bm[blockIdx.y];
+    const int n = m.nbf;
+    const long long tri = (long long)n * (n + 1) / 2;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tri; t += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        decode_pair(t, i, j);
+        const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
+        if (i == j) { m.J[a] *= 2.0; m.K[a] *= 2.0; continue; }
+        const double vj = m.J[a] + m.J[b], vk = m.K[a] + m.K[b];
+        m.J[a] = vj; m.J[b] = vj; m.K[a] = vk; m.K[b] = vk;
+    }
+}
+
+__global__ void k_absmax_batched(const gb::BatchMol* bm, unsigned long long* out) {
+    const gb::BatchMol& m = bm[blockIdx.y];
+    const long long n2 = (long long)m.nbf * m.nbf;
+    double v = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+        v = fmax(v, fabs(m.D[i]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_rows_split_batched(const long long* start, const int* rbra, const int* rket0, const int* rowmol,
+                                     int nrows, const gb::BatchMol* bm, const unsigned long long* dmax, double tau,
+                                     long long* c64, long long* c32, int* k32) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int m = rowmol[r];
+    const double4* A = bm[m].pairs.A;
+    const long long c = start[r + 1] - start[r];
+    const int s = rket0[r];
+    const double qi = A[rbra[r]].w * __longlong_as_double((long long)dmax[m]);
+    int lo = s, hi = s + (int)c;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (qi * A[mid].w >= tau) lo = mid + 1; else hi = mid;
+    }
+    c64[r] = lo - s;
+    c32[r] = c - (lo - s);
+    k32[r] = lo;
+}
+
+int build_plan(BatchPlan& P, cudaStream_t st) {
+    const int nmol = (int)P.mols.size();
+    int rc;
+    std::vector<gb::BatchMol> host(nmol);
+    P.max_n = 0;
+    P.nquartets = 0;
+    for (int m = 0; m < nmol; ++m) {
+        jk_pairs_s* h = P.mols[m];
+        if (h->device != P.device) return fail(JK_ERR_INVALID, "batched molecules on different devices");
+        host[m].pairs = view_of(h);
+        host[m].D = P.D[m];
+        host[m].J = P.J[m];
+        host[m].K = P.K[m];
+        host[m].nbf = h->nbf;
+        P.max_n = std::max(P.max_n, h->nbf);
+        P.nquartets += h->nquartets;
+    }
+    if ((rc = upload(P.bm, host.data(), nmol, st))) return rc;
+    if ((rc = P.dmax.alloc(sizeof(unsigned long long) * nmol))) return rc;
+    const int ncls = gb_num_pair_classes();
+    P.cls.clear();
+    P.cls.reserve(ncls * (ncls + 1) / 2);
+    for (int X = 0; X < ncls; ++X)
+        for (int Y = 0; Y <= X; ++Y) {
+            int nrows = 0;
+            long long total = 0;
+            const ClassRows* first = nullptr;
+            for (int m = 0; m < nmol; ++m)
+                for (const ClassRows& cr : P.mols[m]->rows)
+                    if (cr.bra_cls == X && cr.ket_cls == Y && cr.total > 0) {
+                        nrows += cr.nrows;
+                        total += cr.total;
+                        if (!first) first = &cr;
+                    }
+            if (total == 0) continue;
+            P.cls.emplace_back();
+            BatchClass& bc = P.cls.back();
+            bc.X = X; bc.Y = Y; bc.nrows = nrows; bc.total = total;
+            bc.tune[0] = first->tune[0];
+            bc.tune[1] = first->tune[1];
+            if ((rc = bc.start.alloc(sizeof(long long) * (nrows + 1)))) return rc;
+            if ((rc = bc.bra.alloc(sizeof(int) * nrows))) return rc;
+            if ((rc = bc.ket0.alloc(sizeof(int) * nrows))) return rc;
+            if ((rc = bc.rowmol.alloc(sizeof(int) * nrows))) return rc;
+            int roff = 0;
+            long long qoff = 0;
+            for (int m = 0; m < nmol; ++m)
+                for (const ClassRows& cr : P.mols[m]->rows)
+                    if (cr.bra_cls == X && cr.ket_cls == Y && cr.total > 0) {
+                        CK(cudaMemcpyAsync(bc.bra.as<int>() + roff, cr.bra.p, sizeof(int) * cr.nrows,
+                                           cudaMemcpyDeviceToDevice, st));
+                        CK(cudaMemcpyAsync(bc.ket0.as<int>() + roff, cr.ket0.p, sizeof(int) * cr.nrows,
+                                           cudaMemcpyDeviceToDevice, st));
+                        k_offset_copy<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.nrows, qoff,
+                                                                            bc.start.as<long long>() + roff);
+                        k_fill_int<<<nblk(cr.nrows, 256), 256, 0, st>>>(bc.rowmol.as<int>() + roff, cr.nrows, m);
+                        CKL();
+                        roff += cr.nrows;
+                        qoff += cr.total;
+                    }
+            k_set_ll<<<1, 1, 0, st>>>(bc.start.as<long long>() + nrows, total);
+            CKL();
+            if (P.prec == JK_MIXED) {
+                const long long n1 = nrows + 1;
+                if ((rc = bc.c64.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.c32.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.s64.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.s32.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.k32.alloc(sizeof(int) * nrows))) return rc;
+                if ((rc = bc.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
+            }
+        }
+    if ((rc = P.split_tot.alloc(sizeof(long long) * 2 * std::max<size_t>(1, P.cls.size())))) return rc;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaStreamCreateWithFlags(&P.cs, cudaStreamNonBlocking));
+    for (auto& x : P.ps) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+    for (auto& e : P.join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
+    return 0;
+}
+
+int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* start, const int* ket0,
+                       cudaStream_t s) {
+    gb::JKArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pairs = view_of(P.mols[0]);
+    a.rows.nrows = bc.nrows;
+    a.rows.start = start;
+    a.rows.bra = bc.bra.as<int>();
+    a.rows.ket0 = ket0;
+    a.boys = g_boys[P.device].tab.as<double>();
+    a.boysf = g_boys[P.device].tabf.as<float>();
+    a.tsmall = (float)P.tsmall;
+    a.mols = P.bm.as<gb::BatchMol>();
+    a.row_mol = bc.rowmol.as<int>();
+    const TuneCfg& tc = bc.tune[prec];
+    int nsm = P.mols[0]->nsm;
+    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(bc.total, tc.block, tc.qpt, nsm), tc.block, s);
+    if (e) return fail(JK_ERR_CUDA, std::string("batched ERI launch: ") + cudaGetErrorString((cudaError_t)e));
+    P.launches += 1;
+    return 0;
+}
+
+// The launch sequence of one batched build, on stream cs (forking to ps[]).
+int enqueue_batch(BatchPlan& P) {
+    const int nmol = (int)P.mols.size();
+    int rc;
+    P.launches = 0;
+    const gb::BatchMol* bm = P.bm.as<gb::BatchMol>();
+    const long long n2max = (long long)P.max_n * P.max_n;
+    k_zero_batched<<<dim3(nblk(n2max, 256), nmol), 256, 0, P.cs>>>(bm);
+    CKL();
+    P.launches += 1;
+    if (P.prec == JK_MIXED) {
+        CK(cudaMemsetAsync(P.dmax.p, 0, sizeof(unsigned long long) * nmol, P.cs));
+        k_absmax_batched<<<dim3(64, nmol), 256, 0, P.cs>>>(bm, P.dmax.as<unsigned long long>());
+        CKL();
+        P.launches += 1;
+    }
+    CK(cudaEventRecord(P.fork, P.cs));
+    for (auto& x : P.ps) CK(cudaStreamWaitEvent(x, P.fork, 0));
+    for (size_t k = 0; k < P.cls.size(); ++k) {
+        BatchClass& bc = P.cls[k];
+        cudaStream_t s = (k % 4 == 0) ? P.cs : P.ps[k % 4 - 1];
+        if (P.prec == JK_FP64) {
+            if ((rc = launch_batch_class(P, bc, 0, bc.start.as<long long>(), bc.ket0.as<int>(), s))) return rc;
+        } else {
+            const long long n1 = bc.nrows + 1;
+            k_rows_split_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(
+                bc.start.as<long long>(), bc.bra.as<int>(), bc.ket0.as<int>(), bc.rowmol.as<int>(), bc.nrows, bm,
+                P.dmax.as<unsigned long long>(), P.tau, bc.c64.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>());
+            CKL();
+            CK(cudaMemsetAsync(bc.c64.as<long long>() + bc.nrows, 0, 8, s));
+            CK(cudaMemsetAsync(bc.c32.as<long long>() + bc.nrows, 0, 8, s));
+            long long* tot = P.split_tot.as<long long>() + 2 * k;
+            if ((rc = scan_into(bc.c64.as<long long>(), bc.s64.as<long long>(), n1, tot + 1, bc.scr.as<long long>(), s)))
+                return rc;
+            if ((rc = scan_into(bc.c32.as<long long>(), bc.s32.as<long long>(), n1, tot, bc.scr.as<long long>(), s)))
+                return rc;
+            P.launches += 1 + 2 * scan_launches(n1);
+            if ((rc = launch_batch_class(P, bc, 0, bc.s64.as<long long>(), bc.ket0.as<int>(), s))) return rc;
+            if ((rc = launch_batch_class(P, bc, 1, bc.s32.as<long long>(), bc.k32.as<int>(), s))) return rc;
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        CK(cudaEventRecord(P.join[i], P.ps[i]));
+        CK(cudaStreamWaitEvent(P.cs, P.join[i], 0));
+    }
+    const long long trimax = (long long)P.max_n * (P.max_n + 1) / 2;
+    k_sym_batched<<<dim3(nblk(trimax, 256), nmol), 256, 0, P.cs>>>(bm);
+    CKL();
+    P.launches += 1;
+    return 0;
+}
+
+int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J, double* const* K,
+                 jk_precision prec, cudaStream_t st, long long* launches) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
+                g_plan->tau == g_opt.tau && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph;
+    for (int m = 0; same && m < nmol; ++m)
+        same = g_plan->mols[m] == pairs[m] && g_plan->D[m] == D[m] && g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
+    int rc;
+    if (!same) {
+        g_plan.reset(new BatchPlan());
+        BatchPlan& P = *g_plan;
+        P.mols.assign(pairs, pairs + nmol);
+        P.D.assign(D, D + nmol);
+        P.J.assign(J, J + nmol);
+        P.K.assign(K, K + nmol);
+        P.prec = prec;
+        P.device = dev;
+        P.tau = g_opt.tau;
+        P.tsmall = g_opt.tsmall;
+        P.graph = g_opt.graph;
+        if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
+        if (P.graph) {
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(P.cs, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_batch(P);
+            const cudaError_t ce = cudaStreamEndCapture(P.cs, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); g_plan.reset(); return rc; }
+            if (ce != cudaSuccess) { g_plan.reset(); return fail(JK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); }
+            const cudaError_t ie = cudaGraphInstantiate(&P.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) { g_plan.reset(); return fail(JK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+        }
+    }
+    BatchPlan& P = *g_plan;
+    // order the batch after the caller's prior work on st, and st after the batch
+    CK(cudaEventRecord(P.done, st));
+    CK(cudaStreamWaitEvent(P.cs, P.done, 0));
+    if (P.graph) {
+        CK(cudaGraphLaunch(P.exec, P.cs));
+    } else {
+        if ((rc = enqueue_batch(P))) return rc;
+    }
+    CK(cudaEventRecord(P.done, P.cs));
+    CK(cudaStreamWaitEvent(st, P.done, 0));
+    if (launches) *launches = P.launches;
+    return 0;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Algorithm 2 of the paper (Workload Allocator): start every class at one
+// quartet per thread, then repeatedly try "Combine" (double the quartets per
+// thread, i.e. halve the grid) and keep it only if the class got faster; stop
+// when no class improves.  Timed on a prefix of each class's rows (about an
+// eighth, at least 2^21 quartets) with CUDA events; J and K are scratch.
+int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Item { ClassRows* cr; int nrows; long long total; };
+    std::vector<Item> items;
+    for (ClassRows& cr : h->rows) {
+        if (cr.total <= 0) continue;
+        std::vector<long long> start(cr.nrows + 1);
+        CK(cudaMemcpy(start.data(), cr.start.p, sizeof(long long) * (cr.nrows + 1), cudaMemcpyDeviceToHost));
+        const long long target = std::max<long long>(cr.total / 8, 1LL << 21);
+        int r = (int)(std::lower_bound(start.begin(), start.end(), target) - start.begin());
+        r = std::min(std::max(r, 1), cr.nrows);
+        items.push_back({&cr, r, start[r]});
+        cr.tune[prec] = TuneCfg();
+    }
+    auto time_one = [&](const Item& it, float* ms) -> int {
+        int rc;
+        for (int rep = 0; rep < 2; ++rep) {  // first run warms caches and clocks
+            CK(cudaEventRecord(e0, st));
+            if ((rc = launch_class(h, *it.cr, prec, it.cr->start.as<long long>(), it.cr->ket0.as<int>(), it.total, D,
+                                   J, K, st, nullptr, nullptr, it.nrows)))
+                return rc;
+            CK(cudaEventRecord(e1, st));
+        }
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        return 0;
+    };
+    bool improved = true;
+    int rounds = 0;
+    while (improved && rounds < 8) {
+        improved = false;
+        ++rounds;
+        for (Item& it : items) {
+            TuneCfg& tc = it.cr->tune[prec];
+            if (grid_for(it.total, tc.block, tc.qpt * 2, h->nsm) < h->nsm) continue;  // keep one wave
+            float t1 = 0.f, t2 = 0.f;
+            int rc;
+            if ((rc = time_one(it, &t1))) return rc;
+            tc.qpt *= 2;  // Combine
+            if ((rc = time_one(it, &t2))) return rc;
+            if (t2 < t1) improved = true;
+            else tc.qpt /= 2;  // Revert
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tuned[prec] = 1;
     return 0;
 }
 
@@ -1119,19 +1537,49 @@ int jk_energy(int nbf, const double* D, const double* J, const double* K, double
 }
 
 int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* cuda_stream) {
-    (void)h; (void)D; (void)dEdR; (void)prec; (void)cuda_stream;
-    return fail(JK_ERR_UNSUPPORTED, "jk_grad: not built yet");
+    g_err.clear();
+    if (!h || !D || !dEdR) return fail(JK_ERR_INVALID, "null argument");
+    if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // both precisions run the FP64 derivative kernels
+    CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * h->natom, st));
+    h->launches = 0;
+    for (const ClassRows& cr : h->rows) {
+        if (cr.total <= 0) continue;
+        gb::GradArgs a;
+        a.pairs = view_of(h);
+        a.rows.nrows = cr.nrows;
+        a.rows.start = cr.start.as<long long>();
+        a.rows.bra = cr.bra.as<int>();
+        a.rows.ket0 = cr.ket0.as<int>();
+        a.total = cr.total;
+        a.boys = g_boys[h->device].tab.as<double>();
+        a.D = D;
+        a.nbf = h->nbf;
+        a.atoms = h->pair_atoms.as<int2>();
+        a.grad = dEdR;
+        const int e = gb_launch_grad(cr.bra_cls, cr.ket_cls, a, st);
+        if (e) return fail(JK_ERR_CUDA, std::string("gradient kernel launch: ") + cudaGetErrorString((cudaError_t)e));
+        h->launches += 1;
+    }
+    return JK_OK;
 }
 
 int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J, double* const* K,
                      jk_precision prec, void* cuda_stream) {
     g_err.clear();
     if (nmol < 0 || (nmol > 0 && (!pairs || !D || !J || !K))) return fail(JK_ERR_INVALID, "bad argument");
-    for (int i = 0; i < nmol; ++i) {
-        const int rc = jk_build(pairs[i], D[i], J[i], K[i], prec, cuda_stream);
-        if (rc) return rc;
-    }
-    return JK_OK;
+    if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    if (nmol == 0) return JK_OK;
+    for (int i = 0; i < nmol; ++i)
+        if (!pairs[i] || !D[i] || !J[i] || !K[i]) return fail(JK_ERR_INVALID, "null molecule entry");
+    long long launches = 0;
+    const int rc = batched_impl(nmol, pairs, D, J, K, prec, static_cast<cudaStream_t>(cuda_stream), &launches);
+    if (!rc) pairs[0]->launches = launches;
+    return rc;
 }
 
 int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* cuda_stream) {
@@ -1186,8 +1634,59 @@ int jk_get_option(jk_option opt, double* v) {
 
 int jk_last_split(jk_pairs h, int64_t* n32, int64_t* n64) {
     if (!h) return fail(JK_ERR_INVALID, "null handle");
-    if (n32) *n32 = h->last_n32;
-    if (n64) *n64 = h->last_n64;
+    long long a = 0, b = h->nquartets;
+    if (h->last_prec == JK_MIXED && h->split_tot.p) {
+        std::vector<long long> t(2 * h->rows.size());
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(t.data(), h->split_tot.p, sizeof(long long) * t.size(), cudaMemcpyDeviceToHost));
+        a = b = 0;
+        for (size_t k = 0; k < h->rows.size(); ++k) {
+            if (h->rows[k].total <= 0) continue;
+            a += t[2 * k];
+            b += t[2 * k + 1];
+        }
+    }
+    if (n32) *n32 = a;
+    if (n64) *n64 = b;
+    return JK_OK;
+}
+
+int jk_autotune(jk_pairs h, const double* D, double* J, double* K, jk_precision prec, void* cuda_stream) {
+    g_err.clear();
+    if (!h || !D || !J || !K) return fail(JK_ERR_INVALID, "null argument");
+    if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    return autotune_impl(h, D, J, K, prec == JK_FP64 ? 0 : 1, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int jk_tuning(jk_pairs h, int max_rows, int* rows, int* nrows) {
+    if (!h || !nrows || (max_rows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    int k = 0;
+    for (const ClassRows& cr : h->rows) {
+        if (cr.total <= 0) continue;
+        if (k < max_rows) {
+            int* r = rows + 6 * k;
+            r[0] = cr.bra_cls; r[1] = cr.ket_cls;
+            r[2] = cr.tune[0].block; r[3] = cr.tune[0].qpt; r[4] = cr.tune[1].block; r[5] = cr.tune[1].qpt;
+        }
+        ++k;
+    }
+    *nrows = k;
+    return JK_OK;
+}
+
+int jk_set_tuning(jk_pairs h, int nrows, const int* rows) {
+    if (!h || nrows < 0 || (nrows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    for (int k = 0; k < nrows; ++k) {
+        const int* r = rows + 6 * k;
+        if (r[2] < 32 || r[2] > 128 || r[2] % 32 || r[4] < 32 || r[4] > 128 || r[4] % 32 || r[3] < 1 || r[5] < 1 ||
+            r[3] > (1 << 20) || r[5] > (1 << 20))
+            return fail(JK_ERR_INVALID, "tuning entry out of range");
+        for (ClassRows& cr : h->rows)
+            if (cr.bra_cls == r[0] && cr.ket_cls == r[1]) {
+                cr.tune[0].block = r[2]; cr.tune[0].qpt = r[3];
+                cr.tune[1].block = r[4]; cr.tune[1].qpt = r[5];
+            }
+    }
     return JK_OK;
 }
 

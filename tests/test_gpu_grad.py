@@ -1,0 +1,74 @@
+"""GPU parity of the nuclear-gradient adjoint kernel: against the oracle's
+analytic FP64 gradient (small molecules, every class up to d), central finite
+differences of the GPU energy (24-atom workload, h = 1e-4 bohr), and the
+torch.autograd.Function wrapper."""
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_13203_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(1, [0, 1], 3, 2), (2, [2, 0], 3, 3), (3, [1, 2], 2, 3),
+                                                    (4, [0, 1, 2], 3, 2)])
+def test_gradient_matches_oracle(g, seed, shells, natom, kmax):
+    mol = molgen.random_molecule(300 + seed, natom, shells, 1, kmax, 0.1, 50.0, layout="lattice", spacing=1.8)
+    D = molgen.density(mol, 400 + seed)
+    pairs = g.ShellPairs(mol)
+    gg = g.jk_grad(pairs, torch.from_numpy(D).cuda(), "fp64").cpu().numpy()
+    go = oracle.grad(mol, D, mode="unique")
+    scale = max(1.0, np.abs(go).max())
+    assert np.abs(gg - go).max() <= 1e-10 * scale, (gg, go)
+    assert np.abs(gg.sum(axis=0)).max() <= 1e-10 * scale
+
+
+def test_gradient_fd_24_atoms(g):
+    mol, D = molgen.config(3)
+    thresh = molgen.CONFIG_THRESH[3]
+    Dt = torch.from_numpy(D).cuda()
+    pairs = g.ShellPairs(mol, thresh)
+    grad = g.jk_grad(pairs, Dt, "fp64").cpu().numpy()
+    pairs.free()
+    assert grad.shape == (24, 3)
+    assert np.abs(grad.sum(axis=0)).max() <= 1e-8 * np.abs(grad).max()
+    h = 1e-4
+
+    def energy(xyz):
+        p = g.ShellPairs(mol.with_xyz(xyz), thresh)
+        J, K = g.jk_build(p, Dt, "fp64")
+        e = g.jk_energy(Dt, J, K)
+        p.free()
+        return e
+    for a, x in [(0, 0), (13, 2)]:
+        xp, xm = mol.xyz.copy(), mol.xyz.copy()
+        xp[a, x] += h
+        xm[a, x] -= h
+        fd = (energy(xp) - energy(xm)) / (2 * h)
+        assert abs(fd - grad[a, x]) <= 1e-5 * max(1.0, abs(grad[a, x])), (a, x, fd, grad[a, x])
+
+
+def test_autograd_function(g):
+    mol = molgen.random_molecule(77, 3, [0, 1, 2], 1, 2, 0.2, 20.0, layout="lattice", spacing=2.0)
+    D = molgen.density(mol, 78)
+    xyz = torch.tensor(mol.xyz, dtype=torch.float64, device="cuda", requires_grad=True)
+    Dt = torch.tensor(D, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = g.jk_energy_fn(xyz, Dt, mol)
+    E.backward()
+    go = oracle.grad(mol, D, mode="unique")
+    assert np.abs(xyz.grad.cpu().numpy() - go).max() <= 1e-10 * max(1.0, np.abs(go).max())
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    e = float(E.detach())
+    assert abs(e - oracle.energy(D, Jo, Ko)) <= 1e-10 * max(1.0, abs(e))
+    assert np.abs(Dt.grad.cpu().numpy() - (Jo - 0.5 * Ko)).max() <= 1e-10 * max(1.0, np.abs(Jo).max())
