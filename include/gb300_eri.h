@@ -126,6 +126,23 @@ int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, do
 int jk_energy(int nbf, const double* D, const double* J, const double* K, double* E,
               void* cuda_stream);
 
+/* jk_energy without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- hosts
+ * that own all device memory through their own fixed-budget pool and forbid
+ * libraries from allocating, or latency-critical loops where an allocation's
+ * implicit device synchronisation is not acceptable.  The reduction's partial
+ * sums live in a fixed file-scope device array of 16383 + 1 double2
+ * (256 KiB), held by every GPU that loads the library until the process
+ * exits.  nbf > 16383 is rejected with JK_ERR_INVALID (use jk_energy).
+ * The first call on a device looks up that array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU (different streams, no ordering) race on it
+ * and must be serialised by the caller.  Arguments and result as jk_energy
+ * (synchronous; *E is host memory). */
+int jk_energy_noalloc(int nbf, const double* D, const double* J, const double* K, double* E,
+                      void* cuda_stream);
+
 /* Diagnostic: the device Boys evaluator used by the FP64 kernels (tabulated
  * Taylor grid + downward recursion, Sec. 2.2 "[00|00] analytically").
  * For each of n arguments T[i] (device, float64, T >= 0) writes

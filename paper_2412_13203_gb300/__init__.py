@@ -40,6 +40,7 @@ class _Shells(C.Structure):
 
 
 EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_build_batched", "jk_energy", "jk_boys",
+           "jk_energy_noalloc",
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
            "jk_set_tuning"]
@@ -61,6 +62,7 @@ def load():
         lib.jk_grad.argtypes = [vp, vp, vp, C.c_int, vp]
         lib.jk_build_batched.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_int, vp]
         lib.jk_energy.argtypes = [C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp]
+        lib.jk_energy_noalloc.argtypes = [C.c_int, vp, vp, vp, C.POINTER(C.c_double), vp]
         lib.jk_boys.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, vp]
         lib.jk_set_option.argtypes = [C.c_int, C.c_double]
         lib.jk_get_option.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -155,6 +157,18 @@ def jk_energy(D, J, K, stream=None) -> float:
     """E = tr(DJ)/2 - tr(DK)/4 (compensated device reduction)."""
     E = C.c_double()
     _check(load().jk_energy(int(D.shape[0]), _dev_ptr(D), _dev_ptr(J), _dev_ptr(K), C.byref(E), _stream_ptr(stream)))
+    return E.value
+
+
+def jk_energy_noalloc(D, J, K, stream=None) -> float:
+    """Same value as jk_energy, computed without any device allocation (a fixed
+    library-owned scratch array; nbf <= 16383).  For callers whose device
+    memory is entirely owned by their own allocator, or that cannot afford
+    cudaMalloc's synchronisation; concurrent calls on different streams race
+    on the shared scratch and must be serialised."""
+    E = C.c_double()
+    _check(load().jk_energy_noalloc(int(D.shape[0]), _dev_ptr(D), _dev_ptr(J), _dev_ptr(K), C.byref(E),
+                                    _stream_ptr(stream)))
     return E.value
 
 

@@ -630,6 +630,85 @@ __global__ void k_energy_final(const double2* part, int nb, double* E) {
 
 unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ------------------------------------------------------------------ allocation-free energy
+// Scratch of jk_energy_noalloc: one compensated partial (sum, error) per row of
+// D plus one slot for the result.  It is a fixed file-scope array, so every
+// GPU that loads this library holds these 256 KiB until the process exits,
+// and every call shares (and overwrites) it.
+constexpr int kNoAllocMaxRows = 16383;
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocMaxRows + 1];
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// Row partials: one warp per row of D, compensated (two-sum) accumulation of
+// D J / 2 - D K / 4 including the rounding residuals of the products.
+__global__ void k_energy_rows(const double* D, const double* J, const double* K, int n, double2* part) {
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;  // whole warps leave together
+    double s = 0.0, c = 0.0;
+    const size_t base = (size_t)row * n;
+    for (int j = lane; j < n; j += 32) {
+        const double d = D[base + j], a = 0.5 * d * J[base + j], b = -0.25 * d * K[base + j];
+        double t, e;
+        two_sum(s, a, t, e);
+        s = t; c += e;
+        two_sum(s, b, t, e);
+        s = t; c += e;
+        c += fma(0.5 * d, J[base + j], -a) + fma(-0.25 * d, K[base + j], -b);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        double t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c += c2 + e;
+    }
+    if (lane == 0) part[row] = make_double2(s, c);
+}
+
+// Sum of the row partials (single block), result in out[0].x.
+__global__ void k_energy_rows_final(const double2* part, int n, double2* out) {
+    __shared__ double ss[256], sc[256];
+    double s = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double t, e;
+        two_sum(s, part[i].x, t, e);
+        s = t;
+        c += e + part[i].y;
+    }
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < (unsigned)o) {
+            double t, e;
+            two_sum(ss[threadIdx.x], ss[threadIdx.x + o], t, e);
+            ss[threadIdx.x] = t;
+            sc[threadIdx.x] += sc[threadIdx.x + o] + e;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = make_double2(ss[0] + sc[0], 0.0);
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the array's name is only a host-side stand-in in host code).
+int noalloc_scratch(double2** out) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(JK_ERR_INVALID, "device index");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(JK_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<double2*>(g_noalloc_ptr[dev]);
+    return 0;
+}
 
 int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
 
@@ -1532,6 +1611,26 @@ int jk_energy(int nbf, const double* D, const double* J, const double* K, double
     k_energy_final<<<1, 32, 0, st>>>(part.as<double2>(), nb, out.as<double>());
     CKL();
     CK(cudaMemcpyAsync(E, out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return JK_OK;
+}
+
+int jk_energy_noalloc(int nbf, const double* D, const double* J, const double* K, double* E, void* cuda_stream) {
+    g_err.clear();
+    if (nbf <= 0 || !D || !J || !K || !E) return fail(JK_ERR_INVALID, "bad argument");
+    if (nbf > kNoAllocMaxRows)
+        return fail(JK_ERR_INVALID, "jk_energy_noalloc: nbf = " + std::to_string(nbf) + " exceeds the fixed scratch (" +
+                                        std::to_string(kNoAllocMaxRows) + " rows); use jk_energy");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double2* scratch = nullptr;
+    int rc;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    const int rows_per_block = 8;  // 256 threads = 8 warps = 8 rows
+    k_energy_rows<<<nblk(nbf, rows_per_block), 256, 0, st>>>(D, J, K, nbf, scratch);
+    CKL();
+    k_energy_rows_final<<<1, 256, 0, st>>>(scratch, nbf, scratch + kNoAllocMaxRows);
+    CKL();
+    CK(cudaMemcpyAsync(E, scratch + kNoAllocMaxRows, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return JK_OK;
 }
