@@ -214,14 +214,24 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    g.set_option("profile", 1)
-    ms64, prof64, l64 = timed_steps("fp64", args.steps, args.warmup, profile=True)
-    g.set_option("profile", 0)
-    E64 = g.jk_energy(Dt, J, K)
+    # the headline: the mixed build (W warm-up + K timed steps)
     ms_mx, _, lmx = timed_steps("mixed", args.steps, args.warmup)
     E_mx = g.jk_energy(Dt, J, K)
+    J_mx, K_mx = J.clone(), K.clone()
     n32, n64 = g.last_split(pairs)
     clk = clocks.stop()
+    # per-kernel event timings and per-precision work of one more mixed build
+    g.set_option("profile", 1)
+    _, prof_mx, _ = timed_steps("mixed", 1, 0, profile=True)
+    g.set_option("profile", 0)
+    split = {s["cls"]: s for s in g.split_stats(pairs)}
+    # the plain FP64 form beside it (fewer steps: it is ~3x slower)
+    g.set_option("profile", 1)
+    ms64, prof64, l64 = timed_steps("fp64", min(args.steps, 2), 1, profile=True)
+    g.set_option("profile", 0)
+    E64 = g.jk_energy(Dt, J, K)
+    dJ = float((J_mx - J).abs().max())
+    dK = float((K_mx - K).abs().max())
 
     # end to end through the public API: pinned host D -> device, build, J and K back to pinned host
     Dh = torch.from_numpy(D).pin_memory()
@@ -229,7 +239,7 @@ def main():
     Kh = torch.empty(Dh.shape, dtype=torch.float64).pin_memory()
     Dd = torch.empty_like(Dt)
     e2e = []
-    for k in range(args.warmup + args.steps):
+    for k in range(1 + args.steps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -239,7 +249,7 @@ def main():
         Kh.copy_(K, non_blocking=True)
         e1.record(stream)
         e1.synchronize()
-        if k >= args.warmup:
+        if k >= 1:
             e2e.append(e0.elapsed_time(e1))
 
     nq = pairs.nquartets
@@ -252,13 +262,19 @@ def main():
         dist.all_reduce(vals, op=dist.ReduceOp.MAX)
     t_mx, t_64, t_e2e = [float(x) for x in vals.cpu()]
 
-    # roofline of the dominant kernel (FP64 build): algorithmic FP64 operations
-    # of the generated code / event-timed launch duration, against the measured DFMA peak
+    # roofline of the dominant kernel of the mixed build: algorithmic operations
+    # of the generated code for the quartets that launch processed / its
+    # event-timed duration, against the measured FMA peak of its precision
     stats = {s["cls"]: s for s in g.class_stats(pairs)}
-    per = {k[0]: float(np.mean(v)) for k, v in prof64.items() if k[1] == "fp64"}
-    dom = max(per, key=per.get)
-    achieved = stats[dom]["flops"] / (per[dom] * 1e-3)
+    per_mx = {k: float(np.mean(v)) for k, v in prof_mx.items()}
+    dom_cls, dom_prec = max(per_mx, key=per_mx.get)
+    dom_flops = split[dom_cls]["fp32" if dom_prec == "fp32" else "fp64"]["flops"]
+    dom_peak = peak32 if dom_prec == "fp32" else peak64
+    achieved = dom_flops / (per_mx[(dom_cls, dom_prec)] * 1e-3)
     tot_flops = sum(s["flops"] for s in stats.values())
+    per = {k[0]: float(np.mean(v)) for k, v in prof64.items() if k[1] == "fp64"}
+    dom64 = max(per, key=per.get)
+    ach64 = stats[dom64]["flops"] / (per[dom64] * 1e-3)
 
     out = None
     if rank == 0:
@@ -277,16 +293,23 @@ def main():
                        "mixed_tsmall": g.get_option("mixed_tsmall"), "mixed_fp32_quartets": n32,
                        "mixed_fp64_quartets": n64},
             "fp64": {"value": nq * world / (t_64 * 1e-3), "unit": "quartets/s", "ms_per_step": t_64,
-                     "energy_Eh": E64, "flops_per_s": tot_flops / (t_64 * 1e-3)},
-            "mixed": {"ms_per_step": t_mx, "energy_Eh": E_mx, "energy_minus_fp64_Eh": E_mx - E64},
+                     "steps": min(args.steps, 2), "energy_Eh": E64, "flops_per_s": tot_flops / (t_64 * 1e-3),
+                     "roofline": {"bound": "alu", "kernel": f"eri_jk_{dom64} fp64", "achieved": ach64 / 1e12,
+                                  "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": ach64 / peak64}},
+            "mixed": {"ms_per_step": t_mx, "energy_Eh": E_mx, "energy_minus_fp64_Eh": E_mx - E64,
+                      "max_abs_dJ_vs_fp64": dJ, "max_abs_dK_vs_fp64": dK,
+                      "fp32_share_of_flops": sum(v["fp32"]["flops"] for v in split.values()) / tot_flops},
             "e2e": {"value": nq * world / (t_e2e * 1e-3), "unit": "quartets/s", "ms_per_step": t_e2e,
                     "h2d_bytes_per_step": int(Dh.numel() * 8), "d2h_bytes_per_step": int(2 * Jh.numel() * 8)},
-            "roofline": {"bound": "alu", "kernel": f"eri_jk_{dom} fp64", "achieved": achieved / 1e12,
-                         "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": achieved / peak64, "traffic": None,
-                         "peak_source": "measured DFMA microbenchmark (jk_fma_peak) on this GPU",
-                         "fp32_peak_tflops": peak32 / 1e12},
+            "roofline": {"bound": "alu", "kernel": f"eri_jk_{dom_cls} {dom_prec}", "achieved": achieved / 1e12,
+                         "peak": dom_peak / 1e12, "unit": "TFLOP/s", "frac": achieved / dom_peak, "traffic": None,
+                         "peak_source": f"measured {'FFMA' if dom_prec == 'fp32' else 'DFMA'} microbenchmark "
+                                        "(jk_fma_peak) on this GPU",
+                         "fp32_peak_tflops": peak32 / 1e12, "fp64_peak_tflops": peak64 / 1e12},
+            "class_ms_mixed": {f"{k[0]} {k[1]}": round(v, 3)
+                               for k, v in sorted(per_mx.items(), key=lambda x: -x[1])[:12]},
             "class_ms_fp64": {k: round(v, 3) for k, v in sorted(per.items(), key=lambda x: -x[1])},
-            "gpu_launches": int((l64 + lmx) / 1),
+            "gpu_launches": int(lmx),
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -102,17 +102,21 @@ int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartet
 
 /* J and K for one density (device pointers, nbf x nbf float64).
  * JK_FP64: every primitive quartet in FP64.  JK_MIXED: shell quartets whose
- * bound Q_ab Q_cd max|D| is below the mixed-precision cutoff (jk_set_option)
- * run their primitive arithmetic in FP32 with FP64 accumulation of the
- * contracted block and FP64 J/K updates; the others, the Boys function at
- * small T, the Schwarz factors and the final J/K symmetrisation stay FP64. */
+ * bound Q_ab Q_cd max|D| is below the mixed-precision cutoff tau
+ * (jk_set_option) run in FP32 -- primitive arithmetic, contracted block and
+ * the digestion dot products, from centre differences formed in FP64 --
+ * and each digested sum is added to J and K in FP64 (split accumulation);
+ * the other quartets, the Boys function at small T, the Schwarz factors and
+ * the final J/K symmetrisation stay FP64. */
 int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision prec,
              void* cuda_stream);
 
 /* Nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D (device pointers):
  * dEdR[natom*3] (float64, device) is overwritten.  Derivative integrals by the
  * shift rule d phi_a/dA_i = 2 alpha phi_{a+1_i} - a_i phi_{a-1_i} on centres
- * A, B and C; the D centre by translational invariance.  prec as jk_build. */
+ * A, B and C; the D centre by translational invariance.  Both precisions run
+ * the FP64 derivative kernels, which are compiled for shells up to d: a handle
+ * with f shells returns JK_ERR_UNSUPPORTED. */
 int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, void* cuda_stream);
 
 /* Many independent molecules in one launch sequence (one persistent launch per
@@ -152,7 +156,7 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 
 /* Tunables (process-wide). */
 typedef enum {
-    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-7) */
+    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys in FP64 for T < tsmall (default 1.0) */
     JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous) */
     JK_OPT_GRAPH = 3,            /* nonzero: jk_build_batched captures and replays a CUDA graph */
@@ -191,6 +195,14 @@ int jk_last_launches(jk_pairs pairs, int64_t* nlaunch);
  * operation count of the generated McMurchie-Davidson code for the whole
  * class.  *nrows receives the number of classes with work. */
 int jk_class_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
+
+/* Work of each precision in the last JK_MIXED jk_build on this handle (host,
+ * synchronous; JK_ERR_INVALID if that build was not mixed).  Writes up to
+ * max_rows rows of 8 int64: bra class, ket class, then for the FP32 quartets
+ * and for the FP64 quartets each: shell quartets, primitive quartets and the
+ * algorithmic operation count of the generated code (as jk_class_stats).
+ * *nrows receives the number of classes with work. */
+int jk_split_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
 
 /* Launch timings of the last jk_build with JK_OPT_PROFILE set (host,
  * synchronous): up to max_rows rows of 5 doubles: bra class, ket class,

@@ -43,7 +43,7 @@ EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_bui
            "jk_energy_noalloc",
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
-           "jk_set_tuning"]
+           "jk_set_tuning", "jk_split_stats"]
 
 
 def load():
@@ -72,6 +72,7 @@ def load():
         lib.jk_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         lib.jk_set_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.jk_class_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
+        lib.jk_split_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
         lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
         lib.shellpairs_free.argtypes = [vp]
@@ -277,6 +278,21 @@ def class_stats(pairs: ShellPairs):
         r = buf[6 * k:6 * k + 6]
         out.append(dict(cls=PAIR_CLASS_NAMES[r[0]] + "|" + PAIR_CLASS_NAMES[r[1]], bra=r[0], ket=r[1],
                         nquartets=r[2], nprimq=r[3], nbrap=r[4], flops=r[5]))
+    return out
+
+
+def split_stats(pairs: ShellPairs):
+    """Per class of the last mixed build: FP32 and FP64 shell quartets,
+    primitive quartets and algorithmic operation counts."""
+    buf = (C.c_int64 * (8 * 64))()
+    n = C.c_int()
+    _check(load().jk_split_stats(pairs.handle, 64, buf, C.byref(n)))
+    out = []
+    for k in range(n.value):
+        r = buf[8 * k:8 * k + 8]
+        out.append(dict(cls=PAIR_CLASS_NAMES[r[0]] + "|" + PAIR_CLASS_NAMES[r[1]], bra=r[0], ket=r[1],
+                        fp32=dict(nquartets=r[2], nprimq=r[3], flops=r[4]),
+                        fp64=dict(nquartets=r[5], nprimq=r[6], flops=r[7])))
     return out
 
 

@@ -36,7 +36,7 @@ def _digest(paths, extra=""):
     return h.hexdigest()
 
 
-def build(force: bool = False, lmax: int = 2, jobs: int | None = None, verbose: bool = False) -> str:
+def build(force: bool = False, lmax: int = 3, jobs: int | None = None, verbose: bool = False) -> str:
     sys.path.insert(0, os.path.join(HERE, "codegen"))
     try:
         import md_codegen

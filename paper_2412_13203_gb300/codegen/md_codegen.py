@@ -318,16 +318,27 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     pp, pp2 = ("pairs.ppf", "pairs.ppf2") if f32 else ("pairs.pp", "pairs.pp2")
     vec = "float" if f32 else "double"
     fma = "fmaf" if f32 else "fma"
-    E(f"double acc[{NAB * NCD}];")
-    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * NCD}; ++i) acc[i] = 0.0;")
+    # the contracted block is held in the kernel's own precision: FP64 for
+    # FP64 quartets; FP32 for FP32 quartets (a sum over <= 64 bra primitive
+    # pairs of terms of one sign pattern; J and K still accumulate in FP64)
+    E(f"{real} acc[{NAB * NCD}];")
+    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * NCD}; ++i) acc[i] = 0;")
     if not mode_flat:
         E(f"{real} Xl[{HAB * NCD}];")
         E(f"{real} Rc[{L1 * L1 * L1}];")
     E("for (int ip = 0; ip < ib.z; ++ip) {")
-    E(f"const {vec}4 pa = {pp}[ib.w + ip]; const {vec}2 pb = {pp2}[ib.w + ip];")
-    E(f"const {real} p = pa.w, kp = pb.x, inv2p = pb.y;")
-    E(f"const {real} PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
-    E(f"const {real} PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
+    if f32:
+        # P - A, P - B and A - C were formed in FP64 and rounded once
+        E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
+        E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
+        E("const float PAx = pa.x, PAy = pa.y, PAz = pa.z;")
+        E("const float PBx = pb.x, PBy = pb.y, PBz = pb.z;")
+        E("const float PCx = PAx + ACx, PCy = PAy + ACy, PCz = PAz + ACz;  // P - C")
+    else:
+        E(f"const {vec}4 pa = {pp}[ib.w + ip]; const {vec}2 pb = {pp2}[ib.w + ip];")
+        E(f"const {real} p = pa.w, kp = pb.x, inv2p = pb.y;")
+        E(f"const {real} PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
+        E(f"const {real} PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
     inv2p = Sym(name="inv2p")
     Ebx = gen_E_axis(em, "ebx", la, lb, Sym(name="PAx"), Sym(name="PBx"), inv2p)
     Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
@@ -343,16 +354,25 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     else:
         E(f"for (int i = 0; i < {HAB * NCD}; ++i) Xl[i] = 0;")
     E("for (int jq = 0; jq < ik.z; ++jq) {")
-    E(f"const {vec}4 qa = {pp}[ik.w + jq]; const {vec}2 qb = {pp2}[ik.w + jq];")
-    E(f"const {real} q = qa.w, kq = qb.x, inv2q = qb.y;")
-    E(f"const {real} QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
-    E(f"const {real} QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
+    if f32:
+        E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
+        E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q);")
+        E("const float QCx = qa.x, QCy = qa.y, QCz = qa.z;")
+        E("const float QDx = qb.x, QDy = qb.y, QDz = qb.z;")
+    else:
+        E(f"const {vec}4 qa = {pp}[ik.w + jq]; const {vec}2 qb = {pp2}[ik.w + jq];")
+        E(f"const {real} q = qa.w, kq = qb.x, inv2q = qb.y;")
+        E(f"const {real} QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
+        E(f"const {real} QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
     em.flops = 0
     inv2q = Sym(name="inv2q")
     Ekx = gen_E_axis(em, "ekx", lc, ld, Sym(name="QCx"), Sym(name="QDx"), inv2q, sign=True)
     Eky = gen_E_axis(em, "eky", lc, ld, Sym(name="QCy"), Sym(name="QDy"), inv2q, sign=True)
     Ekz = gen_E_axis(em, "ekz", lc, ld, Sym(name="QCz"), Sym(name="QDz"), inv2q, sign=True)
-    E(f"const {real} PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
+    if f32:
+        E("const float PQx = PCx - QCx, PQy = PCy - QCy, PQz = PCz - QCz;")
+    else:
+        E(f"const {real} PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
     if f32:
         E("const float rs = rsqrtf(p + q);")
         E("const float kqrs = kq * rs;")
@@ -432,14 +452,14 @@ def gen_quartet_body(bra, ket, real, mode_flat):
         for ab in range(NAB):
             for cd in range(NCD):
                 expr = _dot(em, fma, [(sv, f"x{hbi[h]}_{cd}") for h, sv in bprod[ab]])
-                E(f"acc[{ab * NCD + cd}] += (double)({expr});")
+                E(f"acc[{ab * NCD + cd}] += {expr};")
     else:
         E(f"#pragma unroll 1\nfor (int cd = 0; cd < {NCD}; ++cd) {{")
         for h in range(HAB):
             E(f"const {real} xh{h} = Xl[{h} * {NCD} + cd];")
         for ab in range(NAB):
             expr = _dot(em, fma, [(sv, f"xh{hbi[h]}") for h, sv in bprod[ab]])
-            E(f"acc[{ab} * {NCD} + cd] += (double)({expr});")
+            E(f"acc[{ab} * {NCD} + cd] += {expr};")
         E("}")
         em.flops = 2 * cnt["bra"]
     flops_bra = em.flops
@@ -448,6 +468,210 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     stats = dict(flops_per_primq=flops_setup + flops_R + flops_x + flops_eket,
                  flops_per_brap=flops_bra + flops_ebra, flat=mode_flat, **cnt)
     return body, stats
+
+
+def use_chunk(bra, ket):
+    """Classes with an f shell beyond the flat size: one thread per (shell
+    quartet, Cartesian component c of the ket's first shell), so that the
+    per-thread block is NAB x ND instead of NAB x NC x ND and the generated
+    code stays compact (per-axis E arrays, R cube, bra E products in a local
+    array)."""
+    return max(bra + ket) >= 3 and (not use_flat(bra, ket) or sum(bra + ket) > 4)
+
+
+def gen_R_rolled(em, L, f32):
+    """R^{(0)}_{tuv}, t+u+v <= L, into the cube Rc (side L+1) by loops, in
+    place: level n overwrites level n+1 from the highest total t+u+v down,
+    so every value it reads (totals s-1 and s-2 of level n+1) is still there.
+    FP64: R^{(n)}_{000} = pref (-2 rho)^n F_n,
+          R^{(n)}_{t+1,u,v} = t R^{(n+1)}_{t-1,u,v} + X_PQ R^{(n+1)}_{tuv};
+    FP32: the scaled form of gen_R_scaled (prefactor folded into the E products)."""
+    E = em.emit
+    L1 = L + 1
+    real = "float" if f32 else "double"
+    fma = "fmaf" if f32 else "fma"
+    if f32:
+        E(f"Rc[0] = {'-' if L % 2 else ''}F[{L}];")
+    else:
+        E(f"double pwv[{L + 1}];")
+        E("pwv[0] = pref;")
+        E(f"#pragma unroll\nfor (int n = 1; n <= {L}; ++n) pwv[n] = pwv[n - 1] * m2r;")
+        E(f"Rc[0] = pwv[{L}] * F[{L}];")
+    X = ("PQsx", "PQsy", "PQsz") if f32 else ("PQx", "PQy", "PQz")
+    step = "r2" if f32 else "1.0"
+    E(f"#pragma unroll\nfor (int n = {L - 1}; n >= 0; --n) {{")
+    E(f"#pragma unroll 1\nfor (int s_ = {L} - n; s_ >= 1; --s_)")
+    E("for (int t = s_; t >= 0; --t)")
+    E("for (int u = s_ - t; u >= 0; --u) {")
+    E("  const int v = s_ - t - u;")
+    E(f"  const int o = (t * {L1} + u) * {L1} + v;")
+    E(f"  {real} r;")
+    E(f"  if (t > 0) {{ r = {X[0]} * Rc[o - {L1 * L1}]; if (t > 1) r = {fma}(({real})(t - 1) * {step}, Rc[o - {2 * L1 * L1}], r); }}")
+    E(f"  else if (u > 0) {{ r = {X[1]} * Rc[o - {L1}]; if (u > 1) r = {fma}(({real})(u - 1) * {step}, Rc[o - {2 * L1}], r); }}")
+    E(f"  else {{ r = {X[2]} * Rc[o - 1]; if (v > 1) r = {fma}(({real})(v - 1) * {step}, Rc[o - 2], r); }}")
+    E("  Rc[o] = r;")
+    E("}")
+    if f32:
+        E("Rc[0] = (n & 1) ? -F[n] : F[n];")
+    else:
+        E("Rc[0] = pwv[n] * F[n];")
+    E("}")
+
+
+def support(la, lb):
+    """Per Cartesian pair (a, b): its Hermite support [(t, u, v)] in order."""
+    out = []
+    for a in comps(la):
+        for b in comps(lb):
+            out.append([(t, u, v) for t in range(a[0] + b[0] + 1) for u in range(a[1] + b[1] + 1)
+                        for v in range(a[2] + b[2] + 1)])
+    return out
+
+
+def support_table(la, lb):
+    """Packed per-axis indices of every support element: ix | iy << 8 | iz << 16,
+    each the offset of E^{a_i b_i}_t in that axis's array."""
+    T = la + lb + 1
+    rows = []
+    for (a, b), sup in zip([(a, b) for a in comps(la) for b in comps(lb)], support(la, lb)):
+        for (t, u, v) in sup:
+            ix = (a[0] * (lb + 1) + b[0]) * T + t
+            iy = (a[1] * (lb + 1) + b[1]) * T + u
+            iz = (a[2] * (lb + 1) + b[2]) * T + v
+            rows.append(ix | (iy << 8) | (iz << 16))
+    return f"static __device__ __constant__ int c_bsup_{la}{lb}[{len(rows)}] = {{{', '.join(map(str, rows))}}};", len(rows)
+
+
+def gen_quartet_body_chunk(bra, ket, real):
+    """Device code computing acc[NAB*ND] (one ket component c = ci) of one
+    shell quartet.  Expects in scope: pairs, ib, ik, ci, the centres (FP64:
+    A, B, C, Dd; FP32: ACx, ACy, ACz) and the Boys tables."""
+    la, lb = bra
+    lc, ld = ket
+    L = la + lb + lc + ld
+    L1 = L + 1
+    cnt = quartet_counts(bra, ket)
+    NAB, HAB = cnt["NAB"], cnt["HAB"]
+    nd = ncart(ld)
+    f32 = real == "float"
+    fma = "fmaf" if f32 else "fma"
+    em = Emitter(real)
+    E = em.emit
+    hb = herm(la + lb)
+    hbi = hidx(hb)
+    sup = support(la, lb)
+    S_ab = sum(len(x) for x in sup)
+    TB, TK = la + lb + 1, lc + ld + 1
+    E(f"{real} acc[{NAB * nd}];")
+    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * nd}; ++i) acc[i] = 0;")
+    E(f"{real} Xl[{HAB * nd}];")
+    E(f"{real} Rc[{L1 * L1 * L1}];")
+    E(f"{real} Ebp[{S_ab}];")
+    E(f"const int cx = c_comp_{lc}[3 * ci], cy = c_comp_{lc}[3 * ci + 1], cz = c_comp_{lc}[3 * ci + 2];")
+    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    if f32:
+        E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
+        E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
+        E("const float PAx = pa.x, PAy = pa.y, PAz = pa.z;")
+        E("const float PBx = pb.x, PBy = pb.y, PBz = pb.z;")
+        E("const float PCx = PAx + ACx, PCy = PAy + ACy, PCz = PAz + ACz;  // P - C")
+    else:
+        E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
+        E("const double p = pa.w, kp = pb.x, inv2p = pb.y;")
+        E("const double PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
+        E("const double PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
+    inv2p = Sym(name="inv2p")
+    for ax in "xyz":
+        Eb = gen_E_axis(em, f"eb{ax}", la, lb, Sym(name=f"PA{ax}"), Sym(name=f"PB{ax}"), inv2p)
+        E(f"{real} eb{ax}a[{(la + 1) * (lb + 1) * TB}];")
+        for i in range(la + 1):
+            for j in range(lb + 1):
+                for t in range(TB):
+                    E(f"eb{ax}a[{(i * (lb + 1) + j) * TB + t}] = {em.val(Eb.get((i, j, t), ZERO))};")
+    E(f"#pragma unroll 4\nfor (int k = 0; k < {S_ab}; ++k) {{")
+    E(f"  const int w = c_bsup_{la}{lb}[k];")
+    E(f"  Ebp[k] = ebxa[w & 255] * ebya[(w >> 8) & 255] * ebza[w >> 16]{' * kp' if f32 else ''};")
+    E("}")
+    E(f"for (int i = 0; i < {HAB * nd}; ++i) Xl[i] = 0;")
+    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    if f32:
+        E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
+        E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q);")
+        E("const float QCx = qa.x, QCy = qa.y, QCz = qa.z;")
+        E("const float QDx = qb.x, QDy = qb.y, QDz = qb.z;")
+        E("const float PQx = PCx - QCx, PQy = PCy - QCy, PQz = PCz - QCz;")
+        E("const float rs = rsqrtf(p + q);")
+        E("const float kqrs = kq * rs;")
+    else:
+        E("const double4 qa = pairs.pp[ik.w + jq]; const double2 qb = pairs.pp2[ik.w + jq];")
+        E("const double q = qa.w, kq = qb.x, inv2q = qb.y;")
+        E("const double QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
+        E("const double QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
+        E("const double PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
+        E("const double rs = rsqrt(p + q);")
+    inv2q = Sym(name="inv2q")
+    for ax in "xyz":
+        Ek = gen_E_axis(em, f"ek{ax}", lc, ld, Sym(name=f"QC{ax}"), Sym(name=f"QD{ax}"), inv2q, sign=True)
+        E(f"{real} ek{ax}a[{(lc + 1) * (ld + 1) * TK}];")
+        for i in range(lc + 1):
+            for j in range(ld + 1):
+                for t in range(TK):
+                    E(f"ek{ax}a[{(i * (ld + 1) + j) * TK + t}] = {em.val(Ek.get((i, j, t), ZERO))};")
+    E(f"const {real} rho = p * q * rs * rs;")
+    E(f"const {real} T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
+    if f32:
+        E("const float r2 = 2.0f * rho;")
+        E("const float PQsx = r2 * PQx, PQsy = r2 * PQy, PQsz = r2 * PQz;")
+    else:
+        E("const double pref = kp * kq * rs;")
+        E("const double m2r = -2 * rho;")
+    E(f"{real} F[{L + 1}];")
+    if f32:
+        E(f"gb::boys_mixed<{L}>(T, F, boys, boysf, tsmall);")
+    else:
+        E(f"gb::boys_f64<{L}>(T, F, boys);")
+    gen_R_rolled(em, L, f32)
+    # ket transform of the chunk's components (c = ci, d = 0..nd-1)
+    E(f"#pragma unroll 1\nfor (int d = 0; d < {nd}; ++d) {{")
+    E(f"const int dx = c_comp_{ld}[3 * d], dy = c_comp_{ld}[3 * d + 1], dz = c_comp_{ld}[3 * d + 2];")
+    for h in range(HAB):
+        E(f"{real} xh{h} = Xl[{h} * {nd} + d];")
+    E("for (int tau = 0; tau <= cx + dx; ++tau) {")
+    E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {TK} + tau]{' * kqrs' if f32 else ''};")
+    E("for (int nu = 0; nu <= cy + dy; ++nu) {")
+    E(f"const {real} exy = ex * ekya[(cy * {ld + 1} + dy) * {TK} + nu];")
+    E("for (int phi = 0; phi <= cz + dz; ++phi) {")
+    E(f"const {real} e = exy * ekza[(cz * {ld + 1} + dz) * {TK} + phi];")
+    E(f"const {real}* Rb = Rc + (tau * {L1} + nu) * {L1} + phi;")
+    for h, (t, u, v) in enumerate(hb):
+        E(f"xh{h} = {fma}(e, Rb[{(t * L1 + u) * L1 + v}], xh{h});")
+    E("}}}")
+    for h in range(HAB):
+        E(f"Xl[{h} * {nd} + d] = xh{h};")
+    E("}")
+    E("}  // ket primitives")
+    # bra transform: acc[ab][d] += sum_k Ebp[k] X[h_k][d]
+    E(f"#pragma unroll 1\nfor (int d = 0; d < {nd}; ++d) {{")
+    for h in range(HAB):
+        E(f"const {real} xh{h} = Xl[{h} * {nd} + d];")
+    k = 0
+    for ab in range(NAB):
+        terms = []
+        for (t, u, v) in sup[ab]:
+            terms.append(f"Ebp[{k}]")
+            k += 1
+        expr = None
+        for j, (t, u, v) in enumerate(sup[ab]):
+            x = f"xh{hbi[(t, u, v)]}"
+            expr = f"{terms[j]} * {x}" if expr is None else f"{fma}({terms[j]}, {x}, {expr})"
+        E(f"acc[{ab} * {nd} + d] += {expr};")
+    E("}")
+    E("}  // bra primitives")
+    flops_primq = 16 + kBoysCost(L) + 3 * cnt["R"] + 2 * HAB * cnt["S_cd"]
+    flops_brap = 2 * S_ab * cnt["NCD"] + 2 * S_ab
+    return "\n".join(em.lines), dict(flops_per_primq=flops_primq, flops_per_brap=flops_brap, flat=False, chunk=True,
+                                     **cnt)
+
 
 
 def _dot(em, fma, terms):
@@ -485,51 +709,95 @@ def gen_class_kernels(bra, ket):
     lc, ld = ket
     na, nb, nc, nd = ncart(la), ncart(lb), ncart(lc), ncart(ld)
     flat = use_flat(bra, ket)
+    chunk = use_chunk(bra, ket)
+    nch = nc if chunk else 1  # threads per shell quartet
     out = []
     stats = None
     for prec, real in (("f64", "double"), ("f32", "float")):
-        body, st = gen_quartet_body(bra, ket, real, flat)
+        if chunk:
+            body, st = gen_quartet_body_chunk(bra, ket, real)
+        else:
+            body, st = gen_quartet_body(bra, ket, real, flat)
         if prec == "f64":
             stats = st
         name = class_name(bra, ket)
-        vec = "float" if real == "float" else "double"
-        cen = ("Af", "Bf") if real == "float" else ("A", "B")
+        if chunk:
+            digest = f"gb::digest_chunk<{na}, {nb}, {nc}, {nd}>(acc, ci, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);"
+        else:
+            digest = (f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
+                      f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);")
+        if real == "float":
+            centres = ("  const double4 Ad = pairs.A[bra], Cd = pairs.A[ket];\n"
+                       "  const float ACx = (float)(Ad.x - Cd.x), ACy = (float)(Ad.y - Cd.y), ACz = (float)(Ad.z - Cd.z);")
+            dmat = "Dfm"
+        else:
+            centres = "  const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];"
+            dmat = "Dm"
         out.append(f"""
 __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs args) {{
   // persistent grid-stride loop over the quartets of this launch; the total is
   // read on the device (last entry of the row prefix) so launches need no host sync
-  const long long total = args.rows.start[args.rows.nrows];
+  // ({nch} thread(s) per shell quartet: one per Cartesian component of the ket's first shell)
+  const long long total = args.rows.start[args.rows.nrows] * {nch};
   const double* __restrict__ boys = args.boys;
   const float* __restrict__ boysf = args.boysf;
   const float tsmall = args.tsmall;
   (void)boysf; (void)tsmall;
   for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {{
+  const long long qt = tid / {nch};
+  const int ci = (int)(tid - qt * {nch});
+  (void)ci;
   int bra, ket, row;
-  gb::locate_quartet(args.rows, tid, bra, ket, row);
+  gb::locate_quartet(args.rows, qt, bra, ket, row);
   gb::PairsView pairs = args.pairs;
   const double* Dm = args.D;
+  const float* Dfm = args.Df;
   double* Jm = args.J;
   double* Km = args.K;
   int nbf = args.nbf;
+  (void)Dm; (void)Dfm;
   if (args.mols) {{
     const gb::BatchMol& bm = args.mols[args.row_mol[row]];
-    pairs = bm.pairs; Dm = bm.D; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
+    pairs = bm.pairs; Dm = bm.D; Dfm = bm.Df; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
   }}
   const int4 ib = pairs.info[bra], ik = pairs.info[ket];
-  const {vec}4 A = pairs.{cen[0]}[bra], B = pairs.{cen[1]}[bra], C = pairs.{cen[0]}[ket], Dd = pairs.{cen[1]}[ket];
+{centres}
 {indent(body)}
-  double s = 1.0;
-  if (ib.x == ib.y) s *= 0.5;
-  if (ik.x == ik.y) s *= 0.5;
-  if (bra == ket) s *= 0.5;
+  {real} s = 1;
+  if (ib.x == ib.y) s *= 0.5f;
+  if (ik.x == ik.y) s *= 0.5f;
+  if (bra == ket) s *= 0.5f;
 #pragma unroll
-  for (int i = 0; i < {na * nb * nc * nd}; ++i) acc[i] *= s;
-  gb::{"digest" if flat else "digest_loop"}<{na}, {nb}, {nc}, {nd}>(acc, ib.x, ib.y, ik.x, ik.y, Dm, Jm, Km, nbf);
+  for (int i = 0; i < {na * nb * (nd if chunk else nc * nd)}; ++i) acc[i] *= s;
+  {digest.format(dm=dmat)}
   }}
 }}
 """)
-        if bra == ket and prec == "f64":
+        if bra == ket and prec == "f64" and chunk:
+            out.append(f"""
+__global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArgs sa) {{
+  // one thread per (pair, component a = ci of shell a): the diagonal
+  // elements (ab|ab) with that a; Q is the max over the {nch} threads (sa.Q
+  // zeroed by the caller; non-negative doubles order like their bit patterns)
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)sa.count * {nch}) return;
+  const int i = (int)(tid / {nch}), ci = (int)(tid - (long long)i * {nch});
+  const int bra = sa.first + i, ket = bra;
+  const gb::PairsView& pairs = sa.pairs;
+  const double* __restrict__ boys = sa.boys;
+  const float* __restrict__ boysf = nullptr;
+  const float tsmall = 0.f;
+  (void)boysf; (void)tsmall;
+  const int4 ib = pairs.info[bra], ik = ib;
+  const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
+{indent(body)}
+  double m = 0.0;
+  for (int b = 0; b < {nb}; ++b) m = fmax(m, fabs(acc[(ci * {nb} + b) * {nd} + b]));
+  atomicMax(reinterpret_cast<unsigned long long*>(sa.Q + i), (unsigned long long)__double_as_longlong(sqrt(m)));
+}}
+""")
+        elif bra == ket and prec == "f64":
             out.append(f"""
 __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArgs sa) {{
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -786,21 +1054,29 @@ def class_pairs(lmax):
     return [(pcs[i], pcs[j]) for i in range(len(pcs)) for j in range(i + 1)]
 
 
-def generate(outdir, lmax=LMAX, nfiles=8):
+GRAD_LMAX = 2  # derivative kernels are generated for shells up to d
+
+
+def generate(outdir, lmax=LMAX, nfiles=None):
     os.makedirs(outdir, exist_ok=True)
     qs = class_pairs(lmax)
-    # spread classes over translation units by estimated size
+    gqs = class_pairs(min(lmax, GRAD_LMAX))
+    if nfiles is None:
+        nfiles = max(8, len(qs) // 3)
+    # spread classes over translation units by generated code size (compile
+    # time grows with it), largest first onto the lightest unit
+    code_of = {}
     sized = []
     for bra, ket in qs:
-        c = quartet_counts(bra, ket)
-        sized.append(((c["xket"] + c["bra"]) if use_flat(bra, ket) else 400, bra, ket))
+        code_of[(bra, ket)] = gen_class_kernels(bra, ket)
+        sized.append((len(code_of[(bra, ket)][0]), bra, ket))
     sized.sort(reverse=True)
     bins = [[] for _ in range(nfiles)]
     load = [0] * nfiles
     for w, bra, ket in sized:
         k = load.index(min(load))
         bins[k].append((bra, ket))
-        load[k] += w + 100
+        load[k] += w + 2000
     header = '#include "eri_device.cuh"\n'
     stats_all = {}
     files = []
@@ -811,8 +1087,11 @@ def generate(outdir, lmax=LMAX, nfiles=8):
         kets = sorted({ket for _, ket in items})
         for ket in kets:
             src.append(cd_table(*ket))
+        src += [comp_table(l) for l in range(lmax + 1)]
+        for bra_ in sorted({bra for bra, ket in items if use_chunk(bra, ket)}):
+            src.append(support_table(*bra_)[0])
         for bra, ket in items:
-            code, st = gen_class_kernels(bra, ket)
+            code, st = code_of[(bra, ket)]
             src.append(code)
             stats_all[class_name(bra, ket)] = st
             name = class_name(bra, ket)
@@ -825,11 +1104,12 @@ int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStr
 }}
 """)
             if bra == ket:
+                nthr = ncart(bra[0]) if use_chunk(bra, ket) else 1
                 src.append(f"""
 int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
   if (a.count <= 0) return 0;
   const int bs = 128;
-  eri_schwarz_{bra[0]}{bra[1]}<<<(a.count + bs - 1) / bs, bs, 0, s>>>(a);
+  eri_schwarz_{bra[0]}{bra[1]}<<<(unsigned)(((long long)a.count * {nthr} + bs - 1) / bs), bs, 0, s>>>(a);
   return (int)cudaGetLastError();
 }}
 """)
@@ -839,12 +1119,12 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
     # gradient kernels (rolled loops, compact), spread over a few TUs
     ngf = 4
     gbins = [[] for _ in range(ngf)]
-    for i, (bra, ket) in enumerate(sorted(qs, key=lambda x: -sum(x[0] + x[1]))):
+    for i, (bra, ket) in enumerate(sorted(gqs, key=lambda x: -sum(x[0] + x[1]))):
         gbins[i % ngf].append((bra, ket))
     for k, items in enumerate(gbins):
         if not items:
             continue
-        src = [header] + [comp_table(l) for l in range(lmax + 1)]
+        src = [header] + [comp_table(l) for l in range(min(lmax, GRAD_LMAX) + 1)]
         for bra, ket in items:
             src.append(gen_grad_kernel(bra, ket))
         fn = os.path.join(outdir, f"md_grad_{k}.cu")
@@ -858,7 +1138,7 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
     pcs = [pc for pc in PAIR_CLASSES if pc[0] <= lmax]
     for pc in pcs:
         d.append(f"int launch_schwarz_{pc[0]}{pc[1]}(const gb::SchwarzArgs& a, cudaStream_t s);")
-    for bra, ket in qs:
+    for bra, ket in gqs:
         d.append(f"int launch_grad_{class_name(bra, ket)}(const gb::GradArgs& a, cudaStream_t s);")
     n = len(pcs)
     d.append("typedef int (*jk_launch_fn)(int, const gb::JKArgs&, int, int, cudaStream_t);")
@@ -873,10 +1153,29 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
     d.append("typedef int (*grad_launch_fn)(const gb::GradArgs&, cudaStream_t);")
     gtab = []
     for i in range(n):
-        row = [f"launch_grad_{class_name(pcs[i], pcs[j])}" if j <= i else "nullptr" for j in range(n)]
+        row = [f"launch_grad_{class_name(pcs[i], pcs[j])}" if j <= i and (pcs[i], pcs[j]) in gqs else "nullptr"
+               for j in range(n)]
         gtab.append("{" + ", ".join(row) + "}")
     d.append(f"static const grad_launch_fn k_grad_tab[{n}][{n}] = {{{', '.join(gtab)}}};")
-    d.append("int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s) { return k_grad_tab[bra_cls][ket_cls](a, s); }")
+    d.append("// -1: no derivative kernel for this class (shells above the gradient lmax)")
+    d.append("int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s) {\n"
+             "  return k_grad_tab[bra_cls][ket_cls] ? k_grad_tab[bra_cls][ket_cls](a, s) : -1;\n}")
+    d.append(f"int gb_grad_lmax() {{ return {min(lmax, GRAD_LMAX)}; }}")
+    thr = []
+    for prec in ("f64", "f32"):
+        rows_ = []
+        for i in range(n):
+            row = []
+            for j in range(n):
+                t = 1
+                if j <= i and use_chunk(pcs[i], pcs[j]):
+                    t = ncart(pcs[j][0])
+                row.append(str(t))
+            rows_.append("{" + ", ".join(row) + "}")
+        thr.append("{" + ", ".join(rows_) + "}")
+    d.append(f"static const int k_threads_tab[2][{n}][{n}] = {{{', '.join(thr)}}};")
+    d.append("// threads per shell quartet of a class kernel (prec 0: FP64, 1: FP32)")
+    d.append("int gb_class_threads(int bra_cls, int ket_cls, int prec) { return k_threads_tab[prec][bra_cls][ket_cls]; }")
     d.append(f"static const jk_launch_fn k_jk_tab[{n}][{n}] = {{{', '.join(tab)}}};")
     d.append(f"static const schwarz_launch_fn k_sw_tab[{n}] = {{{', '.join(f'launch_schwarz_{pc[0]}{pc[1]}' for pc in pcs)}}};")
     d.append("""

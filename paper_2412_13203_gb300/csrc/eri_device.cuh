@@ -29,12 +29,13 @@ struct PairsView {
     const int4* info;      // per pair: fa, fb (first basis functions of shells a, b), nprim pairs, first prim pair
     const double4* A;      // per pair: centre of a (xyz), w = Q_ab (Schwarz factor)
     const double4* B;      // per pair: centre of b (xyz), w = unused
-    const float4* Af;      // FP32 copies
-    const float4* Bf;
     const double4* pp;     // per primitive pair: P (xyz), p
     const double2* pp2;    // per primitive pair: kappa = sqrt(2 pi^(5/2)) K_AB c_a c_b / p, 1/(2p)
-    const float4* ppf;     // FP32 copies
-    const float2* ppf2;
+    // FP32 kernels see only centre differences, each formed in FP64 and then
+    // rounded once, so that no FP32 subtraction of two absolute coordinates
+    // (|R| ~ 10 bohr) loses the digits of a short distance:
+    const float4* ppf;     // per primitive pair: P - A (xyz), p
+    const float4* ppf2;    // per primitive pair: P - B (xyz), kappa
     const double* alpha;   // per primitive pair: exponent of the shell-a primitive (gradients)
 };
 
@@ -49,6 +50,7 @@ struct RowsView {
 struct BatchMol {
     PairsView pairs;
     const double* D;
+    float* Df;                // FP32 copy of D (mixed builds; written by the max|D| pass)
     double* J;
     double* K;
     int nbf;
@@ -61,6 +63,7 @@ struct JKArgs {
     const float* boysf;       // FP32 Boys table
     float tsmall;             // mixed kernels: FP64 Boys below this T
     const double* D;
+    const float* Df;          // FP32 copy of D (mixed builds: digestion of the FP32 quartets)
     double* J;                // accumulates J' (J = J' + J'^T afterwards)
     double* K;                // accumulates K'
     int nbf;
@@ -179,57 +182,60 @@ __device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, 
 //   K'_ac += sum_bd I D_bd,     K'_ad += sum_bc I D_bc,
 //   K'_bc += sum_ad I D_ad,     K'_bd += sum_ac I D_ac,
 // and J = J' + J'^T, K = K' + K'^T afterwards.
-template <int NA, int NB, int NC, int ND>
-__device__ __forceinline__ void digest(const double* acc, int fa, int fb, int fc, int fd,
-                                       const double* __restrict__ D, double* J, double* K, int n) {
+// R is the arithmetic type of the block and of the density copy (double for
+// FP64 quartets; float for FP32 quartets, whose sums are added to J and K
+// in FP64 by the atomics).
+template <int NA, int NB, int NC, int ND, class R>
+__device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int fd,
+                                       const R* __restrict__ D, double* J, double* K, int n) {
     // J'_ab
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fc + c) * n + fd + d), v);
-            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * v);
+            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
         }
     // J'_cd
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fb + b), v);
-            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * v);
+            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
         }
     // K'_ac and K'_ad
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fc + c, v);
+            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
         }
     }
     // K'_bc and K'_bd
@@ -237,89 +243,140 @@ __device__ __forceinline__ void digest(const double* acc, int fa, int fb, int fc
     for (int b = 0; b < NB; ++b) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fc + c, v);
+            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            double v = 0.0;
+            R v = 0;
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
         }
     }
 }
 
 // Same update with rolled loops (large classes: bounded code size; the block
 // lives in local memory there anyway).
-template <int NA, int NB, int NC, int ND>
-__device__ __forceinline__ void digest_loop(const double* acc, int fa, int fb, int fc, int fd,
-                                            const double* __restrict__ D, double* J, double* K, int n) {
+template <int NA, int NB, int NC, int ND, class R>
+__device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc, int fd,
+                                            const R* __restrict__ D, double* J, double* K, int n) {
 #pragma unroll 1
     for (int ab = 0; ab < NA * NB; ++ab) {
         const int a = ab / NB, b = ab % NB;
-        double v = 0.0;
+        R v = 0;
         for (int cd = 0; cd < NC * ND; ++cd)
             v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fc + cd / ND) * n + fd + cd % ND), v);
-        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * v);
+        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
     }
 #pragma unroll 1
     for (int cd = 0; cd < NC * ND; ++cd) {
         const int c = cd / ND, d = cd % ND;
-        double v = 0.0;
+        R v = 0;
         for (int ab = 0; ab < NA * NB; ++ab)
             v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
-        atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * v);
+        atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
     }
 #pragma unroll 1
     for (int a = 0; a < NA; ++a)
 #pragma unroll 1
         for (int c = 0; c < NC; ++c) {
-            double vac = 0.0;
+            R vac = 0;
             for (int b = 0; b < NB; ++b)
                 for (int d = 0; d < ND; ++d)
                     vac = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
-            atomicAdd(K + (size_t)(fa + a) * n + fc + c, vac);
+            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)vac);
         }
 #pragma unroll 1
     for (int a = 0; a < NA; ++a)
 #pragma unroll 1
         for (int d = 0; d < ND; ++d) {
-            double v = 0.0;
+            R v = 0;
             for (int b = 0; b < NB; ++b)
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
         }
 #pragma unroll 1
     for (int b = 0; b < NB; ++b)
 #pragma unroll 1
         for (int c = 0; c < NC; ++c) {
-            double v = 0.0;
+            R v = 0;
             for (int a = 0; a < NA; ++a)
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fc + c, v);
+            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll 1
     for (int b = 0; b < NB; ++b)
 #pragma unroll 1
         for (int d = 0; d < ND; ++d) {
-            double v = 0.0;
+            R v = 0;
             for (int a = 0; a < NA; ++a)
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
         }
 }
+
+// J/K update of the part of one unique shell quartet that has ket component
+// c = ci (classes computed one ket-component chunk per thread):
+// acc[(a*NB+b)*ND+d] = s (ab|ci d).  The same six updates as `digest`,
+// restricted to that c; the chunks of a quartet add up to the full update.
+template <int NA, int NB, int NC, int ND, class R>
+__device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int fb, int fc, int fd,
+                                             const R* __restrict__ D, double* J, double* K, int n) {
+    const int c = fc + ci;
+#pragma unroll 1
+    for (int ab = 0; ab < NA * NB; ++ab) {  // J'_ab
+        const int a = ab / NB, b = ab % NB;
+        R v = 0;
+        for (int d = 0; d < ND; ++d) v = fma(acc[ab * ND + d], __ldg(D + (size_t)c * n + fd + d), v);
+        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+    }
+#pragma unroll 1
+    for (int d = 0; d < ND; ++d) {  // J'_cd
+        R v = 0;
+        for (int ab = 0; ab < NA * NB; ++ab)
+            v = fma(acc[ab * ND + d], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
+        atomicAdd(J + (size_t)c * n + fd + d, 2.0 * (double)v);
+    }
+#pragma unroll 1
+    for (int a = 0; a < NA; ++a) {
+        R vac = 0;  // K'_ac
+        for (int b = 0; b < NB; ++b)
+            for (int d = 0; d < ND; ++d)
+                vac = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
+        atomicAdd(K + (size_t)(fa + a) * n + c, (double)vac);
+        for (int d = 0; d < ND; ++d) {  // K'_ad
+            R v = 0;
+            for (int b = 0; b < NB; ++b) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + c), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+        }
+    }
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+        R vbc = 0;  // K'_bc
+        for (int a = 0; a < NA; ++a)
+            for (int d = 0; d < ND; ++d)
+                vbc = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), vbc);
+        atomicAdd(K + (size_t)(fb + b) * n + c, (double)vbc);
+        for (int d = 0; d < ND; ++d) {  // K'_bd
+            R v = 0;
+            for (int a = 0; a < NA; ++a) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + c), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+        }
+    }
+}
+
 
 // Schwarz factor from a (ab|ab) block: sqrt(max_i |(ab|ab)_ii|).
 template <int NAB>

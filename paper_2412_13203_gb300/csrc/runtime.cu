@@ -33,6 +33,8 @@ int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int gr
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
 int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap);
 int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s);
+int gb_grad_lmax();
+int gb_class_threads(int bra_cls, int ket_cls, int prec);
 extern "C" int gb_num_pair_classes();
 
 namespace {
@@ -89,7 +91,7 @@ struct DevBuf {
 };
 
 constexpr int kMaxClasses = 10;  // pair classes for l <= 3
-constexpr int kNB = 16;          // primitive-pair-count buckets (ceil log2)
+constexpr int kNB = 128;         // primitive-pair-count buckets (exact count, 128+ share the last)
 
 struct TuneCfg {
     int block = 128;  // threads per block (kernels are compiled for <= 128)
@@ -117,7 +119,7 @@ std::mutex g_boys_mu;
 BoysTables g_boys[64];
 
 struct Options {
-    double tau = 1e-7;
+    double tau = 1e-2;
     double tsmall = 1.0;
     int check_sym = 0;
     int graph = 1;
@@ -137,7 +139,8 @@ struct jk_pairs_s {
     int natom = 0, nshell = 0, nbf = 0;
     long long npair_all = 0, npair = 0, nprimpair = 0;
     double thresh = 0.0, Qmax = 0.0;
-    DevBuf info, A, B, Af, Bf, pp, pp2, ppf, ppf2;  // sorted, kept pairs
+    DevBuf info, A, B, pp, pp2, ppf, ppf2;          // sorted, kept pairs
+    DevBuf Df;                                      // FP32 copy of the last mixed build's D
     DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
     DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
     DevBuf pair_lab;                                // int2 per pair: la, lb
@@ -152,6 +155,7 @@ struct jk_pairs_s {
     int last_prec = 0;
     int tuned[2] = {0, 0};
     DevBuf split_tot;                               // per class: FP32 and FP64 quartets of the last mixed build
+    DevBuf npre;                                    // exclusive prefix of primitive pairs over the kept pairs
     DevBuf scratch;                                 // small reductions
     std::vector<ProfRec> prof;
     ~jk_pairs_s() {
@@ -386,7 +390,8 @@ __global__ void k_pair_count(ShellDev S, long long npair, long long* nprimpair, 
 }
 
 __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, int4* info, double4* A, double4* B,
-                            int2* atoms, int2* lab, double4* pp, double2* pp2, double* alpha) {
+                            int2* atoms, int2* lab, double4* pp, double2* pp2, float4* ppf, float4* ppf2,
+                            double* alpha) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair) return;
     int i, j, a, b;
@@ -410,9 +415,14 @@ __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, 
             const double al = S.e[S.off[a] + u], be = S.e[S.off[b] + v];
             const double p = al + be, ip = 1.0 / p;
             const double Kab = exp(-al * be * ip * AB2);
+            const double kap = s2pi52 * Kab * S.c[S.off[a] + u] * S.c[S.off[b] + v] * ip;
             pp[o + n] = make_double4((al * Ra[0] + be * Rb[0]) * ip, (al * Ra[1] + be * Rb[1]) * ip,
                                      (al * Ra[2] + be * Rb[2]) * ip, p);
-            pp2[o + n] = make_double2(s2pi52 * Kab * S.c[S.off[a] + u] * S.c[S.off[b] + v] * ip, 0.5 * ip);
+            pp2[o + n] = make_double2(kap, 0.5 * ip);
+            // FP32 data: P - A = -(beta/p)(A - B), P - B = (alpha/p)(A - B), each rounded once
+            const double fa = -be * ip, fb = al * ip;
+            ppf[o + n] = make_float4((float)(fa * ABx), (float)(fa * ABy), (float)(fa * ABz), (float)p);
+            ppf2[o + n] = make_float4((float)(fb * ABx), (float)(fb * ABy), (float)(fb * ABz), (float)kap);
             alpha[o + n] = al;
         }
 }
@@ -440,14 +450,12 @@ __global__ void k_store_q(const double* Q, int first, int count, double4* A, uns
     atomicMax(qmax, (unsigned long long)__double_as_longlong(q));
 }
 
-__device__ __forceinline__ int bucket_of(int np) {
-    int b = 0;
-    while ((1 << b) < np) ++b;
-    return b;
-}
+// Exact primitive-pair count: kets of one bucket have the same trip count, so
+// the lanes of a warp working on one quartet row loop in step.
+__device__ __forceinline__ int bucket_of(int np) { return min(np, kNB) - 1; }
 
-// Final key: class (4 bits) | bucket (4 bits) | descending Q (56 bits); Q quantised
-// (7 low mantissa bits cleared) so that the stored Q and the sort order agree.
+// Final key: class (4 bits) | bucket (7 bits) | descending Q (53 bits); Q quantised
+// (10 low mantissa bits cleared) so that the stored Q and the sort order agree.
 __global__ void k_final_key(const double4* A, const int4* info, const int2* lab, long long n, double thresh,
                             double qmax, unsigned long long* key, int* val, long long npad) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -457,9 +465,9 @@ __global__ void k_final_key(const double4* A, const int4* info, const int2* lab,
     const int2 l = lab[k];
     const unsigned long long cls = (unsigned long long)(l.x * (l.x + 1) / 2 + l.y);
     const unsigned long long bk = (unsigned long long)bucket_of(info[k].z);
-    const unsigned long long qb = ((unsigned long long)__double_as_longlong(q)) >> 7;  // 56 bits
+    const unsigned long long qb = ((unsigned long long)__double_as_longlong(q)) >> 10;  // 53 bits (q > 0)
     if (thresh > 0.0 && q * qmax < thresh) { key[k] = ~0ull; val[k] = (int)k; return; }
-    key[k] = (cls << 60) | (bk << 56) | ((~qb) & ((1ull << 56) - 1));
+    key[k] = (cls << 60) | (bk << 53) | ((~qb) & ((1ull << 53) - 1));
     val[k] = (int)k;
 }
 
@@ -467,7 +475,7 @@ __global__ void k_quantise_q(double4* A, long long n) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const unsigned long long b = (unsigned long long)__double_as_longlong(A[k].w);
-    A[k].w = __longlong_as_double((long long)((b >> 7) << 7));
+    A[k].w = __longlong_as_double((long long)((b >> 10) << 10));
 }
 
 __global__ void k_count_kept(const unsigned long long* key, long long n, unsigned long long* cnt) {
@@ -478,8 +486,8 @@ __global__ void k_count_kept(const unsigned long long* key, long long n, unsigne
 __global__ void k_bucket_bounds(const unsigned long long* key, long long n, int* start) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int c = (int)(key[k] >> 56);  // class * 16 + bucket
-    const int cp = (k == 0) ? -1 : (int)(key[k - 1] >> 56);
+    const int c = (int)(key[k] >> 53);  // class * kNB + bucket
+    const int cp = (k == 0) ? -1 : (int)(key[k - 1] >> 53);
     if (c != cp) start[c] = (int)k;
 }
 
@@ -548,10 +556,15 @@ __global__ void k_rows_split(const long long* start, const int* rbra, const int*
     k32[r] = lo;
 }
 
-__global__ void k_absmax(const double* x, long long n, unsigned long long* out) {
+// max |x| (as the bit pattern of a non-negative double) and, if xf is not
+// null, the FP32 copy of x used by the digestion of FP32 quartets.
+__global__ void k_absmax(const double* x, long long n, unsigned long long* out, float* xf) {
     double m = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(x[i]));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        m = fmax(m, fabs(v));
+        if (xf) xf[i] = (float)v;
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -718,31 +731,12 @@ gb::PairsView view_of(const jk_pairs_s* h) {
     v.info = h->info.as<int4>();
     v.A = h->A.as<double4>();
     v.B = h->B.as<double4>();
-    v.Af = h->Af.as<float4>();
-    v.Bf = h->Bf.as<float4>();
     v.pp = h->pp.as<double4>();
     v.pp2 = h->pp2.as<double2>();
     v.ppf = h->ppf.as<float4>();
-    v.ppf2 = h->ppf2.as<float2>();
+    v.ppf2 = h->ppf2.as<float4>();
     v.alpha = h->alpha.as<double>();
     return v;
-}
-
-__global__ void k_to_f32(const double4* A, const double4* B, long long n, float4* Af, float4* Bf) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const double4 a = A[k], b = B[k];
-    Af[k] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
-    Bf[k] = make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
-}
-
-__global__ void k_pp_to_f32(const double4* pp, const double2* pp2, long long n, float4* ppf, float2* ppf2) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const double4 a = pp[k];
-    const double2 b = pp2[k];
-    ppf[k] = make_float4((float)a.x, (float)a.y, (float)a.z, (float)a.w);
-    ppf2[k] = make_float2((float)b.x, (float)b.y);
 }
 
 template <class T>
@@ -766,6 +760,8 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
         const int l = shells->l[s];
         if (l < 0) return fail(JK_ERR_INVALID, "negative angular momentum");
         if (l > JK_LMAX) return fail(JK_ERR_UNSUPPORTED, "angular momentum above f");
+        if ((l + 1) * (l + 2) / 2 > gb_num_pair_classes())  // pair classes compiled: (lmax+1)(lmax+2)/2
+            return fail(JK_ERR_UNSUPPORTED, "angular momentum " + std::to_string(l) + " not compiled into this build");
         if (shells->nprim[s] < 1) return fail(JK_ERR_INVALID, "shell without primitives");
         if (shells->atom[s] < 0 || shells->atom[s] >= atoms->natom) return fail(JK_ERR_INVALID, "shell atom out of range");
         if (shells->prim_offset[s] < 0) return fail(JK_ERR_INVALID, "negative primitive offset");
@@ -828,14 +824,12 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = h->pp.alloc(sizeof(double4) * nprimpair))) return rc;
     if ((rc = h->pp2.alloc(sizeof(double2) * nprimpair))) return rc;
     if ((rc = h->ppf.alloc(sizeof(float4) * nprimpair))) return rc;
-    if ((rc = h->ppf2.alloc(sizeof(float2) * nprimpair))) return rc;
+    if ((rc = h->ppf2.alloc(sizeof(float4) * nprimpair))) return rc;
     if ((rc = h->alpha.alloc(sizeof(double) * nprimpair))) return rc;
     k_pair_fill<<<nblk(np, 128), 128, 0, st>>>(SD, np, d_poff.as<long long>(), u_info.as<int4>(), u_A.as<double4>(),
                                                 u_B.as<double4>(), u_atoms.as<int2>(), u_lab.as<int2>(),
-                                                h->pp.as<double4>(), h->pp2.as<double2>(), h->alpha.as<double>());
-    CKL();
-    k_pp_to_f32<<<nblk(nprimpair, 256), 256, 0, st>>>(h->pp.as<double4>(), h->pp2.as<double2>(), nprimpair,
-                                                       h->ppf.as<float4>(), h->ppf2.as<float2>());
+                                                h->pp.as<double4>(), h->pp2.as<double2>(), h->ppf.as<float4>(),
+                                                h->ppf2.as<float4>(), h->alpha.as<double>());
     CKL();
     // ---- sort 1: by class, then Schwarz per class
     if ((rc = sort_pairs(d_key.as<unsigned long long>(), d_val.as<int>(), npad, st))) return rc;
@@ -871,6 +865,7 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = d_q.alloc(sizeof(double) * np))) return rc;
     if ((rc = d_qmax.alloc(sizeof(unsigned long long)))) return rc;
     CK(cudaMemsetAsync(d_qmax.p, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(d_q.p, 0, sizeof(double) * np, st));  // chunked Schwarz kernels take a max into Q
     gb::PairsView pv;
     std::memset(&pv, 0, sizeof(pv));
     pv.npair = (int)np;
@@ -911,8 +906,6 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = h->info.alloc(sizeof(int4) * nk))) return rc;
     if ((rc = h->A.alloc(sizeof(double4) * nk))) return rc;
     if ((rc = h->B.alloc(sizeof(double4) * nk))) return rc;
-    if ((rc = h->Af.alloc(sizeof(float4) * nk))) return rc;
-    if ((rc = h->Bf.alloc(sizeof(float4) * nk))) return rc;
     if ((rc = h->pair_atoms.alloc(sizeof(int2) * nk))) return rc;
     if ((rc = h->pair_lab.alloc(sizeof(int2) * nk))) return rc;
     if (kept > 0) {
@@ -923,8 +916,6 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
         k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_lab.as<int2>(), d_val.as<int>(), h->pair_lab.as<int2>(), kept);
         CKL();
         k_quantise_q<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), kept);
-        k_to_f32<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), h->B.as<double4>(), kept, h->Af.as<float4>(),
-                                                  h->Bf.as<float4>());
         CKL();
     }
     // ---- class / bucket segments
@@ -951,7 +942,8 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     h->cls_start[ncls] = (int)kept;
     h->bucket_start = bs;
     // ---- quartet rows per (bra class X >= ket class Y)
-    DevBuf d_npk, d_npre;
+    DevBuf d_npk;
+    DevBuf& d_npre = h->npre;
     if ((rc = d_npk.alloc(sizeof(long long) * (nk + 1)))) return rc;
     if ((rc = d_npre.alloc(sizeof(long long) * (nk + 1)))) return rc;
     CK(cudaMemsetAsync(d_npk.p, 0, sizeof(long long) * (nk + 1), st));
@@ -1040,13 +1032,14 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.boysf = g_boys[h->device].tabf.as<float>();
     a.tsmall = (float)g_opt.tsmall;
     a.D = D;
+    a.Df = h->Df.as<float>();
     a.J = J;
     a.K = K;
     a.nbf = h->nbf;
     a.mols = mols;
     a.row_mol = row_mol;
     const TuneCfg& tc = cr.tune[prec];
-    const int grid = grid_for(total_hint, tc.block, tc.qpt, h->nsm);
+    const int grid = grid_for(total_hint * gb_class_threads(cr.bra_cls, cr.ket_cls, prec), tc.block, tc.qpt, h->nsm);
     ProfRec* pr = nullptr;
     if (g_opt.profile) {
         h->prof.emplace_back();
@@ -1121,8 +1114,9 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     } else {
         const int ncr = (int)h->rows.size();
         if ((rc = h->split_tot.alloc(sizeof(long long) * 2 * std::max(1, ncr)))) return rc;
+        if ((rc = h->Df.alloc(sizeof(float) * (size_t)n * n))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
-        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>());
+        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>(), h->Df.as<float>());
         CKL();
         h->launches += 1;
         for (int k = 0; k < ncr; ++k) {
@@ -1221,8 +1215,11 @@ __global__ void k_absmax_batched(const gb::BatchMol* bm, unsigned long long* out
     const gb::BatchMol& m = bm[blockIdx.y];
     const long long n2 = (long long)m.nbf * m.nbf;
     double v = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
-        v = fmax(v, fabs(m.D[i]));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        const double x = m.D[i];
+        v = fmax(v, fabs(x));
+        m.Df[i] = (float)x;  // FP32 copy for the digestion of FP32 quartets
+    }
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(v));
 }
@@ -1258,6 +1255,8 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
         if (h->device != P.device) return fail(JK_ERR_INVALID, "batched molecules on different devices");
         host[m].pairs = view_of(h);
         host[m].D = P.D[m];
+        if (P.prec == JK_MIXED && (rc = h->Df.alloc(sizeof(float) * (size_t)h->nbf * h->nbf))) return rc;
+        host[m].Df = h->Df.as<float>();
         host[m].J = P.J[m];
         host[m].K = P.K[m];
         host[m].nbf = h->nbf;
@@ -1345,7 +1344,8 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     a.row_mol = bc.rowmol.as<int>();
     const TuneCfg& tc = bc.tune[prec];
     int nsm = P.mols[0]->nsm;
-    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(bc.total, tc.block, tc.qpt, nsm), tc.block, s);
+    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(bc.total * gb_class_threads(bc.X, bc.Y, prec), tc.block, tc.qpt, nsm),
+                               tc.block, s);
     if (e) return fail(JK_ERR_CUDA, std::string("batched ERI launch: ") + cudaGetErrorString((cudaError_t)e));
     P.launches += 1;
     return 0;
@@ -1460,6 +1460,15 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
 // when no class improves.  Timed on a prefix of each class's rows (about an
 // eighth, at least 2^21 quartets) with CUDA events; J and K are scratch.
 int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec, cudaStream_t st) {
+    if (prec == 1) {  // the FP32 kernels digest with the FP32 copy of D
+        int rc;
+        const long long n2 = (long long)h->nbf * h->nbf;
+        if ((rc = h->Df.alloc(sizeof(float) * n2))) return rc;
+        if ((rc = h->scratch.alloc(64))) return rc;
+        CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
+        k_absmax<<<152 * 4, 256, 0, st>>>(D, n2, h->scratch.as<unsigned long long>(), h->Df.as<float>());
+        CKL();
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1643,6 +1652,12 @@ int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* 
     CK(cudaGetDevice(&dev));
     if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    {
+        const int gl = gb_grad_lmax(), gcls = (gl + 1) * (gl + 2) / 2;
+        for (const ClassRows& cr : h->rows)
+            if (cr.total > 0 && cr.bra_cls >= gcls)
+                return fail(JK_ERR_UNSUPPORTED, "gradients are compiled for shells up to l = " + std::to_string(gl));
+    }
     // both precisions run the FP64 derivative kernels
     CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * h->natom, st));
     h->launches = 0;
@@ -1806,6 +1821,48 @@ int jk_class_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
             int64_t* r = rows + 6 * k;
             r[0] = cr.bra_cls; r[1] = cr.ket_cls; r[2] = cr.total; r[3] = cr.nprimq; r[4] = cr.nbrap;
             r[5] = (int64_t)fq * cr.nprimq + (int64_t)fb * cr.nbrap;
+        }
+        ++k;
+    }
+    *nrows = k;
+    return JK_OK;
+}
+
+int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
+    g_err.clear();
+    if (!h || !nrows || (max_rows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    if (h->last_prec != JK_MIXED) return fail(JK_ERR_INVALID, "the last jk_build on this handle was not mixed");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    CK(cudaDeviceSynchronize());  // the build may have run on any stream
+    DevBuf acc;
+    int rc;
+    if ((rc = acc.alloc(4 * sizeof(unsigned long long)))) return rc;
+    int k = 0;
+    for (const ClassRows& cr : h->rows) {
+        if (cr.total <= 0) continue;
+        if (k < max_rows) {
+            // per-row split counts: c32/c64 (nrows entries), kets k32/ket0
+            CK(cudaMemset(acc.p, 0, 4 * sizeof(unsigned long long)));
+            k_rows_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c32.as<long long>(), cr.bra.as<int>(), cr.k32.as<int>(),
+                                                       cr.nrows, h->info.as<int4>(), h->npre.as<long long>(),
+                                                       acc.as<unsigned long long>());
+            k_rows_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c64.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                       cr.nrows, h->info.as<int4>(), h->npre.as<long long>(),
+                                                       acc.as<unsigned long long>() + 2);
+            CKL();
+            unsigned long long v[4];
+            long long q2[2];
+            CK(cudaMemcpy(v, acc.p, sizeof(v), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(q2, cr.s32.as<long long>() + cr.nrows, sizeof(long long), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(q2 + 1, cr.s64.as<long long>() + cr.nrows, sizeof(long long), cudaMemcpyDeviceToHost));
+            int fq = 0, fb = 0;
+            gb_class_flops(cr.bra_cls, cr.ket_cls, &fq, &fb);
+            int64_t* r = rows + 8 * k;
+            r[0] = cr.bra_cls; r[1] = cr.ket_cls;
+            r[2] = q2[0]; r[3] = (int64_t)v[0]; r[4] = (int64_t)fq * (int64_t)v[0] + (int64_t)fb * (int64_t)v[1];
+            r[5] = q2[1]; r[6] = (int64_t)v[2]; r[7] = (int64_t)fq * (int64_t)v[2] + (int64_t)fb * (int64_t)v[3];
         }
         ++k;
     }

@@ -86,3 +86,59 @@ def test_mixed_precision_within_target(g):
     Jo, Ko, _ = oracle.jk(mol, D, thresh=1e-10, mode="unique")
     assert np.abs(J - Jo).max() <= 1e-6 and np.abs(K - Ko).max() <= 1e-6
     assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-6
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(21, [3], 2, 2), (22, [0, 3], 2, 2), (23, [1, 3], 2, 2),
+                                                    (24, [2, 3], 2, 2), (25, [3, 3, 0], 2, 1),
+                                                    (26, [0, 1, 2, 3], 2, 2)])
+def test_f_classes_fp64(g, seed, shells, natom, kmax):
+    """Every class with an f shell (the ket-component-chunked kernels), FP64,
+    against the oracle's Obara-Saika/HRR J and K."""
+    mol = molgen.random_molecule(100 + seed, natom, shells, 1, kmax, 0.1, 200.0, layout="lattice", spacing=1.9)
+    D = molgen.density(mol, 200 + seed)
+    pairs, J, K, E = _run(g, mol, D)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    scale = max(1.0, np.abs(Jo).max())
+    assert np.abs(J - Jo).max() <= FP64_TOL * scale, np.abs(J - Jo).max()
+    assert np.abs(K - Ko).max() <= FP64_TOL * scale, np.abs(K - Ko).max()
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= FP64_TOL * max(1.0, abs(E))
+
+
+def test_f_classes_mixed(g):
+    mol = molgen.random_molecule(31, 3, [0, 1, 2, 3], 1, 3, 0.05, 1e3, layout="lattice", spacing=2.6)
+    D = molgen.density(mol, 32)
+    pairs, J, K, E = _run(g, mol, D, 1e-11, "mixed")
+    n32, n64 = g.last_split(pairs)
+    assert n32 > 0 and n32 + n64 == pairs.nquartets
+    Jo, Ko, _ = oracle.jk(mol, D, thresh=1e-11, mode="unique")
+    assert np.abs(J - Jo).max() <= 1e-6 and np.abs(K - Ko).max() <= 1e-6
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-6
+
+
+def test_gradient_rejects_f_shells(g):
+    mol = molgen.random_molecule(33, 2, [0, 3], 1, 1, 0.5, 5.0, layout="lattice", spacing=2.0)
+    pairs = g.ShellPairs(mol)
+    D = torch.from_numpy(molgen.density(mol, 34)).cuda()
+    with pytest.raises(g.JKError) as e:
+        g.jk_grad(pairs, D, "fp64")
+    assert e.value.code == -5
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(41, [0, 1, 2], 3, 3), (42, [2, 2, 1], 2, 4), (43, [2, 0, 1, 2], 3, 2)])
+def test_all_fp32_kernels_against_oracle(g, seed, shells, natom, kmax):
+    """Every quartet through the FP32 kernels (cutoff above every bound): the
+    per-class FP32 code, whatever its thread mapping, agrees with the oracle
+    to FP32 accuracy (an indexing slip would be an O(1) error)."""
+    mol = molgen.random_molecule(500 + seed, natom, shells, 1, kmax, 0.05, 5e3, layout="lattice", spacing=2.2)
+    D = molgen.density(mol, 600 + seed)
+    old = g.get_option("mixed_tau")
+    g.set_option("mixed_tau", 1e300)
+    try:
+        pairs, J, K, E = _run(g, mol, D, None, "mixed")
+        n32, n64 = g.last_split(pairs)
+    finally:
+        g.set_option("mixed_tau", old)
+    assert n64 == 0 and n32 == pairs.nquartets
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    assert np.abs(J - Jo).max() <= 2e-6 * np.abs(Jo).max(), np.abs(J - Jo).max() / np.abs(Jo).max()
+    assert np.abs(K - Ko).max() <= 2e-6 * np.abs(Ko).max(), np.abs(K - Ko).max() / np.abs(Ko).max()
