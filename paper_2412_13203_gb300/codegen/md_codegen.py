@@ -326,7 +326,7 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     if not mode_flat:
         E(f"{real} Xl[{HAB * NCD}];")
         E(f"{real} Rc[{L1 * L1 * L1}];")
-    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
     if f32:
         # P - A, P - B and A - C were formed in FP64 and rounded once
         E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
@@ -568,7 +568,7 @@ def gen_quartet_body_chunk(bra, ket, real):
     E(f"{real} Rc[{L1 * L1 * L1}];")
     E(f"{real} Ebp[{S_ab}];")
     E(f"const int cx = c_comp_{lc}[3 * ci], cy = c_comp_{lc}[3 * ci + 1], cz = c_comp_{lc}[3 * ci + 2];")
-    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
     if f32:
         E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
         E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
@@ -704,6 +704,18 @@ def cd_table(lc, ld):
     return f"static __device__ __constant__ int c_cd_tab_{lc}{ld}[{len(rows)}] = {{{', '.join(map(str, rows))}}};"
 
 
+def split_of(bra, ket):
+    """Most threads one shell quartet's bra primitive pairs are spread over:
+    heavy classes are split so that the launch balances over quartets of very
+    different primitive counts (1 to K^4); light ones are not (each part
+    digests its partial block, which costs more than it saves there)."""
+    if use_chunk(bra, ket):
+        return 1
+    c = quartet_counts(bra, ket)
+    work = c["xket"] + 3 * c["R"]
+    return 8 if work >= 1000 else (4 if work >= 300 else 1)
+
+
 def gen_class_kernels(bra, ket):
     la, lb = bra
     lc, ld = ket
@@ -711,6 +723,7 @@ def gen_class_kernels(bra, ket):
     flat = use_flat(bra, ket)
     chunk = use_chunk(bra, ket)
     nch = nc if chunk else 1  # threads per shell quartet
+    P = split_of(bra, ket)    # bra primitive pairs of a quartet spread over up to P threads
     out = []
     stats = None
     for prec, real in (("f64", "double"), ("f32", "float")):
@@ -737,7 +750,12 @@ def gen_class_kernels(bra, ket):
 __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs args) {{
   // persistent grid-stride loop over the quartets of this launch; the total is
   // read on the device (last entry of the row prefix) so launches need no host sync
-  // ({nch} thread(s) per shell quartet: one per Cartesian component of the ket's first shell)
+  // Work items: rows.start is the prefix of items per row, a row's quartet
+  // being split into min({P}, K_ab) items over its bra primitive pairs; each
+  // item runs as {nch} thread(s) (one per Cartesian component of the ket's
+  // first shell).  Items are taken from the end: the rows are ordered by
+  // ascending ket primitive count, so the heaviest work goes first and the
+  // tail of the launch is light.
   const long long total = args.rows.start[args.rows.nrows] * {nch};
   const double* __restrict__ boys = args.boys;
   const float* __restrict__ boysf = args.boysf;
@@ -745,11 +763,14 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs arg
   (void)boysf; (void)tsmall;
   for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {{
-  const long long qt = tid / {nch};
-  const int ci = (int)(tid - qt * {nch});
+  const long long rt = total - 1 - tid;
+  const long long qt = rt / {nch};
+  const int ci = (int)(rt - qt * {nch});
   (void)ci;
-  int bra, ket, row;
-  gb::locate_quartet(args.rows, qt, bra, ket, row);
+  int row;
+  long long li;
+  gb::locate_row(args.rows, qt, row, li);
+  const int bra = __ldg(args.rows.bra + row);
   gb::PairsView pairs = args.pairs;
   const double* Dm = args.D;
   const float* Dfm = args.Df;
@@ -761,7 +782,12 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs arg
     const gb::BatchMol& bm = args.mols[args.row_mol[row]];
     pairs = bm.pairs; Dm = bm.D; Dfm = bm.Df; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
   }}
-  const int4 ib = pairs.info[bra], ik = pairs.info[ket];
+  const int4 ib = pairs.info[bra];
+  const int nsplit = min({P}, ib.z);
+  const long long qo = li / nsplit;
+  const int ipart = (int)(li - qo * nsplit);
+  const int ket = __ldg(args.rows.ket0 + row) + (int)qo;
+  const int4 ik = pairs.info[ket];
 {centres}
 {indent(body)}
   {real} s = 1;
@@ -790,6 +816,7 @@ __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArg
   const float tsmall = 0.f;
   (void)boysf; (void)tsmall;
   const int4 ib = pairs.info[bra], ik = ib;
+  const int ipart = 0, nsplit = 1;
   const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
 {indent(body)}
   double m = 0.0;
@@ -809,6 +836,7 @@ __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArg
   const float tsmall = 0.f;
   (void)boysf; (void)tsmall;
   const int4 ib = pairs.info[bra], ik = ib;
+  const int ipart = 0, nsplit = 1;
   const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
 {indent(body_f64_for_schwarz(bra, ket))}
   sa.Q[i] = gb::schwarz_from_block<{na * nb}>(acc);
@@ -1174,6 +1202,12 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
             rows_.append("{" + ", ".join(row) + "}")
         thr.append("{" + ", ".join(rows_) + "}")
     d.append(f"static const int k_threads_tab[2][{n}][{n}] = {{{', '.join(thr)}}};")
+    spl = []
+    for i in range(n):
+        spl.append("{" + ", ".join(str(split_of(pcs[i], pcs[j]) if j <= i else 1) for j in range(n)) + "}")
+    d.append(f"static const int k_split_tab[{n}][{n}] = {{{', '.join(spl)}}};")
+    d.append("// most work items one shell quartet of a class is split into (over its bra primitive pairs)")
+    d.append("int gb_class_split(int bra_cls, int ket_cls) { return k_split_tab[bra_cls][ket_cls]; }")
     d.append("// threads per shell quartet of a class kernel (prec 0: FP64, 1: FP32)")
     d.append("int gb_class_threads(int bra_cls, int ket_cls, int prec) { return k_threads_tab[prec][bra_cls][ket_cls]; }")
     d.append(f"static const jk_launch_fn k_jk_tab[{n}][{n}] = {{{', '.join(tab)}}};")

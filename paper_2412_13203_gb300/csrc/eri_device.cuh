@@ -162,6 +162,18 @@ __device__ __forceinline__ void boys_mixed(float T, float* F, const double* __re
 }
 
 // ------------------------------------------------------------------ rows
+// Row r of work item t (the largest r with start[r] <= t < start[nrows]) and
+// the item's offset li = t - start[r] inside the row.
+__device__ __forceinline__ void locate_row(const RowsView& rv, long long t, int& row, long long& li) {
+    int lo = 0, hi = rv.nrows;  // invariant: start[lo] <= t < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(rv.start + mid) <= t) lo = mid; else hi = mid;
+    }
+    row = lo;
+    li = t - __ldg(rv.start + lo);
+}
+
 // Largest r with start[r] <= t (t < start[nrows]).
 __device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, int& bra, int& ket, int& row) {
     int lo = 0, hi = rv.nrows;  // invariant: start[lo] <= t < start[hi]

@@ -35,6 +35,7 @@ int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap);
 int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s);
 int gb_grad_lmax();
 int gb_class_threads(int bra_cls, int ket_cls, int prec);
+int gb_class_split(int bra_cls, int ket_cls);
 extern "C" int gb_num_pair_classes();
 
 namespace {
@@ -105,8 +106,11 @@ struct ClassRows {
     long long nprimq = 0;
     long long nbrap = 0;
     DevBuf start, bra, ket0;
-    // mixed-precision split (filled on the device by jk_build)
-    DevBuf s64, s32, k32, c64, c32, scr;
+    DevBuf istart;      // prefix of work items per row (a quartet splits into min(P, K_ab) items)
+    long long itotal = 0;
+    // mixed-precision split (filled on the device by jk_build): quartet counts
+    // c64/c32, item counts w64/w32 and their prefixes s64/s32, FP32 ket starts k32
+    DevBuf s64, s32, k32, c64, c32, w64, w32, scr;
     TuneCfg tune[2];  // per precision (0 FP64 kernels, 1 FP32 kernels)
 };
 
@@ -154,7 +158,7 @@ struct jk_pairs_s {
     int nsm = 152;
     int last_prec = 0;
     int tuned[2] = {0, 0};
-    DevBuf split_tot;                               // per class: FP32 and FP64 quartets of the last mixed build
+    DevBuf split_tot;                               // per class: FP32, FP64 quartets, FP32, FP64 items (last mixed build)
     DevBuf npre;                                    // exclusive prefix of primitive pairs over the kept pairs
     DevBuf scratch;                                 // small reductions
     std::vector<ProfRec> prof;
@@ -540,9 +544,11 @@ __global__ void k_np_of(const int4* info, long long n, long long* np) {
 
 // Mixed split of every row: kets with Q_i Q_j max|D| >= tau stay FP64 (they lead, Q descending).
 __global__ void k_rows_split(const long long* start, const int* rbra, const int* rket0, int nrows, const double4* A,
-                             const double* dmax, double tau, long long* c64, long long* c32, int* k32) {
+                             const double* dmax, double tau, long long* c64, long long* c32, int* k32,
+                             const int4* info, int P, long long* w64, long long* w32, unsigned long long* qtot) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
+    const long long m = min(P, info[rbra[r]].z);
     const long long c = start[r + 1] - start[r];
     const int s = rket0[r];
     const double qi = A[rbra[r]].w * (*dmax);
@@ -554,6 +560,20 @@ __global__ void k_rows_split(const long long* start, const int* rbra, const int*
     c64[r] = lo - s;
     c32[r] = c - (lo - s);
     k32[r] = lo;
+    w64[r] = (lo - s) * m;
+    w32[r] = (c - (lo - s)) * m;
+    atomicAdd(qtot, (unsigned long long)(c - (lo - s)));
+    atomicAdd(qtot + 1, (unsigned long long)(lo - s));
+}
+
+// Work items of every row: quartets x min(P, K_ab) (bra primitive pairs of the
+// row's bra pair; batched rows look the pair up in their molecule).
+__global__ void k_row_items(const long long* start, const int* rbra, int nrows, const int4* info,
+                            const gb::BatchMol* bm, const int* rowmol, int P, long long* w) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int4* inf = bm ? bm[rowmol[r]].pairs.info : info;
+    w[r] = (start[r + 1] - start[r]) * (long long)min(P, inf[rbra[r]].z);
 }
 
 // max |x| (as the bit pattern of a non-negative double) and, if xf is not
@@ -992,12 +1012,23 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
                                                               cr.nrows, h->info.as<int4>(), d_npre.as<long long>(),
                                                               d_primq.as<unsigned long long>());
             CKL();
-            long long tot = 0;
+            // work items of the FP64 launch (the counts buffer is reused once primq has read it)
+            if ((rc = cr.istart.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+            k_row_items<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.nrows,
+                                                             h->info.as<int4>(), nullptr, nullptr,
+                                                             gb_class_split(X, Y), d_cnt.as<long long>());
+            CKL();
+            if ((rc = scan_exclusive(d_cnt.as<long long>(), cr.istart.as<long long>(), cr.nrows + 1,
+                                     d_tot.as<long long>() + 3, st)))
+                return rc;
+            long long tot = 0, itot = 0;
             unsigned long long pq2[2] = {0, 0};
             CK(cudaMemcpyAsync(&tot, d_tot.as<long long>() + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&itot, d_tot.as<long long>() + 3, sizeof(long long), cudaMemcpyDeviceToHost, st));
             CK(cudaMemcpyAsync(pq2, d_primq.p, sizeof(pq2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             cr.total = tot;
+            cr.itotal = itot;
             cr.nprimq = (long long)pq2[0];
             cr.nbrap = (long long)pq2[1];
             h->nquartets += tot;
@@ -1060,25 +1091,31 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
 }
 
 // Mixed split of one class: FP64 rows (s64, ket0) and FP32 rows (s32, k32),
-// computed on the device; the split totals land in split_tot[0..1].
+// computed on the device; split_tot[0..3] (zeroed by the caller) receives
+// the FP32 and FP64 quartet totals and the FP32 and FP64 work-item totals.
 int split_class(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* split_tot, cudaStream_t st) {
     int rc;
     const long long n1 = cr.nrows + 1;
     if ((rc = cr.c64.alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.c32.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.w64.alloc(sizeof(long long) * n1))) return rc;
+    if ((rc = cr.w32.alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.s64.alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.s32.alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
     if ((rc = cr.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
     k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
                                                       cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
-                                                      cr.c64.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>());
+                                                      cr.c64.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>(),
+                                                      h->info.as<int4>(), gb_class_split(cr.bra_cls, cr.ket_cls),
+                                                      cr.w64.as<long long>(), cr.w32.as<long long>(),
+                                                      reinterpret_cast<unsigned long long*>(split_tot));
     CKL();
-    CK(cudaMemsetAsync(cr.c64.as<long long>() + cr.nrows, 0, 8, st));
-    CK(cudaMemsetAsync(cr.c32.as<long long>() + cr.nrows, 0, 8, st));
-    if ((rc = scan_into(cr.c64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 1, cr.scr.as<long long>(), st)))
+    CK(cudaMemsetAsync(cr.w64.as<long long>() + cr.nrows, 0, 8, st));
+    CK(cudaMemsetAsync(cr.w32.as<long long>() + cr.nrows, 0, 8, st));
+    if ((rc = scan_into(cr.w64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 3, cr.scr.as<long long>(), st)))
         return rc;
-    if ((rc = scan_into(cr.c32.as<long long>(), cr.s32.as<long long>(), n1, split_tot, cr.scr.as<long long>(), st)))
+    if ((rc = scan_into(cr.w32.as<long long>(), cr.s32.as<long long>(), n1, split_tot + 2, cr.scr.as<long long>(), st)))
         return rc;
     h->launches += 1 + 2 * scan_launches(n1);
     return 0;
@@ -1110,10 +1147,12 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     h->last_prec = prec;
     if (prec == JK_FP64) {
         for (const ClassRows& cr : h->rows)
-            if ((rc = launch_class(h, cr, 0, cr.start.as<long long>(), cr.ket0.as<int>(), cr.total, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), cr.itotal, D, J, K, st)))
+                return rc;
     } else {
         const int ncr = (int)h->rows.size();
-        if ((rc = h->split_tot.alloc(sizeof(long long) * 2 * std::max(1, ncr)))) return rc;
+        if ((rc = h->split_tot.alloc(sizeof(long long) * 4 * std::max(1, ncr)))) return rc;
+        CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * 4 * std::max(1, ncr), st));
         if ((rc = h->Df.alloc(sizeof(float) * (size_t)n * n))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
         k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>(), h->Df.as<float>());
@@ -1123,10 +1162,10 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
             ClassRows& cr = h->rows[k];
             if (cr.total <= 0) continue;
             if ((rc = split_class(h, cr, reinterpret_cast<const double*>(h->scratch.p),
-                                  h->split_tot.as<long long>() + 2 * k, st)))
+                                  h->split_tot.as<long long>() + 4 * k, st)))
                 return rc;
-            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.total, D, J, K, st))) return rc;
-            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.total, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.itotal, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st))) return rc;
         }
     }
     const long long tri = (long long)n * (n + 1) / 2;
@@ -1149,7 +1188,8 @@ struct BatchClass {
     int X = 0, Y = 0, nrows = 0;
     long long total = 0;
     DevBuf start, bra, ket0, rowmol;
-    DevBuf s64, s32, k32, c64, c32, scr;
+    DevBuf istart, itot;  // work-item prefix of the FP64 launch, its total
+    DevBuf s64, s32, k32, c64, c32, w64, w32, scr;
     TuneCfg tune[2];
 };
 
@@ -1226,10 +1266,12 @@ __global__ void k_absmax_batched(const gb::BatchMol* bm, unsigned long long* out
 
 __global__ void k_rows_split_batched(const long long* start, const int* rbra, const int* rket0, const int* rowmol,
                                      int nrows, const gb::BatchMol* bm, const unsigned long long* dmax, double tau,
-                                     long long* c64, long long* c32, int* k32) {
+                                     long long* c64, long long* c32, int* k32, int P, long long* w64, long long* w32,
+                                     unsigned long long* qtot) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const int m = rowmol[r];
+    const long long ms = min(P, bm[m].pairs.info[rbra[r]].z);
     const double4* A = bm[m].pairs.A;
     const long long c = start[r + 1] - start[r];
     const int s = rket0[r];
@@ -1242,6 +1284,10 @@ __global__ void k_rows_split_batched(const long long* start, const int* rbra, co
     c64[r] = lo - s;
     c32[r] = c - (lo - s);
     k32[r] = lo;
+    w64[r] = (lo - s) * ms;
+    w32[r] = (c - (lo - s)) * ms;
+    atomicAdd(qtot, (unsigned long long)(c - (lo - s)));
+    atomicAdd(qtot + 1, (unsigned long long)(lo - s));
 }
 
 int build_plan(BatchPlan& P, cudaStream_t st) {
@@ -1308,17 +1354,33 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
                     }
             k_set_ll<<<1, 1, 0, st>>>(bc.start.as<long long>() + nrows, total);
             CKL();
+            {   // work items of the FP64 launch
+                DevBuf w;
+                if ((rc = w.alloc(sizeof(long long) * (nrows + 1)))) return rc;
+                if ((rc = bc.istart.alloc(sizeof(long long) * (nrows + 1)))) return rc;
+                if ((rc = bc.itot.alloc(sizeof(long long)))) return rc;
+                CK(cudaMemsetAsync(w.as<long long>() + nrows, 0, sizeof(long long), st));
+                k_row_items<<<nblk(nrows, 256), 256, 0, st>>>(bc.start.as<long long>(), bc.bra.as<int>(), nrows, nullptr,
+                                                              P.bm.as<gb::BatchMol>(), bc.rowmol.as<int>(),
+                                                              gb_class_split(X, Y), w.as<long long>());
+                CKL();
+                if ((rc = scan_exclusive(w.as<long long>(), bc.istart.as<long long>(), nrows + 1, bc.itot.as<long long>(),
+                                         st)))
+                    return rc;
+            }
             if (P.prec == JK_MIXED) {
                 const long long n1 = nrows + 1;
                 if ((rc = bc.c64.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.c32.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.w64.alloc(sizeof(long long) * n1))) return rc;
+                if ((rc = bc.w32.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.s64.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.s32.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.k32.alloc(sizeof(int) * nrows))) return rc;
                 if ((rc = bc.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
             }
         }
-    if ((rc = P.split_tot.alloc(sizeof(long long) * 2 * std::max<size_t>(1, P.cls.size())))) return rc;
+    if ((rc = P.split_tot.alloc(sizeof(long long) * 4 * std::max<size_t>(1, P.cls.size())))) return rc;
     CK(cudaStreamSynchronize(st));
     CK(cudaStreamCreateWithFlags(&P.cs, cudaStreamNonBlocking));
     for (auto& x : P.ps) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
@@ -1344,8 +1406,8 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     a.row_mol = bc.rowmol.as<int>();
     const TuneCfg& tc = bc.tune[prec];
     int nsm = P.mols[0]->nsm;
-    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(bc.total * gb_class_threads(bc.X, bc.Y, prec), tc.block, tc.qpt, nsm),
-                               tc.block, s);
+    const long long items = bc.total * gb_class_split(bc.X, bc.Y) * gb_class_threads(bc.X, bc.Y, prec);  // upper bound
+    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(items, tc.block, tc.qpt, nsm), tc.block, s);
     if (e) return fail(JK_ERR_CUDA, std::string("batched ERI launch: ") + cudaGetErrorString((cudaError_t)e));
     P.launches += 1;
     return 0;
@@ -1363,6 +1425,7 @@ int enqueue_batch(BatchPlan& P) {
     P.launches += 1;
     if (P.prec == JK_MIXED) {
         CK(cudaMemsetAsync(P.dmax.p, 0, sizeof(unsigned long long) * nmol, P.cs));
+        CK(cudaMemsetAsync(P.split_tot.p, 0, sizeof(long long) * 4 * std::max<size_t>(1, P.cls.size()), P.cs));
         k_absmax_batched<<<dim3(64, nmol), 256, 0, P.cs>>>(bm, P.dmax.as<unsigned long long>());
         CKL();
         P.launches += 1;
@@ -1373,19 +1436,21 @@ int enqueue_batch(BatchPlan& P) {
         BatchClass& bc = P.cls[k];
         cudaStream_t s = (k % 4 == 0) ? P.cs : P.ps[k % 4 - 1];
         if (P.prec == JK_FP64) {
-            if ((rc = launch_batch_class(P, bc, 0, bc.start.as<long long>(), bc.ket0.as<int>(), s))) return rc;
+            if ((rc = launch_batch_class(P, bc, 0, bc.istart.as<long long>(), bc.ket0.as<int>(), s))) return rc;
         } else {
             const long long n1 = bc.nrows + 1;
             k_rows_split_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(
                 bc.start.as<long long>(), bc.bra.as<int>(), bc.ket0.as<int>(), bc.rowmol.as<int>(), bc.nrows, bm,
-                P.dmax.as<unsigned long long>(), P.tau, bc.c64.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>());
+                P.dmax.as<unsigned long long>(), P.tau, bc.c64.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>(),
+                gb_class_split(bc.X, bc.Y), bc.w64.as<long long>(), bc.w32.as<long long>(),
+                reinterpret_cast<unsigned long long*>(P.split_tot.as<long long>() + 4 * k));
             CKL();
-            CK(cudaMemsetAsync(bc.c64.as<long long>() + bc.nrows, 0, 8, s));
-            CK(cudaMemsetAsync(bc.c32.as<long long>() + bc.nrows, 0, 8, s));
-            long long* tot = P.split_tot.as<long long>() + 2 * k;
-            if ((rc = scan_into(bc.c64.as<long long>(), bc.s64.as<long long>(), n1, tot + 1, bc.scr.as<long long>(), s)))
+            CK(cudaMemsetAsync(bc.w64.as<long long>() + bc.nrows, 0, 8, s));
+            CK(cudaMemsetAsync(bc.w32.as<long long>() + bc.nrows, 0, 8, s));
+            long long* tot = P.split_tot.as<long long>() + 4 * k;
+            if ((rc = scan_into(bc.w64.as<long long>(), bc.s64.as<long long>(), n1, tot + 3, bc.scr.as<long long>(), s)))
                 return rc;
-            if ((rc = scan_into(bc.c32.as<long long>(), bc.s32.as<long long>(), n1, tot, bc.scr.as<long long>(), s)))
+            if ((rc = scan_into(bc.w32.as<long long>(), bc.s32.as<long long>(), n1, tot + 2, bc.scr.as<long long>(), s)))
                 return rc;
             P.launches += 1 + 2 * scan_launches(n1);
             if ((rc = launch_batch_class(P, bc, 0, bc.s64.as<long long>(), bc.ket0.as<int>(), s))) return rc;
@@ -1477,8 +1542,8 @@ int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec
     for (ClassRows& cr : h->rows) {
         if (cr.total <= 0) continue;
         std::vector<long long> start(cr.nrows + 1);
-        CK(cudaMemcpy(start.data(), cr.start.p, sizeof(long long) * (cr.nrows + 1), cudaMemcpyDeviceToHost));
-        const long long target = std::max<long long>(cr.total / 8, 1LL << 21);
+        CK(cudaMemcpy(start.data(), cr.istart.p, sizeof(long long) * (cr.nrows + 1), cudaMemcpyDeviceToHost));
+        const long long target = std::max<long long>(cr.itotal / 8, 1LL << 21);
         int r = (int)(std::lower_bound(start.begin(), start.end(), target) - start.begin());
         r = std::min(std::max(r, 1), cr.nrows);
         items.push_back({&cr, r, start[r]});
@@ -1488,7 +1553,7 @@ int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec
         int rc;
         for (int rep = 0; rep < 2; ++rep) {  // first run warms caches and clocks
             CK(cudaEventRecord(e0, st));
-            if ((rc = launch_class(h, *it.cr, prec, it.cr->start.as<long long>(), it.cr->ket0.as<int>(), it.total, D,
+            if ((rc = launch_class(h, *it.cr, prec, it.cr->istart.as<long long>(), it.cr->ket0.as<int>(), it.total, D,
                                    J, K, st, nullptr, nullptr, it.nrows)))
                 return rc;
             CK(cudaEventRecord(e1, st));
@@ -1750,14 +1815,14 @@ int jk_last_split(jk_pairs h, int64_t* n32, int64_t* n64) {
     if (!h) return fail(JK_ERR_INVALID, "null handle");
     long long a = 0, b = h->nquartets;
     if (h->last_prec == JK_MIXED && h->split_tot.p) {
-        std::vector<long long> t(2 * h->rows.size());
+        std::vector<long long> t(4 * h->rows.size());
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(t.data(), h->split_tot.p, sizeof(long long) * t.size(), cudaMemcpyDeviceToHost));
         a = b = 0;
         for (size_t k = 0; k < h->rows.size(); ++k) {
             if (h->rows[k].total <= 0) continue;
-            a += t[2 * k];
-            b += t[2 * k + 1];
+            a += t[4 * k];
+            b += t[4 * k + 1];
         }
     }
     if (n32) *n32 = a;
@@ -1840,7 +1905,8 @@ int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
     int rc;
     if ((rc = acc.alloc(4 * sizeof(unsigned long long)))) return rc;
     int k = 0;
-    for (const ClassRows& cr : h->rows) {
+    for (size_t ri = 0; ri < h->rows.size(); ++ri) {
+        const ClassRows& cr = h->rows[ri];
         if (cr.total <= 0) continue;
         if (k < max_rows) {
             // per-row split counts: c32/c64 (nrows entries), kets k32/ket0
@@ -1855,8 +1921,7 @@ int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
             unsigned long long v[4];
             long long q2[2];
             CK(cudaMemcpy(v, acc.p, sizeof(v), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(q2, cr.s32.as<long long>() + cr.nrows, sizeof(long long), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(q2 + 1, cr.s64.as<long long>() + cr.nrows, sizeof(long long), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(q2, h->split_tot.as<long long>() + 4 * ri, 2 * sizeof(long long), cudaMemcpyDeviceToHost));
             int fq = 0, fb = 0;
             gb_class_flops(cr.bra_cls, cr.ket_cls, &fq, &fb);
             int64_t* r = rows + 8 * k;
