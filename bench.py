@@ -256,11 +256,9 @@ def main():
     t_mx = sum(ms_mx) / len(ms_mx)
     t_64 = sum(ms64) / len(ms64)
     t_e2e = sum(e2e) / len(e2e)
-    # max over ranks
-    vals = torch.tensor([t_mx, t_64, t_e2e], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    t_mx, t_64, t_e2e = [float(x) for x in vals.cpu()]
+    # max over ranks (each rank ran its own copy of the workload: weak scaling)
+    from paper_2412_13203_gb300 import shard
+    t_mx, t_64, t_e2e = shard.max_over_ranks([t_mx, t_64, t_e2e], device=dev)
 
     # roofline of the dominant kernel of the mixed build: algorithmic operations
     # of the generated code for the quartets that launch processed / its

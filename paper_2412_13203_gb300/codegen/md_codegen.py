@@ -339,13 +339,6 @@ def gen_quartet_body(bra, ket, real, mode_flat):
         E(f"const {real} p = pa.w, kp = pb.x, inv2p = pb.y;")
         E(f"const {real} PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
         E(f"const {real} PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
-    inv2p = Sym(name="inv2p")
-    Ebx = gen_E_axis(em, "ebx", la, lb, Sym(name="PAx"), Sym(name="PBx"), inv2p)
-    Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
-    Ebz = gen_E_axis(em, "ebz", la, lb, Sym(name="PAz"), Sym(name="PBz"), inv2p)
-    flops_ebra = em.flops
-    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz, Sym(name="kp") if f32 else None)
-    flops_ebra = em.flops - 0  # total so far (per bra primitive)
     # X accumulators
     if mode_flat:
         for h in range(HAB):
@@ -446,6 +439,15 @@ def gen_quartet_body(bra, ket, real, mode_flat):
         em.flops += 2 * cnt["xket"]
     flops_x = em.flops
     E("}  // ket primitives")
+    # bra E coefficients and products, emitted after the ket loop so that
+    # they hold no registers while it runs
+    em.flops = 0
+    inv2p = Sym(name="inv2p")
+    Ebx = gen_E_axis(em, "ebx", la, lb, Sym(name="PAx"), Sym(name="PBx"), inv2p)
+    Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
+    Ebz = gen_E_axis(em, "ebz", la, lb, Sym(name="PAz"), Sym(name="PBz"), inv2p)
+    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz, Sym(name="kp") if f32 else None)
+    flops_ebra = em.flops
     # bra transform
     em.flops = 0
     if mode_flat:
@@ -786,7 +788,8 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs arg
   const int nsplit = min({P}, ib.z);
   const long long qo = li / nsplit;
   const int ipart = (int)(li - qo * nsplit);
-  const int ket = __ldg(args.rows.ket0 + row) + (int)qo;
+  const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)
+                                  : __ldg(args.rows.ket0 + row) + (int)qo;
   const int4 ik = pairs.info[ket];
 {centres}
 {indent(body)}

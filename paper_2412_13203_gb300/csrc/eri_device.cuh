@@ -41,9 +41,11 @@ struct PairsView {
 
 struct RowsView {
     int nrows;
-    const long long* start;  // [nrows + 1], exclusive prefix of the per-row quartet counts
+    const long long* start;  // [nrows + 1], exclusive prefix of the per-row work items
     const int* bra;          // bra pair of every row
-    const int* ket0;         // first ket pair of every row (kets are contiguous)
+    const int* ket0;         // first ket pair of every row (kets are contiguous) ...
+    const long long* kofs;   // ... or, if klist is set, the row's first entry in klist
+    const int* klist;        // explicit ket pairs (rows of a mixed build's FP64 / demoted lists)
 };
 
 // One molecule of a batched launch.

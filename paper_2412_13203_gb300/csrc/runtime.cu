@@ -92,6 +92,7 @@ struct DevBuf {
 };
 
 constexpr int kMaxClasses = 10;  // pair classes for l <= 3
+constexpr int kSplitSlots = 8;   // per class: FP32 q, FP64 q, FP32/FP64/demoted item totals, list totals
 constexpr int kNB = 128;         // primitive-pair-count buckets (exact count, 128+ share the last)
 
 struct TuneCfg {
@@ -108,9 +109,13 @@ struct ClassRows {
     DevBuf start, bra, ket0;
     DevBuf istart;      // prefix of work items per row (a quartet splits into min(P, K_ab) items)
     long long itotal = 0;
-    // mixed-precision split (filled on the device by jk_build): quartet counts
-    // c64/c32, item counts w64/w32 and their prefixes s64/s32, FP32 ket starts k32
+    // mixed-precision split (filled on the device by jk_build).  Per row: the
+    // kets of the global-bound FP64 prefix are listed explicitly -- FP64 ones
+    // (c64 quartets, w64 items, item prefix s64, list offsets l64) and demoted
+    // ones (cdem, wdem, sdem, ldem) -- and the FP32 suffix stays contiguous
+    // (c32, w32, s32, ket starts k32).
     DevBuf s64, s32, k32, c64, c32, w64, w32, scr;
+    DevBuf cdem, wdem, sdem, l64, ldem;
     TuneCfg tune[2];  // per precision (0 FP64 kernels, 1 FP32 kernels)
 };
 
@@ -147,6 +152,11 @@ struct jk_pairs_s {
     DevBuf Df;                                      // FP32 copy of the last mixed build's D
     DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
     DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
+    DevBuf pair_sh;                                 // int2 per pair: shells a, b (caller's order)
+    DevBuf bf_shell;                                // int per basis function: its shell
+    DevBuf Dsh;                                     // float [nshell^2]: max |D| per shell block (mixed)
+    DevBuf list64, listdem;                         // mixed: FP64 and demoted (FP32) ket lists
+    std::vector<long long> list_off64, list_offd;   // per class: first entry in list64 / listdem
     DevBuf pair_lab;                                // int2 per pair: la, lb
     DevBuf xyz;                                     // atoms
     std::vector<int> cls_start;                     // [ncls + 1] pair ranges per class
@@ -395,7 +405,7 @@ __global__ void k_pair_count(ShellDev S, long long npair, long long* nprimpair, 
 
 __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, int4* info, double4* A, double4* B,
                             int2* atoms, int2* lab, double4* pp, double2* pp2, float4* ppf, float4* ppf2,
-                            double* alpha) {
+                            double* alpha, int2* sh) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair) return;
     int i, j, a, b;
@@ -412,6 +422,7 @@ __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, 
     B[k] = make_double4(Rb[0], Rb[1], Rb[2], 0.0);
     atoms[k] = make_int2(S.atom[a], S.atom[b]);
     lab[k] = make_int2(S.l[a], S.l[b]);
+    sh[k] = make_int2(a, b);
     const double s2pi52 = 5.9149671727956128778;  // sqrt(2 pi^(5/2))
     int n = 0;
     for (int u = 0; u < ka; ++u)
@@ -543,27 +554,93 @@ __global__ void k_np_of(const int4* info, long long n, long long* np) {
 }
 
 // Mixed split of every row: kets with Q_i Q_j max|D| >= tau stay FP64 (they lead, Q descending).
+// Max |D| over every shell block (non-negative floats order like their bits).
+__global__ void k_dsh(const double* D, int n, const int* bf_shell, int nshell, unsigned int* dsh) {
+    const long long n2 = (long long)n * n;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / n), j = (int)(k - (long long)i * n);
+        const float v = (float)fabs(D[k]);
+        atomicMax(dsh + (size_t)bf_shell[i] * nshell + bf_shell[j], __float_as_uint(v));
+    }
+}
+
+// The largest |D| block a quartet's J and K updates touch: D_ab and D_cd
+// (Coulomb), D_ac, D_ad, D_bc, D_bd (exchange).
+__device__ __forceinline__ float quartet_dmax(const float* dsh, int nshell, int2 ab, int2 cd) {
+    const float* r_a = dsh + (size_t)ab.x * nshell;
+    const float* r_b = dsh + (size_t)ab.y * nshell;
+    float m = fmaxf(r_a[ab.y], dsh[(size_t)cd.x * nshell + cd.y]);
+    m = fmaxf(m, fmaxf(r_a[cd.x], r_a[cd.y]));
+    return fmaxf(m, fmaxf(r_b[cd.x], r_b[cd.y]));
+}
+
+// Mixed split of every row.  Kets are sorted by Q descending, so the kets with
+// Q_i Q_j max|D| >= tau (global bound) are a prefix; inside that prefix a
+// quartet stays FP64 only if its density-weighted bound Q_i Q_j max(D blocks it
+// touches) >= tau, else it is demoted to FP32.  Writes per-row quartet and
+// work-item counts of the three parts and adds the FP32 / FP64 quartet totals.
 __global__ void k_rows_split(const long long* start, const int* rbra, const int* rket0, int nrows, const double4* A,
-                             const double* dmax, double tau, long long* c64, long long* c32, int* k32,
-                             const int4* info, int P, long long* w64, long long* w32, unsigned long long* qtot) {
+                             const double* dmax, double tau, const int4* info, const int2* psh, const float* dsh,
+                             int nshell, int P, long long* c64, long long* cdem, long long* c32, int* k32,
+                             long long* w64, long long* wdem, long long* w32, unsigned long long* qtot) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    const long long m = min(P, info[rbra[r]].z);
+    const int i = rbra[r];
+    const long long m = min(P, info[i].z);
     const long long c = start[r + 1] - start[r];
     const int s = rket0[r];
-    const double qi = A[rbra[r]].w * (*dmax);
+    const double qi = A[i].w;
+    const double qg = qi * (*dmax);
     int lo = s, hi = s + (int)c;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (qi * A[mid].w >= tau) lo = mid + 1; else hi = mid;
+        if (qg * A[mid].w >= tau) lo = mid + 1; else hi = mid;
     }
-    c64[r] = lo - s;
-    c32[r] = c - (lo - s);
+    const int2 ab = psh[i];
+    long long n64 = 0;
+    for (int j = s; j < lo; ++j)
+        if (qi * A[j].w * (double)quartet_dmax(dsh, nshell, ab, psh[j]) >= tau) ++n64;
+    const long long nd = (lo - s) - n64, n32 = c - (lo - s);
+    c64[r] = n64;
+    cdem[r] = nd;
+    c32[r] = n32;
     k32[r] = lo;
-    w64[r] = (lo - s) * m;
-    w32[r] = (c - (lo - s)) * m;
-    atomicAdd(qtot, (unsigned long long)(c - (lo - s)));
-    atomicAdd(qtot + 1, (unsigned long long)(lo - s));
+    w64[r] = n64 * m;
+    wdem[r] = nd * m;
+    w32[r] = n32 * m;
+    atomicAdd(qtot, (unsigned long long)(n32 + nd));
+    atomicAdd(qtot + 1, (unsigned long long)n64);
+    atomicAdd(qtot + 7, (unsigned long long)nd);
+}
+
+// Primitive quartets and (quartet x bra primitive pair) units of list rows.
+__global__ void k_list_primq(const long long* cnt, const long long* ofs, const int* klist, const int* rbra, int nrows,
+                             const int4* info, unsigned long long* acc) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long c = cnt[r];
+    if (c == 0) return;
+    long long kp = 0;
+    for (long long k = 0; k < c; ++k) kp += info[klist[ofs[r] + k]].z;
+    atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
+    atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
+}
+
+// Second pass: the kets of every row's FP64 prefix into the FP64 and demoted
+// lists, at the row offsets l64 / ldem (exclusive prefixes of c64 / cdem).
+__global__ void k_rows_fill(const int* rbra, const int* rket0, const int* k32, int nrows, const double4* A, double tau,
+                            const int2* psh, const float* dsh, int nshell, const long long* l64, const long long* ldem,
+                            int* list64, int* listdem) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int i = rbra[r];
+    const double qi = A[i].w;
+    const int2 ab = psh[i];
+    long long o64 = l64[r], od = ldem[r];
+    for (int j = rket0[r]; j < k32[r]; ++j) {
+        if (qi * A[j].w * (double)quartet_dmax(dsh, nshell, ab, psh[j]) >= tau) list64[o64++] = j;
+        else listdem[od++] = j;
+    }
 }
 
 // Work items of every row: quartets x min(P, K_ab) (bra primitive pairs of the
@@ -806,6 +883,12 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = upload(d_np, shells->nprim, S, st))) return rc;
     if ((rc = upload(d_off, shells->prim_offset, S, st))) return rc;
     if ((rc = upload(d_bf, bf.data(), S, st))) return rc;
+    {
+        std::vector<int> bsh(nbf);
+        for (int sh = 0; sh < S; ++sh)
+            for (int k = 0; k < (shells->l[sh] + 1) * (shells->l[sh] + 2) / 2; ++k) bsh[bf[sh] + k] = sh;
+        if ((rc = upload(h->bf_shell, bsh.data(), nbf, st))) return rc;
+    }
     if ((rc = upload(d_e, shells->exps, nprim_tot, st))) return rc;
     if ((rc = upload(d_c, shells->coefs, nprim_tot, st))) return rc;
     if ((rc = d_cn.alloc(sizeof(double) * nprim_tot))) return rc;
@@ -835,11 +918,12 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if (nprimpair > (long long)INT32_MAX) return fail(JK_ERR_UNSUPPORTED, "more than 2^31 primitive pairs");
     h->nprimpair = nprimpair;
     // unsorted pair arrays
-    DevBuf u_info, u_A, u_B, u_atoms, u_lab;
+    DevBuf u_info, u_A, u_B, u_atoms, u_lab, u_sh;
     if ((rc = u_info.alloc(sizeof(int4) * np))) return rc;
     if ((rc = u_A.alloc(sizeof(double4) * np))) return rc;
     if ((rc = u_B.alloc(sizeof(double4) * np))) return rc;
     if ((rc = u_atoms.alloc(sizeof(int2) * np))) return rc;
+    if ((rc = u_sh.alloc(sizeof(int2) * np))) return rc;
     if ((rc = u_lab.alloc(sizeof(int2) * np))) return rc;
     if ((rc = h->pp.alloc(sizeof(double4) * nprimpair))) return rc;
     if ((rc = h->pp2.alloc(sizeof(double2) * nprimpair))) return rc;
@@ -849,20 +933,22 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     k_pair_fill<<<nblk(np, 128), 128, 0, st>>>(SD, np, d_poff.as<long long>(), u_info.as<int4>(), u_A.as<double4>(),
                                                 u_B.as<double4>(), u_atoms.as<int2>(), u_lab.as<int2>(),
                                                 h->pp.as<double4>(), h->pp2.as<double2>(), h->ppf.as<float4>(),
-                                                h->ppf2.as<float4>(), h->alpha.as<double>());
+                                                h->ppf2.as<float4>(), h->alpha.as<double>(), u_sh.as<int2>());
     CKL();
     // ---- sort 1: by class, then Schwarz per class
     if ((rc = sort_pairs(d_key.as<unsigned long long>(), d_val.as<int>(), npad, st))) return rc;
-    DevBuf s_info, s_A, s_B, s_atoms, s_lab;
+    DevBuf s_info, s_A, s_B, s_atoms, s_lab, s_sh;
     if ((rc = s_info.alloc(sizeof(int4) * np))) return rc;
     if ((rc = s_A.alloc(sizeof(double4) * np))) return rc;
     if ((rc = s_B.alloc(sizeof(double4) * np))) return rc;
     if ((rc = s_atoms.alloc(sizeof(int2) * np))) return rc;
+    if ((rc = s_sh.alloc(sizeof(int2) * np))) return rc;
     if ((rc = s_lab.alloc(sizeof(int2) * np))) return rc;
     k_gather<int4><<<nblk(np, 256), 256, 0, st>>>(u_info.as<int4>(), d_val.as<int>(), s_info.as<int4>(), np);
     k_gather<double4><<<nblk(np, 256), 256, 0, st>>>(u_A.as<double4>(), d_val.as<int>(), s_A.as<double4>(), np);
     k_gather<double4><<<nblk(np, 256), 256, 0, st>>>(u_B.as<double4>(), d_val.as<int>(), s_B.as<double4>(), np);
     k_gather<int2><<<nblk(np, 256), 256, 0, st>>>(u_atoms.as<int2>(), d_val.as<int>(), s_atoms.as<int2>(), np);
+    k_gather<int2><<<nblk(np, 256), 256, 0, st>>>(u_sh.as<int2>(), d_val.as<int>(), s_sh.as<int2>(), np);
     k_gather<int2><<<nblk(np, 256), 256, 0, st>>>(u_lab.as<int2>(), d_val.as<int>(), s_lab.as<int2>(), np);
     CKL();
     const int ncls = gb_num_pair_classes();
@@ -927,12 +1013,14 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = h->A.alloc(sizeof(double4) * nk))) return rc;
     if ((rc = h->B.alloc(sizeof(double4) * nk))) return rc;
     if ((rc = h->pair_atoms.alloc(sizeof(int2) * nk))) return rc;
+    if ((rc = h->pair_sh.alloc(sizeof(int2) * nk))) return rc;
     if ((rc = h->pair_lab.alloc(sizeof(int2) * nk))) return rc;
     if (kept > 0) {
         k_gather<int4><<<nblk(kept, 256), 256, 0, st>>>(s_info.as<int4>(), d_val.as<int>(), h->info.as<int4>(), kept);
         k_gather<double4><<<nblk(kept, 256), 256, 0, st>>>(s_A.as<double4>(), d_val.as<int>(), h->A.as<double4>(), kept);
         k_gather<double4><<<nblk(kept, 256), 256, 0, st>>>(s_B.as<double4>(), d_val.as<int>(), h->B.as<double4>(), kept);
         k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_atoms.as<int2>(), d_val.as<int>(), h->pair_atoms.as<int2>(), kept);
+        k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_sh.as<int2>(), d_val.as<int>(), h->pair_sh.as<int2>(), kept);
         k_gather<int2><<<nblk(kept, 256), 256, 0, st>>>(s_lab.as<int2>(), d_val.as<int>(), h->pair_lab.as<int2>(), kept);
         CKL();
         k_quantise_q<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), kept);
@@ -1050,7 +1138,8 @@ int grid_for(long long total, int block, int qpt, int nsm) {
 
 int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
                  long long total_hint, const double* D, double* J, double* K, cudaStream_t st,
-                 const gb::BatchMol* mols = nullptr, const int* row_mol = nullptr, int nrows_override = -1) {
+                 const gb::BatchMol* mols = nullptr, const int* row_mol = nullptr, int nrows_override = -1,
+                 const long long* kofs = nullptr, const int* klist = nullptr) {
     if (total_hint <= 0) return 0;
     gb::JKArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1059,6 +1148,8 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.rows.start = start;
     a.rows.bra = cr.bra.as<int>();
     a.rows.ket0 = ket0;
+    a.rows.kofs = kofs;
+    a.rows.klist = klist;
     a.boys = g_boys[h->device].tab.as<double>();
     a.boysf = g_boys[h->device].tabf.as<float>();
     a.tsmall = (float)g_opt.tsmall;
@@ -1090,34 +1181,46 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     return 0;
 }
 
-// Mixed split of one class: FP64 rows (s64, ket0) and FP32 rows (s32, k32),
-// computed on the device; split_tot[0..3] (zeroed by the caller) receives
-// the FP32 and FP64 quartet totals and the FP32 and FP64 work-item totals.
-int split_class(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* split_tot, cudaStream_t st) {
+// Mixed split of one class, first phase (counts): per-row quartet and item
+// counts of the FP64 list, the demoted list and the FP32 suffix; the quartet
+// totals are added into split_tot[0..1] (FP32 incl. demoted, FP64).
+int split_count(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* split_tot, cudaStream_t st) {
     int rc;
     const long long n1 = cr.nrows + 1;
-    if ((rc = cr.c64.alloc(sizeof(long long) * n1))) return rc;
-    if ((rc = cr.c32.alloc(sizeof(long long) * n1))) return rc;
-    if ((rc = cr.w64.alloc(sizeof(long long) * n1))) return rc;
-    if ((rc = cr.w32.alloc(sizeof(long long) * n1))) return rc;
-    if ((rc = cr.s64.alloc(sizeof(long long) * n1))) return rc;
-    if ((rc = cr.s32.alloc(sizeof(long long) * n1))) return rc;
+    for (DevBuf* b : {&cr.c64, &cr.c32, &cr.cdem, &cr.w64, &cr.w32, &cr.wdem, &cr.s64, &cr.s32, &cr.sdem, &cr.l64,
+                      &cr.ldem})
+        if ((rc = b->alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
     if ((rc = cr.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
-    k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
-                                                      cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
-                                                      cr.c64.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>(),
-                                                      h->info.as<int4>(), gb_class_split(cr.bra_cls, cr.ket_cls),
-                                                      cr.w64.as<long long>(), cr.w32.as<long long>(),
-                                                      reinterpret_cast<unsigned long long*>(split_tot));
+    k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(
+        cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(), cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
+        h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell, gb_class_split(cr.bra_cls, cr.ket_cls),
+        cr.c64.as<long long>(), cr.cdem.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>(), cr.w64.as<long long>(),
+        cr.wdem.as<long long>(), cr.w32.as<long long>(), reinterpret_cast<unsigned long long*>(split_tot));
     CKL();
-    CK(cudaMemsetAsync(cr.w64.as<long long>() + cr.nrows, 0, 8, st));
-    CK(cudaMemsetAsync(cr.w32.as<long long>() + cr.nrows, 0, 8, st));
-    if ((rc = scan_into(cr.w64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 3, cr.scr.as<long long>(), st)))
-        return rc;
-    if ((rc = scan_into(cr.w32.as<long long>(), cr.s32.as<long long>(), n1, split_tot + 2, cr.scr.as<long long>(), st)))
-        return rc;
-    h->launches += 1 + 2 * scan_launches(n1);
+    for (DevBuf* b : {&cr.c64, &cr.c32, &cr.cdem, &cr.w64, &cr.w32, &cr.wdem})
+        CK(cudaMemsetAsync(b->as<long long>() + cr.nrows, 0, 8, st));
+    h->launches += 1;
+    return 0;
+}
+
+// Second phase: item prefixes (s64, sdem, s32; totals into split_tot[2..4]),
+// list offsets (l64, ldem; totals into split_tot[5..6]) and the list fill.
+int split_fill(jk_pairs_s* h, ClassRows& cr, long long* split_tot, int* list64, int* listdem, cudaStream_t st) {
+    int rc;
+    const long long n1 = cr.nrows + 1;
+    long long* scr = cr.scr.as<long long>();
+    if ((rc = scan_into(cr.w32.as<long long>(), cr.s32.as<long long>(), n1, split_tot + 2, scr, st))) return rc;
+    if ((rc = scan_into(cr.w64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 3, scr, st))) return rc;
+    if ((rc = scan_into(cr.wdem.as<long long>(), cr.sdem.as<long long>(), n1, split_tot + 4, scr, st))) return rc;
+    if ((rc = scan_into(cr.c64.as<long long>(), cr.l64.as<long long>(), n1, split_tot + 5, scr, st))) return rc;
+    if ((rc = scan_into(cr.cdem.as<long long>(), cr.ldem.as<long long>(), n1, split_tot + 6, scr, st))) return rc;
+    k_rows_fill<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.bra.as<int>(), cr.ket0.as<int>(), cr.k32.as<int>(), cr.nrows,
+                                                     h->A.as<double4>(), g_opt.tau, h->pair_sh.as<int2>(),
+                                                     h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>(),
+                                                     cr.ldem.as<long long>(), list64, listdem);
+    CKL();
+    h->launches += 1 + 5 * scan_launches(n1);
     return 0;
 }
 
@@ -1151,22 +1254,53 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
                 return rc;
     } else {
         const int ncr = (int)h->rows.size();
-        if ((rc = h->split_tot.alloc(sizeof(long long) * 4 * std::max(1, ncr)))) return rc;
-        CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * 4 * std::max(1, ncr), st));
+        const size_t nst = (size_t)kSplitSlots * std::max(1, ncr);
+        if ((rc = h->split_tot.alloc(sizeof(long long) * nst))) return rc;
+        CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * nst, st));
         if ((rc = h->Df.alloc(sizeof(float) * (size_t)n * n))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
         k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>(), h->Df.as<float>());
         CKL();
-        h->launches += 1;
+        // max |D| per shell block, for the density-weighted FP64 selection
+        const size_t ns2 = (size_t)h->nshell * h->nshell;
+        if ((rc = h->Dsh.alloc(sizeof(float) * ns2))) return rc;
+        CK(cudaMemsetAsync(h->Dsh.p, 0, sizeof(float) * ns2, st));
+        k_dsh<<<152 * 4, 256, 0, st>>>(D, n, h->bf_shell.as<int>(), h->nshell, h->Dsh.as<unsigned int>());
+        CKL();
+        h->launches += 2;
+        const double* dmax = reinterpret_cast<const double*>(h->scratch.p);
+        for (int k = 0; k < ncr; ++k)
+            if (h->rows[k].total > 0 &&
+                (rc = split_count(h, h->rows[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st)))
+                return rc;
+        // list sizes: one host synchronisation per mixed build
+        std::vector<long long> cnt(nst);
+        CK(cudaMemcpyAsync(cnt.data(), h->split_tot.p, sizeof(long long) * nst, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<long long> off64(ncr + 1, 0), offd(ncr + 1, 0);
+        for (int k = 0; k < ncr; ++k) {
+            off64[k + 1] = off64[k] + cnt[kSplitSlots * k + 1];
+            offd[k + 1] = offd[k] + cnt[kSplitSlots * k + 7];
+        }
+        if ((rc = h->list64.alloc(sizeof(int) * std::max(1LL, off64[ncr])))) return rc;
+        if ((rc = h->listdem.alloc(sizeof(int) * std::max(1LL, offd[ncr])))) return rc;
         for (int k = 0; k < ncr; ++k) {
             ClassRows& cr = h->rows[k];
             if (cr.total <= 0) continue;
-            if ((rc = split_class(h, cr, reinterpret_cast<const double*>(h->scratch.p),
-                                  h->split_tot.as<long long>() + 4 * k, st)))
+            int* l64 = h->list64.as<int>() + off64[k];
+            int* ldm = h->listdem.as<int>() + offd[k];
+            if ((rc = split_fill(h, cr, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st))) return rc;
+            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, nullptr, nullptr,
+                                   -1, cr.l64.as<long long>(), l64)))
                 return rc;
-            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), cr.ket0.as<int>(), cr.itotal, D, J, K, st))) return rc;
-            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st))) return rc;
+            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st)))
+                return rc;
+            if ((rc = launch_class(h, cr, 1, cr.sdem.as<long long>(), nullptr, cr.itotal, D, J, K, st, nullptr, nullptr,
+                                   -1, cr.ldem.as<long long>(), ldm)))
+                return rc;
         }
+        h->list_off64 = off64;
+        h->list_offd = offd;
     }
     const long long tri = (long long)n * (n + 1) / 2;
     k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
@@ -1815,14 +1949,14 @@ int jk_last_split(jk_pairs h, int64_t* n32, int64_t* n64) {
     if (!h) return fail(JK_ERR_INVALID, "null handle");
     long long a = 0, b = h->nquartets;
     if (h->last_prec == JK_MIXED && h->split_tot.p) {
-        std::vector<long long> t(4 * h->rows.size());
+        std::vector<long long> t(kSplitSlots * h->rows.size());
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(t.data(), h->split_tot.p, sizeof(long long) * t.size(), cudaMemcpyDeviceToHost));
         a = b = 0;
         for (size_t k = 0; k < h->rows.size(); ++k) {
             if (h->rows[k].total <= 0) continue;
-            a += t[4 * k];
-            b += t[4 * k + 1];
+            a += t[kSplitSlots * k];
+            b += t[kSplitSlots * k + 1];
         }
     }
     if (n32) *n32 = a;
@@ -1909,19 +2043,24 @@ int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
         const ClassRows& cr = h->rows[ri];
         if (cr.total <= 0) continue;
         if (k < max_rows) {
-            // per-row split counts: c32/c64 (nrows entries), kets k32/ket0
+            // FP32: the contiguous suffix (c32 from k32) plus the demoted list;
+            // FP64: the FP64 list
             CK(cudaMemset(acc.p, 0, 4 * sizeof(unsigned long long)));
             k_rows_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c32.as<long long>(), cr.bra.as<int>(), cr.k32.as<int>(),
                                                        cr.nrows, h->info.as<int4>(), h->npre.as<long long>(),
                                                        acc.as<unsigned long long>());
-            k_rows_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c64.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
-                                                       cr.nrows, h->info.as<int4>(), h->npre.as<long long>(),
-                                                       acc.as<unsigned long long>() + 2);
+            k_list_primq<<<nblk(cr.nrows, 256), 256>>>(cr.cdem.as<long long>(), cr.ldem.as<long long>(),
+                                                       h->listdem.as<int>() + h->list_offd[ri], cr.bra.as<int>(),
+                                                       cr.nrows, h->info.as<int4>(), acc.as<unsigned long long>());
+            k_list_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c64.as<long long>(), cr.l64.as<long long>(),
+                                                       h->list64.as<int>() + h->list_off64[ri], cr.bra.as<int>(),
+                                                       cr.nrows, h->info.as<int4>(), acc.as<unsigned long long>() + 2);
             CKL();
             unsigned long long v[4];
             long long q2[2];
             CK(cudaMemcpy(v, acc.p, sizeof(v), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(q2, h->split_tot.as<long long>() + 4 * ri, 2 * sizeof(long long), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(q2, h->split_tot.as<long long>() + kSplitSlots * ri, 2 * sizeof(long long),
+                          cudaMemcpyDeviceToHost));
             int fq = 0, fb = 0;
             gb_class_flops(cr.bra_cls, cr.ket_cls, &fq, &fb);
             int64_t* r = rows + 8 * k;
