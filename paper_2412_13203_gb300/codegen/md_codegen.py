@@ -294,9 +294,18 @@ def quartet_counts(bra, ket):
                 xket=HAB * S_cd, bra=S_ab * NCD, R=math.comb(L + 4, 4))
 
 
-def use_flat(bra, ket):
+def use_flat(bra, ket, prec="f64"):
+    """Straight-line form with the contracted and half-transformed blocks in
+    registers.  An FP32 value takes one register, an FP64 value two, so the
+    FP32 kernels keep larger classes in registers."""
     c = quartet_counts(bra, ket)
-    return c["NAB"] * c["NCD"] + c["HAB"] * c["NCD"] <= 200 and c["xket"] + c["bra"] <= 2500
+    vals = c["NAB"] * c["NCD"] + c["HAB"] * c["NCD"]
+    if prec == "f32" and max(bra + ket) <= 2:
+        return vals <= FLAT_F32_VALUES and c["xket"] + c["bra"] <= 3000
+    return vals <= 200 and c["xket"] + c["bra"] <= 2500
+
+
+FLAT_F32_VALUES = 400
 
 
 def gen_quartet_body(bra, ket, real, mode_flat):
@@ -729,6 +738,7 @@ def gen_class_kernels(bra, ket):
     out = []
     stats = None
     for prec, real in (("f64", "double"), ("f32", "float")):
+        flat = use_flat(bra, ket, prec)
         if chunk:
             body, st = gen_quartet_body_chunk(bra, ket, real)
         else:
