@@ -301,11 +301,11 @@ def use_flat(bra, ket, prec="f64"):
     c = quartet_counts(bra, ket)
     vals = c["NAB"] * c["NCD"] + c["HAB"] * c["NCD"]
     if prec == "f32" and max(bra + ket) <= 2:
-        return vals <= FLAT_F32_VALUES and c["xket"] + c["bra"] <= 3000
+        return vals <= FLAT_F32_VALUES and c["xket"] + c["bra"] <= 4500
     return vals <= 200 and c["xket"] + c["bra"] <= 2500
 
 
-FLAT_F32_VALUES = 400
+FLAT_F32_VALUES = 650
 
 
 def gen_quartet_body(bra, ket, real, mode_flat):
