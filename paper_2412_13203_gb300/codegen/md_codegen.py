@@ -308,8 +308,27 @@ def use_flat(bra, ket, prec="f64"):
 FLAT_F32_VALUES = 650
 
 
-def gen_quartet_body(bra, ket, real, mode_flat):
-    """Device code computing acc[NAB*NCD] (double) for one shell quartet.
+def crange_groups(bra, ket):
+    """FP32 kernels of the l <= 2 classes too large for one straight-line
+    kernel: one straight-line kernel per range of ket components c, each
+    launched over all quartets (so no kernel carries more than one code path
+    and the instruction cache holds it), each digesting its part of the block.
+    Ranges are sized to at most CRANGE_VALUES block values."""
+    if max(bra + ket) > 2 or use_flat(bra, ket, "f32"):
+        return None
+    c = quartet_counts(bra, ket)
+    nc, nd = ncart(ket[0]), ncart(ket[1])
+    per_c = (c["NAB"] + c["HAB"]) * nd
+    g = max(1, CRANGE_VALUES // per_c)
+    return [(c0, min(nc, c0 + g)) for c0 in range(0, nc, g)]
+
+
+CRANGE_VALUES = 430
+
+
+def gen_quartet_body(bra, ket, real, mode_flat, cds=None):
+    """Device code computing acc[NAB*NCD] for one shell quartet (flat mode with
+    `cds`: only those ket component pairs, acc[NAB*len(cds)]).
 
     Expects in scope: pairs (PairsView), bra/ket indices, ib/ik (int4 info),
     A, B, C, Dd centres (double4 or float4 per precision), boys tables."""
@@ -318,6 +337,10 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     L = la + lb + lc + ld
     cnt = quartet_counts(bra, ket)
     NAB, NCD, HAB = cnt["NAB"], cnt["NCD"], cnt["HAB"]
+    if cds is None:
+        cds = list(range(NCD))
+    assert mode_flat or len(cds) == NCD
+    NS = len(cds)  # ket component pairs computed here
     f32 = real == "float"
     em = Emitter(real)
     hb = herm(la + lb)
@@ -330,8 +353,8 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     # the contracted block is held in the kernel's own precision: FP64 for
     # FP64 quartets; FP32 for FP32 quartets (a sum over <= 64 bra primitive
     # pairs of terms of one sign pattern; J and K still accumulate in FP64)
-    E(f"{real} acc[{NAB * NCD}];")
-    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * NCD}; ++i) acc[i] = 0;")
+    E(f"{real} acc[{NAB * NS}];")
+    E(f"#pragma unroll\nfor (int i = 0; i < {NAB * NS}; ++i) acc[i] = 0;")
     if not mode_flat:
         E(f"{real} Xl[{HAB * NCD}];")
         E(f"{real} Rc[{L1 * L1 * L1}];")
@@ -351,8 +374,8 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     # X accumulators
     if mode_flat:
         for h in range(HAB):
-            for cd in range(NCD):
-                E(f"{real} x{h}_{cd} = 0;")
+            for k in range(NS):
+                E(f"{real} x{h}_{k} = 0;")
     else:
         E(f"for (int i = 0; i < {HAB * NCD}; ++i) Xl[i] = 0;")
     E("for (int jq = 0; jq < ik.z; ++jq) {")
@@ -408,10 +431,10 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     em.flops = 0
     if mode_flat:
         for h, (t, u, v) in enumerate(hb):
-            for cd in range(NCD):
+            for k, cd in enumerate(cds):
                 for (tau, nu, phi), s in kprod[cd]:
                     r = R[(t + tau, u + nu, v + phi)]
-                    E(f"x{h}_{cd} = {fma}({em.val(s)}, {em.val(r)}, x{h}_{cd});")
+                    E(f"x{h}_{k} = {fma}({em.val(s)}, {em.val(r)}, x{h}_{k});")
                     em.flops += 2
     else:
         # cube store of R^(0)
@@ -461,9 +484,9 @@ def gen_quartet_body(bra, ket, real, mode_flat):
     em.flops = 0
     if mode_flat:
         for ab in range(NAB):
-            for cd in range(NCD):
-                expr = _dot(em, fma, [(sv, f"x{hbi[h]}_{cd}") for h, sv in bprod[ab]])
-                E(f"acc[{ab * NCD + cd}] += {expr};")
+            for k in range(NS):
+                expr = _dot(em, fma, [(sv, f"x{hbi[h]}_{k}") for h, sv in bprod[ab]])
+                E(f"acc[{ab * NS + k}] += {expr};")
     else:
         E(f"#pragma unroll 1\nfor (int cd = 0; cd < {NCD}; ++cd) {{")
         for h in range(HAB):
@@ -739,18 +762,25 @@ def gen_class_kernels(bra, ket):
     stats = None
     for prec, real in (("f64", "double"), ("f32", "float")):
         flat = use_flat(bra, ket, prec)
+        name = class_name(bra, ket)
+        # kernel variants of this precision: (name suffix, body, digest call, block size)
+        variants = []
         if chunk:
             body, st = gen_quartet_body_chunk(bra, ket, real)
+            variants.append(("", body, f"gb::digest_chunk<{na}, {nb}, {nc}, {nd}>(acc, ci, ib.x, ib.y, ik.x, ik.y, "
+                                       f"{{dm}}, Jm, Km, nbf);", na * nb * nd))
+        elif prec == "f32" and crange_groups(bra, ket):
+            for c0, c1 in crange_groups(bra, ket):
+                cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
+                body, st = gen_quartet_body(bra, ket, real, True, cds)
+                variants.append((f"_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, ib.x, "
+                                                  f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);", na * nb * len(cds)))
         else:
             body, st = gen_quartet_body(bra, ket, real, flat)
+            variants.append(("", body, f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
+                                       f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);", na * nb * nc * nd))
         if prec == "f64":
             stats = st
-        name = class_name(bra, ket)
-        if chunk:
-            digest = f"gb::digest_chunk<{na}, {nb}, {nc}, {nd}>(acc, ci, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);"
-        else:
-            digest = (f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
-                      f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);")
         if real == "float":
             centres = ("  const double4 Ad = pairs.A[bra], Cd = pairs.A[ket];\n"
                        "  const float ACx = (float)(Ad.x - Cd.x), ACy = (float)(Ad.y - Cd.y), ACz = (float)(Ad.z - Cd.z);")
@@ -758,8 +788,9 @@ def gen_class_kernels(bra, ket):
         else:
             centres = "  const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];"
             dmat = "Dm"
-        out.append(f"""
-__global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs args) {{
+        for suffix, body, digest, nacc in variants:
+            out.append(f"""
+__global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JKArgs args) {{
   // persistent grid-stride loop over the quartets of this launch; the total is
   // read on the device (last entry of the row prefix) so launches need no host sync
   // Work items: rows.start is the prefix of items per row, a row's quartet
@@ -808,7 +839,7 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}(const gb::JKArgs arg
   if (ik.x == ik.y) s *= 0.5f;
   if (bra == ket) s *= 0.5f;
 #pragma unroll
-  for (int i = 0; i < {na * nb * (nd if chunk else nc * nd)}; ++i) acc[i] *= s;
+  for (int i = 0; i < {nacc}; ++i) acc[i] *= s;
   {digest.format(dm=dmat)}
   }}
 }}
@@ -1136,11 +1167,18 @@ def generate(outdir, lmax=LMAX, nfiles=None):
             src.append(code)
             stats_all[class_name(bra, ket)] = st
             name = class_name(bra, ket)
+            if crange_groups(bra, ket):
+                f32_launches = "\n".join(f"    eri_jk_{name}_f32_c{c0}<<<grid, block, 0, s>>>(a);"
+                                          for c0, _ in crange_groups(bra, ket))
+            else:
+                f32_launches = f"    eri_jk_{name}_f32<<<grid, block, 0, s>>>(a);"
             src.append(f"""
 int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s) {{
   if (grid <= 0) return 0;
   if (prec == 0) eri_jk_{name}_f64<<<grid, block, 0, s>>>(a);
-  else eri_jk_{name}_f32<<<grid, block, 0, s>>>(a);
+  else {{
+{f32_launches}
+  }}
   return (int)cudaGetLastError();
 }}
 """)

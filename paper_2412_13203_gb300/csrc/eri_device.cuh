@@ -278,6 +278,83 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
     }
 }
 
+// The update of `digest` restricted to the ket components c in [C0, C1) of a
+// quartet: acc[(ab * NCR + (c - C0)) * ND + d], NCR = C1 - C0 (the FP32
+// kernels of the large classes compute a quartet's block one c range per
+// launch; the ranges' updates add up to the full one).
+template <int NA, int NB, int NC, int ND, int C0, int C1, class R>
+__device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int fc, int fd,
+                                              const R* __restrict__ D, double* J, double* K, int n) {
+    constexpr int NCR = C1 - C0;
+#define GB_ACC(a, b, c, d) acc[(((a) * NB + (b)) * NCR + ((c) - C0)) * ND + (d)]
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {  // J'_ab
+            R v = 0;
+#pragma unroll
+            for (int c = C0; c < C1; ++c)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fc + c) * n + fd + d), v);
+            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+        }
+#pragma unroll
+    for (int c = C0; c < C1; ++c)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {  // J'_cd
+            R v = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fb + b), v);
+            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
+        }
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int c = C0; c < C1; ++c) {  // K'_ac
+            R v = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fd + d), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)v);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {  // K'_ad
+            R v = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int c = C0; c < C1; ++c) {  // K'_bc
+            R v = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {  // K'_bd
+            R v = 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+        }
+    }
+#undef GB_ACC
+}
+
+
 // Same update with rolled loops (large classes: bounded code size; the block
 // lives in local memory there anyway).
 template <int NA, int NB, int NC, int ND, class R>
