@@ -305,7 +305,7 @@ def use_flat(bra, ket, prec="f64"):
     return vals <= 200 and c["xket"] + c["bra"] <= 2500
 
 
-FLAT_F32_VALUES = 430
+FLAT_F32_VALUES = 250
 
 
 def crange_groups(bra, ket):
@@ -323,7 +323,7 @@ def crange_groups(bra, ket):
     return [(c0, min(nc, c0 + g)) for c0 in range(0, nc, g)]
 
 
-CRANGE_VALUES = 250
+CRANGE_VALUES = 150
 
 
 def gen_quartet_body(bra, ket, real, mode_flat, cds=None):
