@@ -53,6 +53,10 @@ struct BatchMol {
     PairsView pairs;
     const double* D;
     float* Df;                // FP32 copy of D (mixed builds; written by the max|D| pass)
+    float* Dsh;               // mixed builds: max |D| per shell block [nshell^2]
+    const int* bf_shell;      // shell of every basis function
+    const int2* psh;          // shells a, b of every kept pair
+    int nshell;
     double* J;
     double* K;
     int nbf;

@@ -1324,6 +1324,9 @@ struct BatchClass {
     DevBuf start, bra, ket0, rowmol;
     DevBuf istart, itot;  // work-item prefix of the FP64 launch, its total
     DevBuf s64, s32, k32, c64, c32, w64, w32, scr;
+    DevBuf cdem, wdem, sdem, l64, ldem;  // density-weighted split (as ClassRows)
+    long long cap64 = 0, capdem = 0;     // list capacities of this class
+    long long off64 = 0, offdem = 0;     // its segments in the plan's lists
     TuneCfg tune[2];
 };
 
@@ -1335,11 +1338,13 @@ struct BatchPlan {
     double tau = 0.0, tsmall = 0.0;
     long long nquartets = 0;
     DevBuf bm, dmax, split_tot;
+    DevBuf list64, listdem;  // mixed: FP64 and demoted ket lists, one segment per class
     std::vector<BatchClass> cls;
     cudaStream_t cs = nullptr, ps[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr}, done = nullptr;
     cudaGraphExec_t exec = nullptr;
-    long long launches = 0;
+    long long launches = 0;        // kernels of the (captured) launch sequence
+    long long launches_total = 0;  // plus the pre-pass of a mixed build
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         for (auto& x : ps) if (x) cudaStreamDestroy(x);
@@ -1398,30 +1403,71 @@ __global__ void k_absmax_batched(const gb::BatchMol* bm, unsigned long long* out
     if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(v));
 }
 
+// Max |D| per shell block of every molecule (grid.y = molecule).
+__global__ void k_dsh_batched(const gb::BatchMol* bm) {
+    const gb::BatchMol& m = bm[blockIdx.y];
+    const int n = m.nbf;
+    const long long n2 = (long long)n * n;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / n), j = (int)(k - (long long)i * n);
+        atomicMax(reinterpret_cast<unsigned int*>(m.Dsh) + (size_t)m.bf_shell[i] * m.nshell + m.bf_shell[j],
+                  __float_as_uint((float)fabs(m.D[k])));
+    }
+}
+
+// k_rows_split for batched rows (each row's molecule from rowmol).
 __global__ void k_rows_split_batched(const long long* start, const int* rbra, const int* rket0, const int* rowmol,
                                      int nrows, const gb::BatchMol* bm, const unsigned long long* dmax, double tau,
-                                     long long* c64, long long* c32, int* k32, int P, long long* w64, long long* w32,
-                                     unsigned long long* qtot) {
+                                     int P, long long* c64, long long* cdem, long long* c32, int* k32, long long* w64,
+                                     long long* wdem, long long* w32, unsigned long long* qtot) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    const int m = rowmol[r];
-    const long long ms = min(P, bm[m].pairs.info[rbra[r]].z);
-    const double4* A = bm[m].pairs.A;
+    const gb::BatchMol& mol = bm[rowmol[r]];
+    const double4* A = mol.pairs.A;
+    const int i = rbra[r];
+    const long long ms = min(P, mol.pairs.info[i].z);
     const long long c = start[r + 1] - start[r];
     const int s = rket0[r];
-    const double qi = A[rbra[r]].w * __longlong_as_double((long long)dmax[m]);
+    const double qi = A[i].w;
+    const double qg = qi * __longlong_as_double((long long)dmax[rowmol[r]]);
     int lo = s, hi = s + (int)c;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (qi * A[mid].w >= tau) lo = mid + 1; else hi = mid;
+        if (qg * A[mid].w >= tau) lo = mid + 1; else hi = mid;
     }
-    c64[r] = lo - s;
-    c32[r] = c - (lo - s);
+    const int2 ab = mol.psh[i];
+    long long n64 = 0;
+    for (int j = s; j < lo; ++j)
+        if (qi * A[j].w * (double)quartet_dmax(mol.Dsh, mol.nshell, ab, mol.psh[j]) >= tau) ++n64;
+    const long long nd = (lo - s) - n64, n32 = c - (lo - s);
+    c64[r] = n64;
+    cdem[r] = nd;
+    c32[r] = n32;
     k32[r] = lo;
-    w64[r] = (lo - s) * ms;
-    w32[r] = (c - (lo - s)) * ms;
-    atomicAdd(qtot, (unsigned long long)(c - (lo - s)));
-    atomicAdd(qtot + 1, (unsigned long long)(lo - s));
+    w64[r] = n64 * ms;
+    wdem[r] = nd * ms;
+    w32[r] = n32 * ms;
+    atomicAdd(qtot, (unsigned long long)(n32 + nd));
+    atomicAdd(qtot + 1, (unsigned long long)n64);
+    atomicAdd(qtot + 7, (unsigned long long)nd);
+}
+
+// k_rows_fill for batched rows.
+__global__ void k_rows_fill_batched(const int* rbra, const int* rket0, const int* k32, const int* rowmol, int nrows,
+                                    const gb::BatchMol* bm, double tau, const long long* l64, const long long* ldem,
+                                    int* list64, int* listdem) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const gb::BatchMol& mol = bm[rowmol[r]];
+    const double4* A = mol.pairs.A;
+    const int i = rbra[r];
+    const double qi = A[i].w;
+    const int2 ab = mol.psh[i];
+    long long o64 = l64[r], od = ldem[r];
+    for (int j = rket0[r]; j < k32[r]; ++j) {
+        if (qi * A[j].w * (double)quartet_dmax(mol.Dsh, mol.nshell, ab, mol.psh[j]) >= tau) list64[o64++] = j;
+        else listdem[od++] = j;
+    }
 }
 
 int build_plan(BatchPlan& P, cudaStream_t st) {
@@ -1436,7 +1482,12 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
         host[m].pairs = view_of(h);
         host[m].D = P.D[m];
         if (P.prec == JK_MIXED && (rc = h->Df.alloc(sizeof(float) * (size_t)h->nbf * h->nbf))) return rc;
+        if (P.prec == JK_MIXED && (rc = h->Dsh.alloc(sizeof(float) * (size_t)h->nshell * h->nshell))) return rc;
         host[m].Df = h->Df.as<float>();
+        host[m].Dsh = h->Dsh.as<float>();
+        host[m].bf_shell = h->bf_shell.as<int>();
+        host[m].psh = h->pair_sh.as<int2>();
+        host[m].nshell = h->nshell;
         host[m].J = P.J[m];
         host[m].K = P.K[m];
         host[m].nbf = h->nbf;
@@ -1508,13 +1559,15 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
                 if ((rc = bc.c32.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.w64.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.w32.alloc(sizeof(long long) * n1))) return rc;
+                for (DevBuf* b : {&bc.cdem, &bc.wdem, &bc.sdem, &bc.l64, &bc.ldem})
+                    if ((rc = b->alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.s64.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.s32.alloc(sizeof(long long) * n1))) return rc;
                 if ((rc = bc.k32.alloc(sizeof(int) * nrows))) return rc;
                 if ((rc = bc.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
             }
         }
-    if ((rc = P.split_tot.alloc(sizeof(long long) * 4 * std::max<size_t>(1, P.cls.size())))) return rc;
+    if ((rc = P.split_tot.alloc(sizeof(long long) * kSplitSlots * std::max<size_t>(1, P.cls.size())))) return rc;
     CK(cudaStreamSynchronize(st));
     CK(cudaStreamCreateWithFlags(&P.cs, cudaStreamNonBlocking));
     for (auto& x : P.ps) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
@@ -1525,7 +1578,7 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
 }
 
 int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* start, const int* ket0,
-                       cudaStream_t s) {
+                       cudaStream_t s, const long long* kofs = nullptr, const int* klist = nullptr) {
     gb::JKArgs a;
     std::memset(&a, 0, sizeof(a));
     a.pairs = view_of(P.mols[0]);
@@ -1533,6 +1586,8 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     a.rows.start = start;
     a.rows.bra = bc.bra.as<int>();
     a.rows.ket0 = ket0;
+    a.rows.kofs = kofs;
+    a.rows.klist = klist;
     a.boys = g_boys[P.device].tab.as<double>();
     a.boysf = g_boys[P.device].tabf.as<float>();
     a.tsmall = (float)P.tsmall;
@@ -1557,13 +1612,6 @@ int enqueue_batch(BatchPlan& P) {
     k_zero_batched<<<dim3(nblk(n2max, 256), nmol), 256, 0, P.cs>>>(bm);
     CKL();
     P.launches += 1;
-    if (P.prec == JK_MIXED) {
-        CK(cudaMemsetAsync(P.dmax.p, 0, sizeof(unsigned long long) * nmol, P.cs));
-        CK(cudaMemsetAsync(P.split_tot.p, 0, sizeof(long long) * 4 * std::max<size_t>(1, P.cls.size()), P.cs));
-        k_absmax_batched<<<dim3(64, nmol), 256, 0, P.cs>>>(bm, P.dmax.as<unsigned long long>());
-        CKL();
-        P.launches += 1;
-    }
     CK(cudaEventRecord(P.fork, P.cs));
     for (auto& x : P.ps) CK(cudaStreamWaitEvent(x, P.fork, 0));
     for (size_t k = 0; k < P.cls.size(); ++k) {
@@ -1572,23 +1620,28 @@ int enqueue_batch(BatchPlan& P) {
         if (P.prec == JK_FP64) {
             if ((rc = launch_batch_class(P, bc, 0, bc.istart.as<long long>(), bc.ket0.as<int>(), s))) return rc;
         } else {
+            // counts come from the pre-pass (batch_prepass); scans, list fill, launches
             const long long n1 = bc.nrows + 1;
-            k_rows_split_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(
-                bc.start.as<long long>(), bc.bra.as<int>(), bc.ket0.as<int>(), bc.rowmol.as<int>(), bc.nrows, bm,
-                P.dmax.as<unsigned long long>(), P.tau, bc.c64.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>(),
-                gb_class_split(bc.X, bc.Y), bc.w64.as<long long>(), bc.w32.as<long long>(),
-                reinterpret_cast<unsigned long long*>(P.split_tot.as<long long>() + 4 * k));
+            long long* tot = P.split_tot.as<long long>() + kSplitSlots * k;
+            long long* scr = bc.scr.as<long long>();
+            if ((rc = scan_into(bc.w32.as<long long>(), bc.s32.as<long long>(), n1, tot + 2, scr, s))) return rc;
+            if ((rc = scan_into(bc.w64.as<long long>(), bc.s64.as<long long>(), n1, tot + 3, scr, s))) return rc;
+            if ((rc = scan_into(bc.wdem.as<long long>(), bc.sdem.as<long long>(), n1, tot + 4, scr, s))) return rc;
+            if ((rc = scan_into(bc.c64.as<long long>(), bc.l64.as<long long>(), n1, tot + 5, scr, s))) return rc;
+            if ((rc = scan_into(bc.cdem.as<long long>(), bc.ldem.as<long long>(), n1, tot + 6, scr, s))) return rc;
+            int* l64 = P.list64.as<int>() + bc.off64;
+            int* ldm = P.listdem.as<int>() + bc.offdem;
+            k_rows_fill_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(bc.bra.as<int>(), bc.ket0.as<int>(), bc.k32.as<int>(),
+                                                                    bc.rowmol.as<int>(), bc.nrows, bm, P.tau,
+                                                                    bc.l64.as<long long>(), bc.ldem.as<long long>(),
+                                                                    l64, ldm);
             CKL();
-            CK(cudaMemsetAsync(bc.w64.as<long long>() + bc.nrows, 0, 8, s));
-            CK(cudaMemsetAsync(bc.w32.as<long long>() + bc.nrows, 0, 8, s));
-            long long* tot = P.split_tot.as<long long>() + 4 * k;
-            if ((rc = scan_into(bc.w64.as<long long>(), bc.s64.as<long long>(), n1, tot + 3, bc.scr.as<long long>(), s)))
+            P.launches += 1 + 5 * scan_launches(n1);
+            if ((rc = launch_batch_class(P, bc, 0, bc.s64.as<long long>(), nullptr, s, bc.l64.as<long long>(), l64)))
                 return rc;
-            if ((rc = scan_into(bc.w32.as<long long>(), bc.s32.as<long long>(), n1, tot + 2, bc.scr.as<long long>(), s)))
-                return rc;
-            P.launches += 1 + 2 * scan_launches(n1);
-            if ((rc = launch_batch_class(P, bc, 0, bc.s64.as<long long>(), bc.ket0.as<int>(), s))) return rc;
             if ((rc = launch_batch_class(P, bc, 1, bc.s32.as<long long>(), bc.k32.as<int>(), s))) return rc;
+            if ((rc = launch_batch_class(P, bc, 1, bc.sdem.as<long long>(), nullptr, s, bc.ldem.as<long long>(), ldm)))
+                return rc;
         }
     }
     for (int i = 0; i < 3; ++i) {
@@ -1599,6 +1652,78 @@ int enqueue_batch(BatchPlan& P) {
     k_sym_batched<<<dim3(nblk(trimax, 256), nmol), 256, 0, P.cs>>>(bm);
     CKL();
     P.launches += 1;
+    return 0;
+}
+
+// Mixed batched builds, before the (captured) launch sequence: max|D| and the
+// FP32 copy of D, the shell-block maxima of D, and the per-row split counts of
+// every class; then one host synchronisation reads the list sizes.  If a
+// class's lists outgrow their segments, the lists are re-laid out (*relaid) and
+// a captured graph must be captured again.
+int batch_prepass(BatchPlan& P, bool* relaid) {
+    const int nmol = (int)P.mols.size();
+    const gb::BatchMol* bm = P.bm.as<gb::BatchMol>();
+    *relaid = false;
+    const size_t nst = (size_t)kSplitSlots * std::max<size_t>(1, P.cls.size());
+    CK(cudaMemsetAsync(P.dmax.p, 0, sizeof(unsigned long long) * nmol, P.cs));
+    CK(cudaMemsetAsync(P.split_tot.p, 0, sizeof(long long) * nst, P.cs));
+    k_absmax_batched<<<dim3(64, nmol), 256, 0, P.cs>>>(bm, P.dmax.as<unsigned long long>());
+    CKL();
+    for (jk_pairs h : P.mols) CK(cudaMemsetAsync(h->Dsh.p, 0, sizeof(float) * (size_t)h->nshell * h->nshell, P.cs));
+    const long long n2max = (long long)P.max_n * P.max_n;
+    k_dsh_batched<<<dim3((unsigned)std::min<long long>(nblk(n2max, 256), 1024), nmol), 256, 0, P.cs>>>(bm);
+    CKL();
+    for (size_t k = 0; k < P.cls.size(); ++k) {
+        BatchClass& bc = P.cls[k];
+        k_rows_split_batched<<<nblk(bc.nrows, 256), 256, 0, P.cs>>>(
+            bc.start.as<long long>(), bc.bra.as<int>(), bc.ket0.as<int>(), bc.rowmol.as<int>(), bc.nrows, bm,
+            P.dmax.as<unsigned long long>(), P.tau, gb_class_split(bc.X, bc.Y), bc.c64.as<long long>(),
+            bc.cdem.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>(), bc.w64.as<long long>(),
+            bc.wdem.as<long long>(), bc.w32.as<long long>(),
+            reinterpret_cast<unsigned long long*>(P.split_tot.as<long long>() + kSplitSlots * k));
+        CKL();
+        for (DevBuf* b : {&bc.c64, &bc.c32, &bc.cdem, &bc.w64, &bc.w32, &bc.wdem})
+            CK(cudaMemsetAsync(b->as<long long>() + bc.nrows, 0, 8, P.cs));
+    }
+    std::vector<long long> cnt(nst);
+    CK(cudaMemcpyAsync(cnt.data(), P.split_tot.p, sizeof(long long) * nst, cudaMemcpyDeviceToHost, P.cs));
+    CK(cudaStreamSynchronize(P.cs));
+    bool grow = false;
+    for (size_t k = 0; k < P.cls.size(); ++k)
+        grow = grow || cnt[kSplitSlots * k + 1] > P.cls[k].cap64 || cnt[kSplitSlots * k + 7] > P.cls[k].capdem;
+    if (grow) {  // new segments with 25 % headroom
+        long long o64 = 0, od = 0;
+        for (size_t k = 0; k < P.cls.size(); ++k) {
+            BatchClass& bc = P.cls[k];
+            bc.cap64 = std::max(bc.cap64, cnt[kSplitSlots * k + 1] + cnt[kSplitSlots * k + 1] / 4 + 1024);
+            bc.capdem = std::max(bc.capdem, cnt[kSplitSlots * k + 7] + cnt[kSplitSlots * k + 7] / 4 + 1024);
+            bc.off64 = o64;
+            bc.offdem = od;
+            o64 += bc.cap64;
+            od += bc.capdem;
+        }
+        int rc;
+        if ((rc = P.list64.alloc(sizeof(int) * o64))) return rc;
+        if ((rc = P.listdem.alloc(sizeof(int) * od))) return rc;
+        *relaid = true;
+    }
+    return 0;
+}
+
+int capture_batch(BatchPlan& P) {
+    if (P.exec) {
+        cudaGraphExecDestroy(P.exec);
+        P.exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(P.cs, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_batch(P);
+    const cudaError_t ce = cudaStreamEndCapture(P.cs, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess) return fail(JK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&P.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(JK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
     return 0;
 }
 
@@ -1625,30 +1750,24 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
         P.tsmall = g_opt.tsmall;
         P.graph = g_opt.graph;
         if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
-        if (P.graph) {
-            cudaGraph_t graph = nullptr;
-            CK(cudaStreamBeginCapture(P.cs, cudaStreamCaptureModeThreadLocal));
-            rc = enqueue_batch(P);
-            const cudaError_t ce = cudaStreamEndCapture(P.cs, &graph);
-            if (rc) { if (graph) cudaGraphDestroy(graph); g_plan.reset(); return rc; }
-            if (ce != cudaSuccess) { g_plan.reset(); return fail(JK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)); }
-            const cudaError_t ie = cudaGraphInstantiate(&P.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) { g_plan.reset(); return fail(JK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
-        }
     }
     BatchPlan& P = *g_plan;
     // order the batch after the caller's prior work on st, and st after the batch
     CK(cudaEventRecord(P.done, st));
     CK(cudaStreamWaitEvent(P.cs, P.done, 0));
+    bool relaid = false;
+    if (P.prec == JK_MIXED && (rc = batch_prepass(P, &relaid))) { g_plan.reset(); return rc; }
+    const long long pre = P.prec == JK_MIXED ? 3 + (long long)P.cls.size() : 0;  // pre-pass kernels
     if (P.graph) {
+        if ((!P.exec || relaid) && (rc = capture_batch(P))) { g_plan.reset(); return rc; }
         CK(cudaGraphLaunch(P.exec, P.cs));
     } else {
         if ((rc = enqueue_batch(P))) return rc;
     }
+    P.launches_total = P.launches + pre;
     CK(cudaEventRecord(P.done, P.cs));
     CK(cudaStreamWaitEvent(st, P.done, 0));
-    if (launches) *launches = P.launches;
+    if (launches) *launches = P.launches_total;
     return 0;
 }
 

@@ -47,15 +47,30 @@ def test_batched_matches_oracle_and_single(g, graph):
     g.set_option("graph", 1)
 
 
-def test_batched_mixed(g):
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batched_mixed(g, graph):
+    """The batched mixed form (density-weighted FP64 selection, pre-pass outside
+    the captured graph) against FP64 builds, and against the single-molecule
+    mixed path, which selects the same quartets; a second call replays."""
+    g.set_option("graph", graph)
     mols = _mols()
     pairs = [g.ShellPairs(m, 1e-12) for m, _ in mols]
     Ds = [torch.from_numpy(D).cuda() for _, D in mols]
-    Js, Ks = g.jk_build_batched(pairs, Ds, precision="mixed")
-    torch.cuda.synchronize()
-    for p, J, K, Dt in zip(pairs, Js, Ks, Ds):
-        J1, K1 = g.jk_build(p, Dt, "fp64")
-        assert float((J1 - J).abs().max()) <= 1e-6 and float((K1 - K).abs().max()) <= 1e-6
+    try:
+        for rep in range(2):
+            if rep == 1:  # new density values under the same pointers: the pre-pass re-reads them
+                for D in Ds:
+                    D.mul_(1.5)
+            Js, Ks = g.jk_build_batched(pairs, Ds, precision="mixed")
+            torch.cuda.synchronize()
+            for p, J, K, Dt in zip(pairs, Js, Ks, Ds):
+                J1, K1 = g.jk_build(p, Dt, "fp64")
+                assert float((J1 - J).abs().max()) <= 1e-6 and float((K1 - K).abs().max()) <= 1e-6
+                Jm, Km = g.jk_build(p, Dt, "mixed")
+                assert float((Jm - J).abs().max()) <= 1e-10 * max(1.0, float(Jm.abs().max()))
+                assert float((Km - K).abs().max()) <= 1e-10 * max(1.0, float(Km.abs().max()))
+    finally:
+        g.set_option("graph", 1)
 
 
 def test_autotune_keeps_results(g):
