@@ -31,9 +31,9 @@ class V:
 def _split_top(s, sep):
     out, depth, cur = [], 0, ""
     for ch in s:
-        if ch == "(":
+        if ch in "([":
             depth += 1
-        elif ch == ")":
+        elif ch in ")]":
             depth -= 1
         if ch == sep and depth == 0:
             out.append(cur)
@@ -45,49 +45,119 @@ def _split_top(s, sep):
     return out
 
 
+class _Ptr:
+    """`const T* q = base + off`: q[k] reads base[off + k]."""
+
+    def __init__(self, base, off):
+        self.base, self.off = base, off
+
+    def __getitem__(self, k):
+        return self.base[self.off + k]
+
+
+_FOR = re.compile(r"for \(int (\w+) = (.+?); \1 (<=|<|>=) (.+?); (\+\+\1|--\1|\1 \+= \w+)\)\s*(\{?)\s*(.*)$")
+
+
+def _expr(e):
+    e = re.sub(r"\b(\d+\.\d*|\d+)f\b", r"\1", e)
+    e = re.sub(r"\b__fdividef\(", "_div(", e)
+    e = re.sub(r"\brsqrtf?\(", "_rsqrt(", e)
+    e = re.sub(r"\bfmaf?\(", "_fma(", e)
+    e = re.sub(r"\((?:double|float|int)\)\(", "float(", e)
+    m = re.search(r"\(([^()]+)\) \? (.+?) : (.+)$", e)
+    if m:
+        e = e[:m.start()] + f"({m.group(2)} if ({m.group(1)}) else {m.group(3)})"
+    return e
+
+
+def _stmt(st):
+    """One C statement (no control flow) -> Python lines."""
+    st = st.strip().rstrip(";").strip()
+    if not st:
+        return []
+    m = re.match(r"^gb::boys_(?:f64|mixed)<(\d+)>\(T, F.*\)$", st)
+    if m:
+        return [f"F = _boys({m.group(1)}, T)"]
+    m = re.match(r"^(?:const )?(?:int|float|double)[24]?\* (\w+) = (\w+) \+ (.+)$", st)
+    if m:
+        return [f"{m.group(1)} = _Ptr({m.group(2)}, {_expr(m.group(3))})"]
+    m = re.match(r"^(?:float|double|int) (\w+)\[(\d+)\]$", st)
+    if m:
+        return [f"{m.group(1)} = [0.0] * {m.group(2)}"]
+    m = re.match(r"^(?:float|double) (\w+)$", st)
+    if m:
+        return [f"{m.group(1)} = 0.0"]
+    st = re.sub(r"^(?:const )?(?:float|double|int)[24]? ", "", st)
+    return [_expr(p.strip()) for p in re.split(r",\s*(?=[A-Za-z_]\w*\s*=[^=])", st)]
+
+
+def _if_chain(line):
+    """`[else ][if (c) ]{ s1; if (c2) s2; }` -> (keyword header, body lines)."""
+    m = re.match(r"^(else )?(?:if \((.+?)\) )?\{ (.*) \}$", line)
+    kw = ("elif" if m.group(1) else "if") if m.group(2) else "else"
+    head = f"{kw} {_expr(m.group(2))}:" if m.group(2) else "else:"
+    body = []
+    for st in _split_top(m.group(3), ";"):
+        st = st.strip()
+        mm = re.match(r"^if \((.+?)\) (.+)$", st)
+        if mm:
+            body.append(f"if {_expr(mm.group(1))}: " + "; ".join(_stmt(mm.group(2))))
+        else:
+            body += _stmt(st)
+    return head, body
+
+
 def to_python(body):
-    """Translate a generated flat body (C) into Python source."""
-    lines, ind = [], 0
+    """Translate a generated kernel body (C) into Python source."""
+    out, ind, stack, pending = [], 0, [], 0
+
+    def emit(s, extra=0):
+        out.append(" " * (ind + extra) + s)
+
     for raw in body.split("\n"):
         line = raw.split("//")[0].strip()
         if not line or line.startswith("#pragma"):
             continue
-        line = re.sub(r"\b(\d+\.\d*|\d+)f\b", r"\1", line)
-        line = re.sub(r"\b__fdividef\(", "_div(", line)
-        line = re.sub(r"\brsqrtf?\(", "_rsqrt(", line)
-        line = re.sub(r"\bfmaf?\(", "_fma(", line)
-        m = re.match(r"(?:float|double) acc\[(\d+)\];$", line)
+        m = _FOR.match(line)
         if m:
-            lines.append(" " * ind + f"acc = [0.0] * {m.group(1)}")
-            continue
-        if re.match(r"for \(int i = 0; i < \d+; \+\+i\) acc\[i\] = 0;$", line):
-            continue
-        m = re.match(r"for \(int ip = ipart; ip < ib\.z; ip \+= nsplit\) \{$", line)
-        if m:
-            lines.append(" " * ind + "for ip in range(ipart, ib.z, nsplit):")
+            var, a, op, b, step, brace, rest = m.groups()
+            a, b = _expr(a), _expr(b)
+            if step.startswith("--"):
+                rng = f"range({a}, ({b}) - 1, -1)"
+            elif "+=" in step:
+                rng = f"range({a}, {b}, {step.split('+=')[1].strip()})"
+            else:
+                rng = f"range({a}, {b}{' + 1' if op == '<=' else ''})"
+            emit(f"for {var} in {rng}:")
             ind += 4
+            if brace:
+                stack.append(1 + pending)
+                pending = 0
+            elif rest:
+                for s_ in _stmt(rest):
+                    emit(s_)
+                ind -= 4
+            else:
+                pending += 1
             continue
-        if re.match(r"for \(int jq = 0; jq < ik\.z; \+\+jq\) \{$", line):
-            lines.append(" " * ind + "for jq in range(ik.z):")
-            ind += 4
+        if re.match(r"^(else )?(if \(.+?\) )?\{ .* \}$", line):
+            head, lines = _if_chain(line)
+            emit(head)
+            for s_ in lines:
+                emit(s_, 4)
             continue
-        if line == "}":
-            ind -= 4
+        if re.fullmatch(r"\}+", line):
+            for _ in line:
+                ind -= 4 * stack.pop()
             continue
-        m = re.match(r"(?:float|double) F\[(\d+)\];$", line)
-        if m:
+        if line.startswith("}"):
+            ind -= 4 * stack.pop()
             continue
-        m = re.match(r"gb::boys_(?:f64|mixed)<(\d+)>\(T, F.*\);$", line)
-        if m:
-            lines.append(" " * ind + f"F = _boys({m.group(1)}, T)")
-            continue
-        for stmt in _split_top(line.rstrip(";"), ";"):
-            stmt = stmt.strip()
-            stmt = re.sub(r"^(?:const )?(?:float|double)[24]? ", "", stmt)
-            for part in re.split(r",\s*(?=[A-Za-z_]\w*\s*=[^=])", stmt):
-                lines.append(" " * ind + part.strip())
-    assert ind == 0
-    return "\n".join(lines)
+        for st in _split_top(line, ";"):
+            for s_ in _stmt(st):
+                emit(s_)
+    assert ind == 0 and not stack, (ind, stack)
+    return "\n".join(out)
 
 
 def _pair_data(a, b):
@@ -109,7 +179,7 @@ def _pair_data(a, b):
     return pp, pp2, ppf, ppf2
 
 
-def _run(body, bra, ket, shells):
+def _run(body, bra, ket, shells, ci=0):
     ns = {"_fma": lambda a, b, c: a * b + c, "_rsqrt": lambda x: 1.0 / math.sqrt(x), "_div": lambda a, b: a / b,
           "_boys": lambda L, T: list(oracle.boys(L, float(T)))}
     A_, B_, C_, D_ = shells
@@ -122,7 +192,14 @@ def _run(body, bra, ket, shells):
     ns.update(pairs=pairs, ib=V(0, 0, nb, 0), ik=V(0, 0, len(ket_pp[0]), nb), ipart=0, nsplit=1,
               A=V(*A_[0]), B=V(*B_[0]), C=V(*C_[0]), Dd=V(*D_[0]))
     AC = A_[0] - C_[0]
-    ns.update(ACx=AC[0], ACy=AC[1], ACz=AC[2], boys=None, boysf=None, tsmall=0.0)
+    ns.update(ACx=AC[0], ACy=AC[1], ACz=AC[2], boys=None, boysf=None, tsmall=0.0, ci=ci)
+    for l in range(4):
+        ns[f"c_comp_{l}"] = [x for c in mg.comps(l) for x in c]
+    lc, ld = ket
+    ns[f"c_cd_tab_{lc}{ld}"] = [x for c in mg.comps(lc) for d in mg.comps(ld) for x in c + d]
+    txt = mg.support_table(*bra)[0]
+    ns[f"c_bsup_{bra[0]}{bra[1]}"] = [int(v) for v in txt[txt.index("{") + 1:txt.index("}")].split(",")]
+    ns["_Ptr"] = _Ptr
     exec(to_python(body), ns)
     return np.array(ns["acc"])
 
@@ -169,3 +246,43 @@ def test_fp32_range_bodies_cover_the_block(bra, ket):
         got = _run(body, bra, ket, sh).reshape(na * nb, len(cds))
         want = ref.reshape(na * nb, nc * nd)[:, cds]
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), (c0, np.abs(got - want).max())
+
+
+LOOP = [(b, k) for b, k in mg.class_pairs(2) if not mg.use_flat(b, k, "f64")]
+
+
+@pytest.mark.parametrize("bra,ket", LOOP, ids=[mg.class_name(b, k) for b, k in LOOP])
+def test_loop_body_matches_oracle(bra, ket):
+    """FP64 looped form of the large l <= 2 classes (R cube, runtime loops)."""
+    rng = np.random.default_rng(sum(bra) * 13 + sum(ket) * 3)
+    sh = _shells(rng, [bra[0], bra[1], ket[0], ket[1]], 2)
+    body, _ = mg.gen_quartet_body(bra, ket, "double", False)
+    got = _run(body, bra, ket, sh)
+    ref = oracle.eri_quartet(sh).reshape(-1)
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), np.abs(got - ref).max()
+
+
+def _ordered(x, y):
+    ix, iy = mg.PAIR_CLASSES.index(x), mg.PAIR_CLASSES.index(y)
+    return (x, y) if ix >= iy else (y, x)
+
+
+CHUNK = [c for c in (_ordered(*xy) for xy in [((3, 0), (1, 1)), ((3, 1), (1, 1)), ((3, 0), (2, 2)), ((3, 2), (2, 1)),
+                                              ((3, 3), (1, 0)), ((3, 3), (3, 3)), ((3, 1), (3, 0))])
+         if mg.use_chunk(*c)]
+
+
+@pytest.mark.parametrize("bra,ket", CHUNK, ids=[mg.class_name(b, k) for b, k in CHUNK])
+@pytest.mark.parametrize("real", ["double", "float"])
+def test_chunk_body_matches_oracle(bra, ket, real):
+    """Classes with an f shell: one thread per ket component c (rolled R
+    recursion, support tables); the threads of a quartet assemble the block."""
+    rng = np.random.default_rng(sum(bra) * 7 + sum(ket) + (real == "float"))
+    sh = _shells(rng, [bra[0], bra[1], ket[0], ket[1]], 1)
+    ref = oracle.eri_quartet(sh)
+    na, nb, nc, nd = ref.shape
+    body, _ = mg.gen_quartet_body_chunk(bra, ket, real)
+    for ci in range(nc):
+        got = _run(body, bra, ket, sh, ci).reshape(na * nb, nd)
+        want = ref[:, :, ci, :].reshape(na * nb, nd)
+        assert np.abs(got - want).max() <= 1e-11 * max(1.0, np.abs(ref).max()), (ci, np.abs(got - want).max())
