@@ -1117,6 +1117,90 @@ int launch_grad_{name}(const gb::GradArgs& a, cudaStream_t s) {{
     return "\n".join(em.lines) + "\n"
 
 
+# ---------------------------------------------------------------- path search (analysis)
+def r_targets(bra, ket, cds=None):
+    """The Hermite integrals R^(0)_{tuv} a kernel body reads: bra Hermite
+    index plus the support of every ket component pair it computes."""
+    hb = herm(bra[0] + bra[1])
+    cdl = [(c, d) for c in comps(ket[0]) for d in comps(ket[1])]
+    out = set()
+    for k in (range(len(cdl)) if cds is None else cds):
+        c, d = cdl[k]
+        for tau in range(c[0] + d[0] + 1):
+            for nu in range(c[1] + d[1] + 1):
+                for phi in range(c[2] + d[2] + 1):
+                    out.update((0, t + tau, u + nu, v + phi) for (t, u, v) in hb)
+    return out
+
+
+def _r_children(node, axis):
+    n, *k = node
+    one = list(k)
+    one[axis] -= 1
+    kids = [(n + 1, *one)]
+    if k[axis] >= 2:
+        two = list(k)
+        two[axis] -= 2
+        kids.append((n + 1, *two))
+    return kids
+
+
+def r_path(targets, lam=None):
+    """Nodes R^(n)_{tuv} needed to reach `targets` through the recursion
+    R^(n)_{k} = (k_i - 1) R^(n+1)_{k - 2e_i} + X_i R^(n+1)_{k - e_i}.
+
+    lam None: the fixed order the emitted code uses (reduce t first, then u,
+    then v).  Otherwise the greedy search of the paper's Graph Compiler
+    (Sec. 5, Algorithm 1): going down from the highest total angular momentum,
+    every node takes the axis ("recurrence position") of least cost
+    (new - reused) + lam * (angular momentum of the new nodes).
+    Returns {node: axis or None}."""
+    chosen = {}
+    todo = set(targets)
+    while todo:
+        top = max(sum(x[1:]) for x in todo)
+        level = sorted(x for x in todo if sum(x[1:]) == top)
+        todo -= set(level)
+        for node in level:
+            if top == 0:
+                chosen[node] = None
+                continue
+            axes = [i for i in range(3) if node[1 + i] > 0]
+            if lam is None:
+                best = axes[0]
+            else:
+                def cost(i):
+                    kids = _r_children(node, i)
+                    new = [c for c in kids if c not in chosen and c not in todo]
+                    return (len(new) - (len(kids) - len(new))) + lam * sum(sum(c[1:]) for c in new)
+                best = min(axes, key=cost)
+            chosen[node] = best
+            todo.update(c for c in _r_children(node, best) if c not in chosen)
+    return chosen
+
+
+def r_path_flops(chosen):
+    """Operations of a recursion path: one multiply per node plus one FMA
+    where the node has a second child (the F_n base values are not counted)."""
+    return sum(0 if ax is None else len(_r_children(n, ax)) for n, ax in chosen.items())
+
+
+def path_report(lmax=2, lams=(0.0, 0.5, 1.0, 2.0)):
+    """Per class: R recursion operations of the kernels as emitted (fixed
+    order, per FP32 range kernel where the class has them) and with the
+    greedy path search at the best lam."""
+    rows = []
+    for bra, ket in class_pairs(lmax):
+        groups = crange_groups(bra, ket)
+        nd = ncart(ket[1])
+        sets = [None] if not groups else [[c * nd + d for c in range(c0, c1) for d in range(nd)] for c0, c1 in groups]
+        fixed = sum(r_path_flops(r_path(r_targets(bra, ket, cds))) for cds in sets)
+        greedy = sum(min(r_path_flops(r_path(r_targets(bra, ket, cds), lam)) for lam in lams) for cds in sets)
+        rows.append((class_name(bra, ket), fixed, greedy))
+    return rows
+
+
+
 def indent(s, n=2):
     return "\n".join(" " * n + l for l in s.split("\n"))
 

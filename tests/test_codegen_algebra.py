@@ -286,3 +286,55 @@ def test_chunk_body_matches_oracle(bra, ket, real):
         got = _run(body, bra, ket, sh, ci).reshape(na * nb, nd)
         want = ref[:, :, ci, :].reshape(na * nb, nd)
         assert np.abs(got - want).max() <= 1e-11 * max(1.0, np.abs(ref).max()), (ci, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("lam", [None, 0.0, 1.0])
+def test_r_path_search_is_a_valid_recursion(lam):
+    """The recursion paths (fixed order and the Algorithm-1 greedy search):
+    every target is reached, every chosen node's children are on the path,
+    and the recursion evaluated along the path reproduces the Hermite R
+    values of the fixed-order code (random rho, P-Q, F_n)."""
+    rng = np.random.default_rng(5)
+    for bra, ket in [((1, 1), (1, 0)), ((2, 1), (2, 1)), ((2, 2), (1, 1))]:
+        T = mg.r_targets(bra, ket)
+        path = mg.r_path(T, lam)
+        assert T <= set(path)
+        for node, ax in path.items():
+            if ax is not None:
+                assert all(c in path for c in mg._r_children(node, ax))
+        L = sum(bra) + sum(ket)
+        X = rng.uniform(-1, 1, 3)
+        F = rng.uniform(0.1, 1, L + 1)
+        memo = {}
+
+        def R(node):  # evaluate along the chosen axes
+            if node not in memo:
+                n, *k = node
+                ax = path[node]
+                if ax is None:
+                    memo[node] = F[n]
+                else:
+                    kids = mg._r_children(node, ax)
+                    val = X[ax] * R(kids[0])
+                    if len(kids) == 2:
+                        val += (k[ax] - 1) * R(kids[1])
+                    memo[node] = val
+            return memo[node]
+        ref_path = mg.r_path(T, None)
+        memo_ref = {}
+
+        def Rref(node):
+            if node not in memo_ref:
+                n, *k = node
+                ax = ref_path[node]
+                memo_ref[node] = F[n] if ax is None else (
+                    X[ax] * Rref(mg._r_children(node, ax)[0]) +
+                    ((k[ax] - 1) * Rref(mg._r_children(node, ax)[1]) if k[ax] >= 2 else 0.0))
+            return memo_ref[node]
+        for t in T:
+            assert abs(R(t) - Rref(t)) <= 1e-12 * max(1.0, abs(Rref(t)))
+
+
+def test_path_search_never_costs_more():
+    for name, fixed, greedy in mg.path_report():
+        assert greedy <= fixed, name
