@@ -1,0 +1,249 @@
+"""CPU emulation of the generated ERI kernels (test infrastructure only).
+
+The kernel text the generator emits for the GPU library is compiled as plain
+C++ with host stand-ins for the few CUDA names it uses (tests/emu/cuda_runtime.h)
+and run one thread at a time: the grid-stride loops of the J/K kernels then
+visit every work item in order, the gradient kernels are called once per
+quartet.  Pair data, quartet rows, work-item prefixes and the Boys table are
+built here in Python as the library's runtime builds them; J/K/gradient come
+out exactly as the kernels compute them (the FP32 kernels in real FP32), so the
+tests can hold every generated kernel against the oracle without a GPU."""
+from __future__ import annotations
+
+import ctypes as C
+import hashlib
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+sys.path.insert(0, os.path.join(ROOT, "paper_2412_13203_gb300", "codegen"))
+import md_codegen as mg  # noqa: E402
+
+BUILD = os.path.join(HERE, "_emu_build")
+KBOYS_ROWS, KBOYS_TAYLOR, KBOYS_NGRID, KLMAX_BOYS = 15, 8, 1281, 13
+
+
+def _source(lmax, only=None):
+    qs = [q for q in mg.class_pairs(lmax) if only is None or q in only]
+    gqs = [q for q in mg.class_pairs(min(lmax, mg.GRAD_LMAX)) if q in qs]
+    src = ['#include "eri_device.cuh"', "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"]
+    src += [mg.comp_table(l) for l in range(lmax + 1)]
+    for ket in sorted({k for _, k in qs}):
+        src.append(mg.cd_table(*ket))
+    for bra in sorted({b for b, k in qs if mg.use_chunk(b, k)}):
+        src.append(mg.support_table(*bra)[0])
+    pcs = [pc for pc in mg.PAIR_CLASSES if pc[0] <= lmax]
+    jk_cases, grad_cases = [], []
+    for bra, ket in qs:
+        src.append(mg.gen_class_kernels(bra, ket)[0])
+        name = mg.class_name(bra, ket)
+        key = pcs.index(bra) * 16 + pcs.index(ket)
+        if mg.crange_groups(bra, ket):
+            f32 = " ".join(f"eri_jk_{name}_f32_c{c0}(a);" for c0, _ in mg.crange_groups(bra, ket))
+        else:
+            f32 = f"eri_jk_{name}_f32(a);"
+        jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else {{ {f32} }} return 0;")
+        if (bra, ket) in gqs:
+            g = mg.gen_grad_kernel(bra, ket)
+            src.append(g[:g.index("\nint launch_grad_")])
+            grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)total; ++blockIdx.x) "
+                              f"eri_grad_{name}_f64(g); return 0;")
+    src.append("""
+static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
+                        const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
+    gb::PairsView v;
+    std::memset(&v, 0, sizeof(v));
+    v.npair = npair; v.info = info; v.A = A; v.B = B; v.pp = pp; v.pp2 = pp2; v.ppf = ppf; v.ppf2 = ppf2;
+    v.alpha = alpha;
+    return v;
+}
+extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
+                      const double4* pp, const double2* pp2, const float4* ppf, const float4* ppf2,
+                      const double* alpha, int nrows, const long long* start, const int* bra, const int* ket0,
+                      const double* boys, const float* boysf, float tsmall, const double* D, const float* Df,
+                      double* J, double* K, int nbf) {
+    gb::JKArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pairs = pv(npair, info, A, B, pp, pp2, ppf, ppf2, alpha);
+    a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
+    a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.D = D; a.Df = Df; a.J = J; a.K = K; a.nbf = nbf;
+    blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    switch (X * 16 + Y) {
+""" + "\n".join(jk_cases) + """
+    }
+    return -1;
+}
+extern "C" int emu_grad(int X, int Y, int npair, const int4* info, const double4* A, const double4* B,
+                        const double4* pp, const double2* pp2, const double* alpha, int nrows,
+                        const long long* start, const int* bra, const int* ket0, long long total,
+                        const double* boys, const double* D, int nbf, const int2* atoms, double* grad) {
+    gb::GradArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.pairs = pv(npair, info, A, B, pp, pp2, nullptr, nullptr, alpha);
+    g.rows.nrows = nrows; g.rows.start = start; g.rows.bra = bra; g.rows.ket0 = ket0;
+    g.total = total; g.boys = boys; g.D = D; g.nbf = nbf; g.atoms = atoms; g.grad = grad;
+    threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    switch (X * 16 + Y) {
+""" + "\n".join(grad_cases) + """
+    }
+    return -1;
+}
+""")
+    return "\n".join(src)
+
+
+_LIBS = {}
+
+
+def load(lmax=2, only=None):
+    """Compile (cached by source hash) and load the emulation library of the
+    class pairs `only` (all classes up to lmax if None)."""
+    key = (lmax, None if only is None else tuple(sorted(only)))
+    if key in _LIBS:
+        return _LIBS[key]
+    src = _source(lmax, only)
+    hdrs = [os.path.join(ROOT, "paper_2412_13203_gb300", "csrc", "eri_device.cuh"),
+            os.path.join(HERE, "emu", "cuda_runtime.h")]
+    h = hashlib.sha1(src.encode())
+    for p in hdrs:
+        h.update(open(p, "rb").read())
+    os.makedirs(BUILD, exist_ok=True)
+    lib = os.path.join(BUILD, f"emu_{lmax}_{h.hexdigest()[:12]}.so")
+    if not os.path.exists(lib):
+        cpp = lib[:-3] + ".cpp"
+        with open(cpp, "w") as f:
+            f.write(src)
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-w", "-I", os.path.join(HERE, "emu"),
+                        "-I", os.path.join(ROOT, "paper_2412_13203_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                        cpp, "-o", tmp], check=True)
+        os.replace(tmp, lib)
+    _LIBS[key] = C.CDLL(lib)
+    return _LIBS[key]
+
+
+def boys_tables(oracle):
+    """The Boys Taylor table in the library's layout: F_{m+j}(T_k)/j! for
+    T_k = k/16, m = 0..13, and exp(-T_k)/j! in the last row (values from the
+    oracle's Boys function)."""
+    tab = np.zeros((KBOYS_NGRID, KBOYS_ROWS, KBOYS_TAYLOR))
+    fact = np.array([math.factorial(j) for j in range(KBOYS_TAYLOR)], dtype=float)
+    for k in range(KBOYS_NGRID):
+        T = k / 16.0
+        F = oracle.boys(KLMAX_BOYS + KBOYS_TAYLOR, T)
+        for m in range(KLMAX_BOYS + 1):
+            tab[k, m] = F[m:m + KBOYS_TAYLOR] / fact
+        tab[k, KLMAX_BOYS + 1] = math.exp(-T) / fact
+    return tab.ravel(), tab.ravel().astype(np.float32)
+
+
+class Problem:
+    """Pairs, rows and matrices of one molecule, laid out as the library's
+    runtime lays them out (pairs canonicalised l_a >= l_b, grouped by class;
+    for bra class = ket class only kets up to the bra)."""
+
+    def __init__(self, mol, D, oracle, lmax=2):
+        self.mol, self.lmax = mol, lmax
+        c = oracle.normalize(mol)
+        l, K, off, atom = mol.shell_l, mol.shell_nprim, mol.shell_prim_offset, mol.shell_atom
+        S = len(l)
+        bf = np.concatenate([[0], np.cumsum([(x + 1) * (x + 2) // 2 for x in l])])[:-1]
+        self.pcs = [pc for pc in mg.PAIR_CLASSES if pc[0] <= lmax]
+        pairs = []
+        for i in range(S):
+            for j in range(i + 1):
+                a, b = (j, i) if l[j] > l[i] else (i, j)
+                pairs.append((self.pcs.index((int(l[a]), int(l[b]))), a, b))
+        pairs.sort()
+        Q = oracle.schwarz(mol)
+        info, A, B, pp, pp2, ppf, ppf2, alpha, atoms = [], [], [], [], [], [], [], [], []
+        s2 = math.sqrt(2 * math.pi ** 2.5)
+        for cls, a, b in pairs:
+            Ra, Rb = mol.xyz[atom[a]], mol.xyz[atom[b]]
+            AB = Ra - Rb
+            info.append((bf[a], bf[b], K[a] * K[b], len(pp)))
+            A.append((*Ra, Q[a, b]))
+            B.append((*Rb, 0.0))
+            atoms.append((atom[a], atom[b]))
+            for u in range(K[a]):
+                for v in range(K[b]):
+                    al, be = mol.exps[off[a] + u], mol.exps[off[b] + v]
+                    p = al + be
+                    kap = s2 * math.exp(-al * be / p * (AB @ AB)) * c[off[a] + u] * c[off[b] + v] / p
+                    pp.append((*((al * Ra + be * Rb) / p), p))
+                    pp2.append((kap, 0.5 / p))
+                    ppf.append((*(-be / p * AB), p))
+                    ppf2.append((*(al / p * AB), kap))
+                    alpha.append(al)
+        self.cls = np.array([x[0] for x in pairs])
+        present = sorted(set(self.cls.tolist()))
+        # compile every class when the molecule spans all l <= 2 classes (shared,
+        # cached library), else only the classes this molecule has
+        self.only = None if lmax == 2 else {(self.pcs[x], self.pcs[y]) for x in present for y in present if y <= x}
+        f = lambda x, t: np.ascontiguousarray(np.array(x, dtype=t))
+        self.info, self.atoms = f(info, np.int32), f(atoms, np.int32)
+        self.A, self.B, self.pp, self.pp2 = f(A, np.float64), f(B, np.float64), f(pp, np.float64), f(pp2, np.float64)
+        self.ppf, self.ppf2, self.alpha = f(ppf, np.float32), f(ppf2, np.float32), f(alpha, np.float64)
+        self.D = np.ascontiguousarray(D, dtype=np.float64)
+        self.Df = self.D.astype(np.float32)
+        self.nbf = D.shape[0]
+        self.boys, self.boysf = boys_tables(oracle)
+
+    def rows(self, X, Y, items=True):
+        """Rows (bra, first ket, quartet count) of class pair (X, Y) and their
+        prefix: of work items (min(P, K_ab) per quartet) or of quartets."""
+        bras = np.where(self.cls == X)[0]
+        kets = np.where(self.cls == Y)[0]
+        if len(bras) == 0 or len(kets) == 0:
+            return None
+        P = mg.split_of(self.pcs[X], self.pcs[Y])
+        bra, ket0, cnt = [], [], []
+        for i in bras:
+            n = (i - kets[0] + 1) if X == Y else len(kets)
+            bra.append(i)
+            ket0.append(kets[0])
+            cnt.append(n * (min(P, self.info[i, 2]) if items else 1))
+        start = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+        return np.array(bra, np.int32), np.array(ket0, np.int32), start
+
+    def _p(self, a):
+        return a.ctypes.data_as(C.c_void_p)
+
+    def jk(self, prec, tsmall=1.0):
+        lib = load(self.lmax, self.only)
+        J = np.zeros((self.nbf, self.nbf))
+        K = np.zeros((self.nbf, self.nbf))
+        for X in range(len(self.pcs)):
+            for Y in range(X + 1):
+                r = self.rows(X, Y)
+                if r is None:
+                    continue
+                bra, ket0, start = r
+                rc = lib.emu_jk(X, Y, prec, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
+                                self._p(self.pp), self._p(self.pp2), self._p(self.ppf), self._p(self.ppf2),
+                                self._p(self.alpha), len(bra), self._p(start), self._p(bra), self._p(ket0),
+                                self._p(self.boys), self._p(self.boysf), C.c_float(tsmall), self._p(self.D),
+                                self._p(self.Df), self._p(J), self._p(K), self.nbf)
+                assert rc == 0
+        return J + J.T, K + K.T
+
+    def grad(self):
+        lib = load(self.lmax, self.only)
+        g = np.zeros((self.mol.xyz.shape[0], 3))
+        for X in range(len(self.pcs)):
+            for Y in range(X + 1):
+                r = self.rows(X, Y, items=False)
+                if r is None:
+                    continue
+                bra, ket0, start = r
+                rc = lib.emu_grad(X, Y, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
+                                  self._p(self.pp), self._p(self.pp2), self._p(self.alpha), len(bra),
+                                  self._p(start), self._p(bra), self._p(ket0), C.c_longlong(int(start[-1])),
+                                  self._p(self.boys), self._p(self.D), self.nbf, self._p(self.atoms), self._p(g))
+                assert rc == 0
+        return g

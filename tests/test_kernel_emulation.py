@@ -1,0 +1,51 @@
+"""The generated CUDA kernels, compiled as plain C++ and run thread by thread
+on the CPU (tests/kernel_emu.py), against the oracle: J and K of every l <= 2
+class in FP64 and in FP32 (all quartets in the FP32 kernels), and the nuclear
+gradient.  This exercises the kernels' own work-item decoding, splitting over
+bra primitive pairs, degeneracy factors, digestion and Boys evaluation, not
+only the generated algebra."""
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+
+kernel_emu = pytest.importorskip("kernel_emu")
+
+
+def _mol(seed, shells, natom, kmax):
+    mol = molgen.random_molecule(seed, natom, shells, 1, kmax, 0.1, 60.0, layout="lattice", spacing=1.9)
+    return mol, molgen.density(mol, seed + 50)
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(61, [0, 1, 2], 2, 3), (62, [2, 1], 2, 2), (63, [0, 2, 2], 2, 2)])
+def test_emulated_jk_fp64_and_fp32(seed, shells, natom, kmax):
+    mol, D = _mol(seed, shells, natom, kmax)
+    pr = kernel_emu.Problem(mol, D, oracle)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    J, K = pr.jk(0)
+    assert np.abs(J - Jo).max() <= 1e-10 * max(1.0, np.abs(Jo).max())
+    assert np.abs(K - Ko).max() <= 1e-10 * max(1.0, np.abs(Ko).max())
+    J, K = pr.jk(1)
+    assert np.abs(J - Jo).max() <= 2e-6 * np.abs(Jo).max()
+    assert np.abs(K - Ko).max() <= 2e-6 * np.abs(Ko).max()
+
+
+def test_emulated_gradient():
+    mol, D = _mol(64, [0, 1, 2], 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle)
+    g = pr.grad()
+    go = oracle.grad(mol, D, mode="unique")
+    assert np.abs(g - go).max() <= 1e-10 * max(1.0, np.abs(go).max())
+
+
+@pytest.mark.parametrize("seed,shells", [(65, [0, 3]), (66, [1, 3])])
+def test_emulated_f_classes(seed, shells):
+    """Classes with an f shell (one thread per ket component, rolled R)."""
+    mol, D = _mol(seed, shells, 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=3)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    for prec, tol in ((0, 1e-10), (1, 2e-6)):
+        J, K = pr.jk(prec)
+        assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), (prec, np.abs(J - Jo).max())
+        assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), (prec, np.abs(K - Ko).max())
