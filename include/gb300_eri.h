@@ -107,7 +107,11 @@ int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartet
  * the digestion dot products, from centre differences formed in FP64 --
  * and each digested sum is added to J and K in FP64 (split accumulation);
  * the other quartets, the Boys function at small T, the Schwarz factors and
- * the final J/K symmetrisation stay FP64. */
+ * the final J/K symmetrisation stay FP64.  The bound is density-weighted:
+ * Q_ab Q_cd times the largest |D| element of the six shell blocks of D the
+ * quartet's J and K updates read.  A JK_MIXED build synchronises the stream
+ * once, after its split pass, to size its quartet lists; JK_FP64 builds are
+ * fully asynchronous. */
 int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision prec,
              void* cuda_stream);
 
@@ -121,7 +125,10 @@ int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, vo
 
 /* Many independent molecules in one launch sequence (one persistent launch per
  * angular class over all molecules' work), optionally captured into a CUDA
- * graph (JK_OPT_GRAPH).  D[i], J[i], K[i] are device pointers of molecule i. */
+ * graph (JK_OPT_GRAPH) that is replayed while the molecules, matrix pointers
+ * and options stay the same.  D[i], J[i], K[i] are device pointers of
+ * molecule i.  JK_MIXED: a split pass outside the graph selects the FP64
+ * quartets as jk_build does and synchronises once to size the lists. */
 int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J,
                      double* const* K, jk_precision prec, void* cuda_stream);
 
