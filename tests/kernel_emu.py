@@ -65,12 +65,14 @@ static gb::PairsView pv(int npair, const int4* info, const double4* A, const dou
 extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
                       const double4* pp, const double2* pp2, const float4* ppf, const float4* ppf2,
                       const double* alpha, int nrows, const long long* start, const int* bra, const int* ket0,
+                      const long long* kofs, const int* klist,
                       const double* boys, const float* boysf, float tsmall, const double* D, const float* Df,
                       double* J, double* K, int nbf) {
     gb::JKArgs a;
     std::memset(&a, 0, sizeof(a));
     a.pairs = pv(npair, info, A, B, pp, pp2, ppf, ppf2, alpha);
     a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
+    a.rows.kofs = kofs; a.rows.klist = klist;
     a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.D = D; a.Df = Df; a.J = J; a.K = K; a.nbf = nbf;
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
@@ -214,7 +216,10 @@ class Problem:
     def _p(self, a):
         return a.ctypes.data_as(C.c_void_p)
 
-    def jk(self, prec, tsmall=1.0):
+    def jk(self, prec, tsmall=1.0, lists=False):
+        """J and K from the class kernels of one precision.  lists=True hands
+        every row's kets to the kernels as an explicit ket list (the form of
+        a mixed build's FP64 and demoted lists), in reversed order."""
         lib = load(self.lmax, self.only)
         J = np.zeros((self.nbf, self.nbf))
         K = np.zeros((self.nbf, self.nbf))
@@ -224,9 +229,17 @@ class Problem:
                 if r is None:
                     continue
                 bra, ket0, start = r
+                kofs = klist = None
+                if lists:
+                    cnt = np.array([(i - ket0[k] + 1) if X == Y else int((self.cls == Y).sum())
+                                    for k, i in enumerate(bra)], dtype=np.int64)
+                    kofs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+                    klist = np.concatenate([np.arange(k0, k0 + c)[::-1] for k0, c in zip(ket0, cnt)]).astype(np.int32)
+                    ket0 = np.zeros_like(ket0)
                 rc = lib.emu_jk(X, Y, prec, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
                                 self._p(self.pp), self._p(self.pp2), self._p(self.ppf), self._p(self.ppf2),
                                 self._p(self.alpha), len(bra), self._p(start), self._p(bra), self._p(ket0),
+                                None if kofs is None else self._p(kofs), None if klist is None else self._p(klist),
                                 self._p(self.boys), self._p(self.boysf), C.c_float(tsmall), self._p(self.D),
                                 self._p(self.Df), self._p(J), self._p(K), self.nbf)
                 assert rc == 0

@@ -29,6 +29,10 @@ def test_emulated_jk_fp64_and_fp32(seed, shells, natom, kmax):
     J, K = pr.jk(1)
     assert np.abs(J - Jo).max() <= 2e-6 * np.abs(Jo).max()
     assert np.abs(K - Ko).max() <= 2e-6 * np.abs(Ko).max()
+    # the explicit-ket-list form of the rows (mixed builds' FP64 and demoted lists)
+    J, K = pr.jk(0, lists=True)
+    assert np.abs(J - Jo).max() <= 1e-10 * max(1.0, np.abs(Jo).max())
+    assert np.abs(K - Ko).max() <= 1e-10 * max(1.0, np.abs(Ko).max())
 
 
 def test_emulated_gradient():
