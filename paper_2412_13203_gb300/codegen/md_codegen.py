@@ -948,13 +948,24 @@ def gen_grad_kernel(bra, ket):
     E(f"__global__ void __launch_bounds__(128) eri_grad_{name}_f64(const gb::GradArgs args) {{")
     E("const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
     E("if (tid >= args.total) return;")
-    E("int bra, ket, row;")
-    E("gb::locate_quartet(args.rows, tid, bra, ket, row);")
+    # work items as in the J/K kernels: a quartet split into min(P, K_ab) items
+    # over its bra primitive pairs, heaviest rows (largest ket primitive count,
+    # at the end of the range) first so that the launch tail is light
+    P = split_of(bra, ket)
+    E("int row;")
+    E("long long li;")
+    E("gb::locate_row(args.rows, args.total - 1 - tid, row, li);")
+    E("const int bra = __ldg(args.rows.bra + row);")
     E("const gb::PairsView& pairs = args.pairs;")
     E("const double* __restrict__ boys = args.boys;")
     E("const double* __restrict__ Dm = args.D;")
     E("const int n = args.nbf;")
-    E("const int4 ib = pairs.info[bra], ik = pairs.info[ket];")
+    E("const int4 ib = pairs.info[bra];")
+    E(f"const int nsplit = min({P}, ib.z);")
+    E("const long long qo = li / nsplit;")
+    E("const int ipart = (int)(li - qo * nsplit);")
+    E("const int ket = __ldg(args.rows.ket0 + row) + (int)qo;")
+    E("const int4 ik = pairs.info[ket];")
     E("const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];")
     E("double s = 1.0;")
     E("if (ib.x == ib.y) s *= 0.5;")
@@ -972,7 +983,7 @@ def gen_grad_kernel(bra, ket):
     E(f"double X[{H1 * NCD}];")
     E(f"double XC[{3 * H0 * NCD}];")
     E(f"double Rc[{S * S * S}];")
-    E("for (int ip = 0; ip < ib.z; ++ip) {")
+    E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
     E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
     E("const double p = pa.w, kp = pb.x, inv2p = pb.y, alpha = pairs.alpha[ib.w + ip], beta = p - alpha;")
     E("const double PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")

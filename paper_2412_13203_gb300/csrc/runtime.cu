@@ -1982,12 +1982,13 @@ int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* 
     for (const ClassRows& cr : h->rows) {
         if (cr.total <= 0) continue;
         gb::GradArgs a;
+        std::memset(&a, 0, sizeof(a));
         a.pairs = view_of(h);
         a.rows.nrows = cr.nrows;
-        a.rows.start = cr.start.as<long long>();
+        a.rows.start = cr.istart.as<long long>();  // work items, as the J/K kernels
         a.rows.bra = cr.bra.as<int>();
         a.rows.ket0 = cr.ket0.as<int>();
-        a.total = cr.total;
+        a.total = cr.itotal;
         a.boys = g_boys[h->device].tab.as<double>();
         a.D = D;
         a.nbf = h->nbf;

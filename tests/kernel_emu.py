@@ -250,7 +250,7 @@ class Problem:
         g = np.zeros((self.mol.xyz.shape[0], 3))
         for X in range(len(self.pcs)):
             for Y in range(X + 1):
-                r = self.rows(X, Y, items=False)
+                r = self.rows(X, Y)
                 if r is None:
                     continue
                 bra, ket0, start = r
