@@ -227,7 +227,7 @@ def main():
     split = {s["cls"]: s for s in g.split_stats(pairs)}
     # the plain FP64 form beside it (fewer steps: it is ~3x slower)
     g.set_option("profile", 1)
-    ms64, prof64, l64 = timed_steps("fp64", min(args.steps, 2), 1, profile=True)
+    ms64, prof64, _ = timed_steps("fp64", min(args.steps, 2), 1, profile=True)
     g.set_option("profile", 0)
     E64 = g.jk_energy(Dt, J, K)
     dJ = float((J_mx - J).abs().max())
