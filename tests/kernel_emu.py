@@ -38,7 +38,7 @@ def _source(lmax, only=None):
     for bra in sorted({b for b, k in qs if mg.use_chunk(b, k)}):
         src.append(mg.support_table(*bra)[0])
     pcs = [pc for pc in mg.PAIR_CLASSES if pc[0] <= lmax]
-    jk_cases, grad_cases = [], []
+    jk_cases, grad_cases, sw_cases = [], [], []
     for bra, ket in qs:
         src.append(mg.gen_class_kernels(bra, ket)[0])
         name = mg.class_name(bra, ket)
@@ -48,6 +48,10 @@ def _source(lmax, only=None):
         else:
             f32 = f"eri_jk_{name}_f32(a);"
         jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else {{ {f32} }} return 0;")
+        if bra == ket:
+            nthr = mg.ncart(bra[0]) if mg.use_chunk(bra, ket) else 1
+            sw_cases.append(f"    case {pcs.index(bra)}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(count * {nthr}); "
+                            f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); return 0;")
         if (bra, ket) in gqs:
             g = mg.gen_grad_kernel(bra, ket)
             src.append(g[:g.index("\nint launch_grad_")])
@@ -77,6 +81,19 @@ extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
 """ + "\n".join(jk_cases) + """
+    }
+    return -1;
+}
+extern "C" int emu_schwarz(int X, int npair, const int4* info, const double4* A, const double4* B,
+                           const double4* pp, const double2* pp2, int first, int count, const double* boys,
+                           double* Q) {
+    gb::SchwarzArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.pairs = pv(npair, info, A, B, pp, pp2, nullptr, nullptr, nullptr);
+    sa.first = first; sa.count = count; sa.boys = boys; sa.Q = Q;
+    threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    switch (X) {
+""" + "\n".join(sw_cases) + """
     }
     return -1;
 }
@@ -183,6 +200,7 @@ class Problem:
                     ppf2.append((*(al / p * AB), kap))
                     alpha.append(al)
         self.cls = np.array([x[0] for x in pairs])
+        self.pair_shells = [(a, b) for _, a, b in pairs]
         present = sorted(set(self.cls.tolist()))
         # compile every class when the molecule spans all l <= 2 classes (shared,
         # cached library), else only the classes this molecule has
@@ -244,6 +262,21 @@ class Problem:
                                 self._p(self.Df), self._p(J), self._p(K), self.nbf)
                 assert rc == 0
         return J + J.T, K + K.T
+
+    def schwarz(self):
+        """Q_ab of every pair from the generated Schwarz kernels (pair order
+        of this problem), for comparison with the oracle's."""
+        lib = load(self.lmax, self.only)
+        Q = np.zeros(len(self.info))
+        for X in range(len(self.pcs)):
+            idx = np.where(self.cls == X)[0]
+            if len(idx) == 0:
+                continue
+            rc = lib.emu_schwarz(X, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
+                                 self._p(self.pp), self._p(self.pp2), int(idx[0]), len(idx), self._p(self.boys),
+                                 Q[idx[0]:].ctypes.data_as(C.c_void_p))
+            assert rc == 0
+        return Q
 
     def grad(self):
         lib = load(self.lmax, self.only)

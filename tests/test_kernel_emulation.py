@@ -53,3 +53,15 @@ def test_emulated_f_classes(seed, shells):
         J, K = pr.jk(prec)
         assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), (prec, np.abs(J - Jo).max())
         assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), (prec, np.abs(K - Ko).max())
+
+
+@pytest.mark.parametrize("seed,shells,lmax", [(67, [0, 1, 2], 2), (68, [2, 3], 3)])
+def test_emulated_schwarz_factors(seed, shells, lmax):
+    """Q_ab = sqrt(max_i |(ab|ab)_ii|) from the generated Schwarz kernels
+    (single-thread and per-component forms) against the oracle's."""
+    mol, D = _mol(seed, shells, 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=lmax)
+    Q = pr.schwarz()
+    Qo = oracle.schwarz(mol)
+    want = np.array([Qo[a, b] for a, b in pr.pair_shells])
+    assert np.abs(Q - want).max() <= 1e-11 * max(1.0, want.max()), np.abs(Q - want).max()
