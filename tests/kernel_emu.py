@@ -10,10 +10,12 @@ out exactly as the kernels compute them (the FP32 kernels in real FP32), so the
 tests can hold every generated kernel against the oracle without a GPU."""
 from __future__ import annotations
 
+import concurrent.futures as cf
 import ctypes as C
 import hashlib
 import math
 import os
+import re
 import subprocess
 import sys
 
@@ -28,19 +30,30 @@ BUILD = os.path.join(HERE, "_emu_build")
 KBOYS_ROWS, KBOYS_TAYLOR, KBOYS_NGRID, KLMAX_BOYS = 15, 8, 1281, 13
 
 
-def _source(lmax, only=None):
+def _sources(lmax, only=None, ntu=8):
+    """Translation units: `ntu` holding the kernels (spread by size, compiled
+    in parallel) and one holding the dispatch entry points."""
     qs = [q for q in mg.class_pairs(lmax) if only is None or q in only]
     gqs = [q for q in mg.class_pairs(min(lmax, mg.GRAD_LMAX)) if q in qs]
-    src = ['#include "eri_device.cuh"', "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"]
-    src += [mg.comp_table(l) for l in range(lmax + 1)]
+    head = ['#include "eri_device.cuh"']
+    head += [mg.comp_table(l) for l in range(lmax + 1)]
     for ket in sorted({k for _, k in qs}):
-        src.append(mg.cd_table(*ket))
+        head.append(mg.cd_table(*ket))
     for bra in sorted({b for b, k in qs if mg.use_chunk(b, k)}):
-        src.append(mg.support_table(*bra)[0])
+        head.append(mg.support_table(*bra)[0])
     pcs = [pc for pc in mg.PAIR_CLASSES if pc[0] <= lmax]
-    jk_cases, grad_cases, sw_cases = [], [], []
+    jk_cases, grad_cases, sw_cases, decls = [], [], [], []
+    tus = [list(head) for _ in range(ntu)]
+    load_ = [0] * ntu
     for bra, ket in qs:
-        src.append(mg.gen_class_kernels(bra, ket)[0])
+        code = mg.gen_class_kernels(bra, ket)[0]
+        if (bra, ket) in gqs:
+            g = mg.gen_grad_kernel(bra, ket)
+            code += g[:g.index("\nint launch_grad_")]
+        k = load_.index(min(load_))
+        tus[k].append(code)
+        load_[k] += len(code)
+        decls += ["void " + m + ";" for m in re.findall(r"void (?:__launch_bounds__\([^)]*\) )?(eri_\w+\(const gb::\w+ \w+\))", code)]
         name = mg.class_name(bra, ket)
         key = pcs.index(bra) * 16 + pcs.index(ket)
         if mg.crange_groups(bra, ket):
@@ -53,10 +66,9 @@ def _source(lmax, only=None):
             sw_cases.append(f"    case {pcs.index(bra)}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(count * {nthr}); "
                             f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); return 0;")
         if (bra, ket) in gqs:
-            g = mg.gen_grad_kernel(bra, ket)
-            src.append(g[:g.index("\nint launch_grad_")])
             grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)total; ++blockIdx.x) "
                               f"eri_grad_{name}_f64(g); return 0;")
+    src = ['#include "eri_device.cuh"', "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
@@ -113,7 +125,7 @@ extern "C" int emu_grad(int X, int Y, int npair, const int4* info, const double4
     return -1;
 }
 """)
-    return "\n".join(src)
+    return ["\n".join(t) for t in tus if len(t) > len(head)], "\n".join(src)
 
 
 _LIBS = {}
@@ -125,22 +137,31 @@ def load(lmax=2, only=None):
     key = (lmax, None if only is None else tuple(sorted(only)))
     if key in _LIBS:
         return _LIBS[key]
-    src = _source(lmax, only)
+    tus, disp = _sources(lmax, only)
     hdrs = [os.path.join(ROOT, "paper_2412_13203_gb300", "csrc", "eri_device.cuh"),
             os.path.join(HERE, "emu", "cuda_runtime.h")]
-    h = hashlib.sha1(src.encode())
+    h = hashlib.sha1("".join(tus + [disp]).encode())
     for p in hdrs:
         h.update(open(p, "rb").read())
     os.makedirs(BUILD, exist_ok=True)
-    lib = os.path.join(BUILD, f"emu_{lmax}_{h.hexdigest()[:12]}.so")
+    stem = os.path.join(BUILD, f"emu_{lmax}_{h.hexdigest()[:12]}")
+    lib = stem + ".so"
     if not os.path.exists(lib):
-        cpp = lib[:-3] + ".cpp"
-        with open(cpp, "w") as f:
-            f.write(src)
+        flags = ["-std=c++17", "-O1", "-fPIC", "-w", "-I", os.path.join(HERE, "emu"),
+                 "-I", os.path.join(ROOT, "paper_2412_13203_gb300", "csrc"), "-I", os.path.join(ROOT, "include")]
+
+        def compile_one(i_src):
+            i, text = i_src
+            cpp, obj = f"{stem}_{i}.cpp", f"{stem}_{i}.o"
+            with open(cpp, "w") as f:
+                f.write(text)
+            subprocess.run(["g++", "-c", cpp, "-o", obj] + flags, check=True)
+            return obj
+
+        with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+            objs = list(ex.map(compile_one, enumerate(tus + [disp])))
         tmp = lib + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-w", "-I", os.path.join(HERE, "emu"),
-                        "-I", os.path.join(ROOT, "paper_2412_13203_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
-                        cpp, "-o", tmp], check=True)
+        subprocess.run(["g++", "-shared", "-o", tmp] + objs, check=True)
         os.replace(tmp, lib)
     _LIBS[key] = C.CDLL(lib)
     return _LIBS[key]
