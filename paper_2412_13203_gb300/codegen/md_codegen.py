@@ -423,7 +423,9 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None):
     else:
         E(f"gb::boys_f64<{L}>(T, F, boys);")
     flops_setup = 16 + (kBoysCost(L))
-    if f32:
+    if mode_flat and R_PATH_LAMBDA is not None:
+        R = gen_R_path(em, L, r_targets(bra, ket, cds), f32, R_PATH_LAMBDA)
+    elif f32:
         R = gen_R_scaled(em, L, "F", ("PQsx", "PQsy", "PQsz"), "r2k")
     else:
         R = gen_R(em, L, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
@@ -1188,6 +1190,43 @@ def r_path(targets, lam=None):
             chosen[node] = best
             todo.update(c for c in _r_children(node, best) if c not in chosen)
     return chosen
+
+
+# Recursion order of the R values in the straight-line kernels: None keeps the
+# fixed t-then-u-then-v order over full levels (the code the GPU runs has been
+# measured with); a number selects Algorithm 1's greedy search with that lambda
+# over only the R values the kernel reads (checked on the CPU, not yet timed).
+R_PATH_LAMBDA = None
+
+
+def gen_R_path(em, L, targets, f32, lam):
+    """R^(0) for `targets` along the path r_path(targets, lam): deepest level
+    first; FP64 with the prefactor in the base values, FP32 in the scaled form
+    of gen_R_scaled (names PQs*, r2k*, F as there)."""
+    path = r_path(targets, lam)
+    X = ("PQsx", "PQsy", "PQsz") if f32 else ("PQx", "PQy", "PQz")
+    sym = {}
+    if not f32:
+        depth = max(n for (n, t, u, v) in path)
+        pw = [Sym(name="pref")]
+        for n in range(1, depth + 1):
+            pw.append(em.product([pw[-1], Sym(name="m2r")], f"pw{n}"))
+    for node in sorted(path, key=lambda x: (-x[0], x[1:])):
+        n, t, u, v = node
+        ax = path[node]
+        if ax is None:
+            if f32:
+                sym[node] = Sym(name=f"F[{n}]") if n % 2 == 0 else em.define(f"r{n}_000", f"-F[{n}]")
+            else:
+                sym[node] = em.product([pw[n], Sym(name=f"F[{n}]")], f"r{n}_000")
+            continue
+        k = (t, u, v)[ax]
+        kids = _r_children(node, ax)
+        terms = [(Sym(name=X[ax]), sym[kids[0]])]
+        if len(kids) == 2:
+            terms.append((Sym(name=f"r2k{k - 1}") if f32 else Sym(float(k - 1)), sym[kids[1]]))
+        sym[node] = em.lincomb(terms, f"r{n}_{t}_{u}_{v}")
+    return {(t, u, v): sym[(0, t, u, v)] for (_, t, u, v) in targets}
 
 
 def r_path_flops(chosen):

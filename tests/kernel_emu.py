@@ -187,7 +187,7 @@ class Problem:
     runtime lays them out (pairs canonicalised l_a >= l_b, grouped by class;
     for bra class = ket class only kets up to the bra)."""
 
-    def __init__(self, mol, D, oracle, lmax=2):
+    def __init__(self, mol, D, oracle, lmax=2, own_classes=False):
         self.mol, self.lmax = mol, lmax
         c = oracle.normalize(mol)
         l, K, off, atom = mol.shell_l, mol.shell_nprim, mol.shell_prim_offset, mol.shell_atom
@@ -225,7 +225,8 @@ class Problem:
         present = sorted(set(self.cls.tolist()))
         # compile every class when the molecule spans all l <= 2 classes (shared,
         # cached library), else only the classes this molecule has
-        self.only = None if lmax == 2 else {(self.pcs[x], self.pcs[y]) for x in present for y in present if y <= x}
+        self.only = None if (lmax == 2 and not own_classes) else \
+            {(self.pcs[x], self.pcs[y]) for x in present for y in present if y <= x}
         f = lambda x, t: np.ascontiguousarray(np.array(x, dtype=t))
         self.info, self.atoms = f(info, np.int32), f(atoms, np.int32)
         self.A, self.B, self.pp, self.pp2 = f(A, np.float64), f(B, np.float64), f(pp, np.float64), f(pp2, np.float64)

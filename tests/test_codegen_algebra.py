@@ -338,3 +338,28 @@ def test_r_path_search_is_a_valid_recursion(lam):
 def test_path_search_never_costs_more():
     for name, fixed, greedy in mg.path_report():
         assert greedy <= fixed, name
+
+
+@pytest.mark.parametrize("lam", [0.0, 1.0])
+def test_path_searched_r_emission(monkeypatch, lam):
+    """With the Algorithm-1 recursion order switched on, the straight-line
+    FP64/FP32 bodies and the FP32 range bodies still equal the oracle."""
+    monkeypatch.setattr(mg, "R_PATH_LAMBDA", lam)
+    rng = np.random.default_rng(int(lam * 10) + 3)
+    for bra, ket in [((1, 1), (1, 0)), ((2, 1), (1, 1)), ((2, 0), (2, 0))]:
+        sh = _shells(rng, [bra[0], bra[1], ket[0], ket[1]], 2)
+        ref = oracle.eri_quartet(sh).reshape(-1)
+        for real in ("double", "float"):
+            body, _ = mg.gen_quartet_body(bra, ket, real, True)
+            got = _run(body, bra, ket, sh)
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (bra, ket, real)
+    bra, ket = (2, 1), (2, 1)
+    sh = _shells(rng, [2, 1, 2, 1], 1)
+    ref = oracle.eri_quartet(sh)
+    na, nb, nc, nd = ref.shape
+    for c0, c1 in mg.crange_groups(bra, ket):
+        cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
+        body, _ = mg.gen_quartet_body(bra, ket, "float", True, cds)
+        got = _run(body, bra, ket, sh).reshape(na * nb, len(cds))
+        want = ref.reshape(na * nb, nc * nd)[:, cds]
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())

@@ -65,3 +65,17 @@ def test_emulated_schwarz_factors(seed, shells, lmax):
     Qo = oracle.schwarz(mol)
     want = np.array([Qo[a, b] for a, b in pr.pair_shells])
     assert np.abs(Q - want).max() <= 1e-11 * max(1.0, want.max()), np.abs(Q - want).max()
+
+
+def test_emulated_path_searched_r(monkeypatch):
+    """The kernels emitted with Algorithm 1's recursion order (off in the
+    built library) give the same J and K."""
+    import md_codegen
+    monkeypatch.setattr(md_codegen, "R_PATH_LAMBDA", 1.0)
+    mol, D = _mol(69, [0, 1, 2], 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle, own_classes=True)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    for prec, tol in ((0, 1e-10), (1, 2e-6)):
+        J, K = pr.jk(prec)
+        assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), prec
+        assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), prec
