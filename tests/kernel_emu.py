@@ -68,7 +68,7 @@ def _sources(lmax, only=None, ntu=8):
         if (bra, ket) in gqs:
             grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)total; ++blockIdx.x) "
                               f"eri_grad_{name}_f64(g); return 0;")
-    src = ['#include "eri_device.cuh"', "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
+    src = ['#include "eri_device.cuh"', "#include <vector>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
@@ -90,6 +90,30 @@ extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const
     a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
     a.rows.kofs = kofs; a.rows.klist = klist;
     a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.D = D; a.Df = Df; a.J = J; a.K = K; a.nbf = nbf;
+    blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    switch (X * 16 + Y) {
+""" + "\n".join(jk_cases) + """
+    }
+    return -1;
+}
+extern "C" int emu_jk_batched(int X, int Y, int prec, int nmol, const int* npair, void* const* info, void* const* A,
+                              void* const* B, void* const* pp, void* const* pp2, void* const* ppf, void* const* ppf2,
+                              void* const* D, void* const* Df, void* const* J, void* const* K, const int* nbf,
+                              int nrows, const long long* start, const int* bra, const int* ket0, const int* rowmol,
+                              const double* boys, const float* boysf, float tsmall) {
+    std::vector<gb::BatchMol> bm(nmol);
+    for (int m = 0; m < nmol; ++m) {
+        std::memset(&bm[m], 0, sizeof(gb::BatchMol));
+        bm[m].pairs = pv(npair[m], (const int4*)info[m], (const double4*)A[m], (const double4*)B[m],
+                         (const double4*)pp[m], (const double2*)pp2[m], (const float4*)ppf[m], (const float4*)ppf2[m],
+                         nullptr);
+        bm[m].D = (const double*)D[m]; bm[m].Df = (float*)Df[m];
+        bm[m].J = (double*)J[m]; bm[m].K = (double*)K[m]; bm[m].nbf = nbf[m];
+    }
+    gb::JKArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
+    a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.mols = bm.data(); a.row_mol = rowmol;
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
 """ + "\n".join(jk_cases) + """
@@ -315,3 +339,44 @@ class Problem:
                                   self._p(self.boys), self._p(self.D), self.nbf, self._p(self.atoms), self._p(g))
                 assert rc == 0
         return g
+
+
+def jk_batched(problems, prec, tsmall=1.0):
+    """J and K of several molecules through the kernels' batched mode: the
+    rows of all molecules concatenated per class, each tagged with its
+    molecule, the molecule's pairs and matrices looked up per row."""
+    lmax = problems[0].lmax
+    lib = load(lmax, None)
+    nmol = len(problems)
+    Js = [np.zeros((p.nbf, p.nbf)) for p in problems]
+    Ks = [np.zeros((p.nbf, p.nbf)) for p in problems]
+    arr = lambda xs: (C.c_void_p * nmol)(*[x.ctypes.data for x in xs])
+    ptrs = dict(info=arr([p.info for p in problems]), A=arr([p.A for p in problems]), B=arr([p.B for p in problems]),
+                pp=arr([p.pp for p in problems]), pp2=arr([p.pp2 for p in problems]),
+                ppf=arr([p.ppf for p in problems]), ppf2=arr([p.ppf2 for p in problems]),
+                D=arr([p.D for p in problems]), Df=arr([p.Df for p in problems]), J=arr(Js), K=arr(Ks))
+    npair = np.array([len(p.info) for p in problems], np.int32)
+    nbf = np.array([p.nbf for p in problems], np.int32)
+    p0 = problems[0]
+    for X in range(len(p0.pcs)):
+        for Y in range(X + 1):
+            bra, ket0, cnt, rowmol = [], [], [], []
+            for m, p in enumerate(problems):
+                r = p.rows(X, Y)
+                if r is None:
+                    continue
+                b, k, st = r
+                bra.append(b); ket0.append(k); cnt.append(np.diff(st)); rowmol.append(np.full(len(b), m, np.int32))
+            if not bra:
+                continue
+            bra, ket0, rowmol = np.concatenate(bra), np.concatenate(ket0), np.concatenate(rowmol)
+            start = np.concatenate([[0], np.cumsum(np.concatenate(cnt))]).astype(np.int64)
+            rc = lib.emu_jk_batched(X, Y, prec, nmol, npair.ctypes.data_as(C.c_void_p), ptrs["info"], ptrs["A"],
+                                    ptrs["B"], ptrs["pp"], ptrs["pp2"], ptrs["ppf"], ptrs["ppf2"], ptrs["D"],
+                                    ptrs["Df"], ptrs["J"], ptrs["K"], nbf.ctypes.data_as(C.c_void_p), len(bra),
+                                    start.ctypes.data_as(C.c_void_p), bra.ctypes.data_as(C.c_void_p),
+                                    ket0.ctypes.data_as(C.c_void_p), rowmol.ctypes.data_as(C.c_void_p),
+                                    p0.boys.ctypes.data_as(C.c_void_p), p0.boysf.ctypes.data_as(C.c_void_p),
+                                    C.c_float(tsmall))
+            assert rc == 0
+    return [J + J.T for J in Js], [K + K.T for K in Ks]

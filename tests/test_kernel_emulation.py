@@ -79,3 +79,16 @@ def test_emulated_path_searched_r(monkeypatch):
         J, K = pr.jk(prec)
         assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), prec
         assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), prec
+
+
+def test_emulated_batched_mode():
+    """The kernels' batched mode (rows of several molecules in one launch,
+    per-row molecule lookup) gives each molecule's J and K."""
+    mols = [_mol(70 + i, sh, 2, 2) for i, sh in enumerate([[0, 1, 2], [1, 2], [0, 0, 2]])]
+    prs = [kernel_emu.Problem(m, D, oracle) for m, D in mols]
+    for prec, tol in ((0, 1e-10), (1, 2e-6)):
+        Js, Ks = kernel_emu.jk_batched(prs, prec)
+        for (mol, D), J, K in zip(mols, Js, Ks):
+            Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+            assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), prec
+            assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), prec
