@@ -553,7 +553,6 @@ __global__ void k_np_of(const int4* info, long long n, long long* np) {
     if (k < n) np[k] = info[k].z;
 }
 
-// Mixed split of every row: kets with Q_i Q_j max|D| >= tau stay FP64 (they lead, Q descending).
 // Max |D| over every shell block (non-negative floats order like their bits).
 __global__ void k_dsh(const double* D, int n, const int* bf_shell, int nshell, unsigned int* dsh) {
     const long long n2 = (long long)n * n;
@@ -1126,7 +1125,7 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     return 0;
 }
 
-// Grid of a persistent class launch: `qpt` quartets per thread (the Workload
+// Grid of a persistent class launch: `qpt` work items per thread (the Workload
 // Allocator's unit of work, Algorithm 2 "Combine" doubles it), at least one
 // wave of one block per SM, at most 64 blocks per SM.
 int grid_for(long long total, int block, int qpt, int nsm) {
@@ -1315,9 +1314,10 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
 // Many molecules in one launch per (bra class, ket class): the rows of every
 // molecule are concatenated, each row carries its molecule index, and the
 // kernels read that molecule's pairs / D / J / K from a device table.  The
-// whole sequence (zeroing, optional mixed split, class launches on four
-// forked streams, symmetrisation) is captured once into a CUDA graph and
-// replayed while the molecule list, the matrices and the options are unchanged.
+// launch sequence (zeroing, a mixed build's scans and list fill, class
+// launches on four forked streams, symmetrisation) is captured into a CUDA
+// graph and replayed while the molecule list, the matrices and the options are
+// unchanged; a mixed build's split counts come from a pre-pass before it.
 struct BatchClass {
     int X = 0, Y = 0, nrows = 0;
     long long total = 0;
