@@ -26,10 +26,18 @@ paper's HGP recurrences.  Per shell quartet the generated kernel
      acc[ab][cd] (contracted over bra primitives),
   4. digests the block into J' and K' (fused, atomics).
 
-Two emission modes:
-  * "flat": everything straight-line (small classes, values in registers);
+Emission forms (chosen per class and precision):
+  * "flat": everything straight-line, values in registers (small classes;
+    FP32 kernels up to FLAT_F32_VALUES block values);
+  * FP32 ket-component ranges: the large l <= 2 classes' FP32 work as one
+    straight-line kernel per range of ket components c, each launched over
+    all quartets (crange_groups);
   * "loop": R stored in a (L+1)^3 cube, the ket-component loop runtime, the
-    per-axis E tables in small arrays (large classes, bounded code size).
+    per-axis E tables in small arrays (FP64 work of the large classes);
+  * "chunk": classes with an f shell, one thread per ket component c, a rolled
+    R recursion and bra E products in a local array (compact code).
+Every kernel decodes work items (a quartet split over up to split_of()
+threads by its bra primitive pairs) heaviest first.
 
 The generator also prints the exact FMA/FLOP count per primitive quartet of
 every class (used for the FLOP roofline).
