@@ -97,6 +97,18 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def cartesian_integrals(class_stats):
+    """Cartesian integrals of the screened unique quartets: sum over classes of
+    quartets x n_a n_b n_c n_d (classes named like "dp|ps")."""
+    lval = {"s": 0, "p": 1, "d": 2, "f": 3}
+    nc = lambda ch: (lval[ch] + 1) * (lval[ch] + 2) // 2
+    total = 0
+    for name, st in class_stats.items():
+        bra, ket = name.split("|")
+        total += st["nquartets"] * nc(bra[0]) * nc(bra[1]) * nc(ket[0]) * nc(ket[1])
+    return total
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -270,6 +282,10 @@ def main():
     dom_peak = peak32 if dom_prec == "fp32" else peak64
     achieved = dom_flops / (per_mx[(dom_cls, dom_prec)] * 1e-3)
     tot_flops = sum(s["flops"] for s in stats.values())
+    try:
+        n_cart = cartesian_integrals(stats)
+    except (KeyError, ValueError, IndexError):
+        n_cart = None
     per = {k[0]: float(np.mean(v)) for k, v in prof64.items() if k[1] == "fp64"}
     dom64 = max(per, key=per.get)
     ach64 = stats[dom64]["flops"] / (per[dom64] * 1e-3)
@@ -294,7 +310,10 @@ def main():
                      "steps": min(args.steps, 2), "energy_Eh": E64, "flops_per_s": tot_flops / (t_64 * 1e-3),
                      "roofline": {"bound": "alu", "kernel": f"eri_jk_{dom64} fp64", "achieved": ach64 / 1e12,
                                   "peak": peak64 / 1e12, "unit": "TFLOP/s", "frac": ach64 / peak64}},
-            "mixed": {"ms_per_step": t_mx, "energy_Eh": E_mx, "energy_minus_fp64_Eh": E_mx - E64,
+            "mixed": {"ms_per_step": t_mx,
+                      "primitive_quartets_per_s": pairs.nprimquartets * world / (t_mx * 1e-3),
+                      "cartesian_integrals_per_s": None if n_cart is None else n_cart * world / (t_mx * 1e-3),
+                      "energy_Eh": E_mx, "energy_minus_fp64_Eh": E_mx - E64,
                       "max_abs_dJ_vs_fp64": dJ, "max_abs_dK_vs_fp64": dK,
                       "fp32_share_of_flops": sum(v["fp32"]["flops"] for v in split.values()) / tot_flops},
             "e2e": {"value": nq * world / (t_e2e * 1e-3), "unit": "quartets/s", "ms_per_step": t_e2e,
