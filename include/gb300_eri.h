@@ -88,7 +88,12 @@ typedef struct jk_pairs_s* jk_pairs;
  * compute the Schwarz factors from a diagonal (ab|ab) pass, sort the pairs
  * by angular class, primitive count and Q, and enumerate the surviving
  * quartet rows per class.  Synchronous: returns after the device work is
- * complete.  *out receives a new handle.  cuda_stream: cudaStream_t or NULL. */
+ * complete.  *out receives a new handle.  cuda_stream: cudaStream_t or NULL.
+ * The arguments and the basis (l in 0..JK_LMAX and compiled, nprim >= 1,
+ * atom index in range, exponents > 0, finite coefficients, coordinates and
+ * threshold) are checked on the host before any CUDA call: a malformed input
+ * returns JK_ERR_INVALID (JK_ERR_UNSUPPORTED for an l that is not compiled)
+ * with *out = NULL and no device work. */
 int shellpairs_build(const jk_atoms* atoms, const jk_shells* shells, double thresh,
                      jk_pairs* out, void* cuda_stream);
 

@@ -845,11 +845,8 @@ int upload(DevBuf& d, const T* h, size_t n, cudaStream_t st) {
 
 int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk_pairs_s* h, cudaStream_t st) {
     const int S = shells->nshell;
-    CK(cudaGetDevice(&h->device));
-    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
-    int rc;
-    if ((rc = ensure_boys(h->device, st))) return rc;
-    // ---- host-side validation and basis offsets
+    // ---- host-side validation and basis offsets (before any CUDA call, so a
+    // malformed basis is reported the same way with or without a device)
     std::vector<int> bf(S);
     int nbf = 0, nprim_tot = 0;
     for (int s = 0; s < S; ++s) {
@@ -870,6 +867,10 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
             return fail(JK_ERR_INVALID, "non-positive exponent or non-finite coefficient");
     for (int i = 0; i < 3 * atoms->natom; ++i)
         if (!std::isfinite(atoms->xyz[i])) return fail(JK_ERR_INVALID, "non-finite coordinate");
+    CK(cudaGetDevice(&h->device));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+    int rc;
+    if ((rc = ensure_boys(h->device, st))) return rc;
     h->natom = atoms->natom;
     h->nshell = S;
     h->nbf = nbf;

@@ -1,8 +1,8 @@
 """Host-side argument checks of the C ABI (no GPU needed).
 
-Every entry point validates its arguments on the host before the first CUDA
-call, so a bad call returns a negative status with a message and never reaches
-the device.  These tests exercise exactly those paths through the exported
+Every entry point validates its arguments (and shellpairs_build the whole
+basis) on the host before the first CUDA call, so a bad call returns a
+negative status with a message and never reaches the device.  These tests exercise exactly those paths through the exported
 symbols; nothing here launches a kernel or touches a CUDA context."""
 import ctypes as C
 import math
@@ -176,3 +176,32 @@ def test_fma_peak_argument_checks(lib):
     f = C.c_double()
     assert lib.jk_fma_peak(JK_FP64, 0, C.byref(f), None) == JK_ERR_INVALID
     assert lib.jk_fma_peak(JK_FP64, 100, None, None) == JK_ERR_INVALID
+
+
+def corrupt(a, field, idx, value):
+    b = {k: v.copy() for k, v in a.items()}
+    b[field][idx] = value
+    return b
+
+
+@pytest.mark.parametrize("field,idx,value,code,word", [
+    ("l", 1, -1, JK_ERR_INVALID, "negative angular momentum"),
+    ("l", 1, 4, -5, "angular momentum"),
+    ("nprim", 0, 0, JK_ERR_INVALID, "without primitives"),
+    ("atom", 1, 2, JK_ERR_INVALID, "atom out of range"),
+    ("atom", 0, -1, JK_ERR_INVALID, "atom out of range"),
+    ("off", 1, -2, JK_ERR_INVALID, "negative primitive offset"),
+    ("exps", 1, 0.0, JK_ERR_INVALID, "exponent"),
+    ("exps", 2, -0.3, JK_ERR_INVALID, "exponent"),
+    ("exps", 0, math.nan, JK_ERR_INVALID, "exponent"),
+    ("coefs", 2, math.inf, JK_ERR_INVALID, "coefficient"),
+    ("xyz", (1, 2), math.nan, JK_ERR_INVALID, "coordinate"),
+])
+def test_shellpairs_build_rejects_malformed_basis(lib, field, idx, value, code, word):
+    """The basis checks run on the host before the first CUDA call, so they
+    report the same status whether or not a device is present."""
+    a = corrupt(molecule_arrays(), field, idx, value)  # keeps the arrays alive during the call
+    atoms, shells = structs(a)
+    rc, h = build(lib, atoms, shells)
+    assert rc == code and h.value is None
+    assert word in err(lib)
