@@ -97,6 +97,36 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def pure_leg(g, pairs, Dt, J, K, stream, flush, steps):
+    """Event-timed pure-basis steps: T D T^T, the mixed build, T^T J T and
+    T^T K T.  The pure density is T^T D T of the workload's density."""
+    import torch
+    Dp = g.sph_transform(pairs, Dt, "to_pure")
+    Dc = torch.empty_like(Dt)
+    Jp = torch.empty_like(Dp)
+    Kp = torch.empty_like(Dp)
+    tr, tot = [], []
+    for k in range(1 + steps):
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        g.sph_transform(pairs, Dp, "to_cartesian", out=Dc)
+        ev[1].record(stream)
+        g.jk_build(pairs, Dc, "mixed", J, K)
+        ev[2].record(stream)
+        g.sph_transform(pairs, J, "to_pure", out=Jp)
+        g.sph_transform(pairs, K, "to_pure", out=Kp)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if k >= 1:
+            tr.append(ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3]))
+            tot.append(ev[0].elapsed_time(ev[3]))
+    t = sum(tot) / len(tot)
+    return {"nsph": pairs.nsph, "nbf": pairs.nbf, "ms_per_step": t, "transform_ms": sum(tr) / len(tr),
+            "value": pairs.nquartets / (t * 1e-3), "unit": "quartets/s",
+            "energy_Eh": g.jk_energy(Dp, Jp, Kp), "steps": steps}
+
+
 def cartesian_integrals(class_stats):
     """Cartesian integrals of the screened unique quartets: sum over classes of
     quartets x n_a n_b n_c n_d (classes named like "dp|ps")."""
@@ -290,6 +320,14 @@ def main():
     dom64 = max(per, key=per.get)
     ach64 = stats[dom64]["flops"] / (per[dom64] * 1e-3)
 
+    # the same workload with its d shells pure: transform D to the Cartesian
+    # basis, mixed build, transform J and K back (reported beside the
+    # headline; the headline above is the Cartesian build)
+    try:
+        pure = pure_leg(g, pairs, Dt, J, K, stream, flush, args.steps)
+    except Exception as e:  # noqa: BLE001 -- reported, never fatal to the line
+        pure = {"error": f"{type(e).__name__}: {e}"}
+
     out = None
     if rank == 0:
         cpu = None
@@ -326,6 +364,7 @@ def main():
             "class_ms_mixed": {f"{k[0]} {k[1]}": round(v, 3)
                                for k, v in sorted(per_mx.items(), key=lambda x: -x[1])[:12]},
             "class_ms_fp64": {k: round(v, 3) for k, v in sorted(per.items(), key=lambda x: -x[1])},
+            "pure_d_shells": pure,
             "gpu_launches": int(lmx),
             "clocks": clk,
             "cpu_baseline": cpu,

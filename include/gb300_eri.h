@@ -227,6 +227,28 @@ int jk_profile(jk_pairs pairs, int max_rows, double* rows, int* nrows);
  * with CUDA events over `iters` dependent-chain iterations per thread. */
 int jk_fma_peak(jk_precision prec, int iters, double* flops_per_s, void* cuda_stream);
 
+/* Pure (real solid-harmonic) d and f shells.  The integrals of Sec. 2.2
+ * (Eq. 1) are over Cartesian components; a basis with pure d/f shells is
+ * served by transforming matrices between the two bases:
+ *     D_cart = T D_pure T^T,  J_pure = T^T J_cart T,  K_pure = T^T K_cart T,
+ * with T block-diagonal over the shells: identity for s and p (p stays x, y,
+ * z), and for l = 2, 3 the 2l+1 real solid harmonics S_lm, m = -l..l (no
+ * Condon-Shortley phase), each with the norm of the normalised axial
+ * Cartesian component.  jk_build and jk_grad on D_cart then give the pure-
+ * basis J/K and the gradient at fixed D_pure (T does not depend on the
+ * geometry).  The pure basis orders shells as the Cartesian one does. */
+typedef enum { JK_SPH_TO_CART = 0, JK_CART_TO_SPH = 1 } jk_sph_dir;
+
+/* Number of pure basis functions of a handle (host, no device work). */
+int jk_sph_nbf(jk_pairs pairs, int* nsph);
+
+/* out = T in T^T (JK_SPH_TO_CART: in nsph x nsph, out nbf x nbf) or
+ * out = T^T in T (JK_CART_TO_SPH: in nbf x nbf, out nsph x nsph); DEVICE
+ * pointers, row-major float64, caller-owned; `in` and `out` must not overlap
+ * (JK_ERR_INVALID).  Asynchronous on cuda_stream; the first call on a handle
+ * also uploads the shell layout and the coefficient tables. */
+int jk_sph_transform(jk_pairs pairs, jk_sph_dir dir, const double* in, double* out, void* cuda_stream);
+
 void shellpairs_free(jk_pairs pairs);
 
 /* Message of the last failure on the calling thread ("" if none). */

@@ -43,7 +43,7 @@ EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_bui
            "jk_energy_noalloc",
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
-           "jk_set_tuning", "jk_split_stats"]
+           "jk_set_tuning", "jk_split_stats", "jk_sph_nbf", "jk_sph_transform"]
 
 
 def load():
@@ -75,6 +75,8 @@ def load():
         lib.jk_split_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
         lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
+        lib.jk_sph_nbf.argtypes = [vp, C.POINTER(C.c_int)]
+        lib.jk_sph_transform.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.shellpairs_free.argtypes = [vp]
         lib.shellpairs_free.restype = None
         lib.jk_last_error.restype = C.c_char_p
@@ -126,6 +128,9 @@ class ShellPairs:
         npair, nq, npq = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib.shellpairs_info(h, C.byref(nbf), C.byref(npair), C.byref(nq), C.byref(npq)))
         self.nbf, self.npairs, self.nquartets, self.nprimquartets = nbf.value, npair.value, nq.value, npq.value
+        ns = C.c_int()
+        _check(lib.jk_sph_nbf(h, C.byref(ns)))
+        self.nsph = ns.value  # basis size with pure d and f shells
         self._keep = None
 
     def free(self):
@@ -180,6 +185,39 @@ def jk_grad(pairs: ShellPairs, D, precision: str = "fp64", out=None, stream=None
         out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
     _check(load().jk_grad(pairs.handle, _dev_ptr(D), _dev_ptr(out), _PREC[precision], _stream_ptr(stream)))
     return out
+
+
+_SPH_DIR = {"to_cartesian": 0, "to_pure": 1}
+
+
+def sph_transform(pairs: ShellPairs, M, direction: str, out=None, stream=None):
+    """``to_cartesian``: T M T^T (M nsph x nsph, e.g. a pure-basis density);
+    ``to_pure``: T^T M T (M nbf x nbf, e.g. Cartesian J or K).  T is the
+    block-diagonal Cartesian-to-pure matrix of the handle's shells."""
+    import torch
+    n_in, n_out = (pairs.nsph, pairs.nbf) if direction == "to_cartesian" else (pairs.nbf, pairs.nsph)
+    if tuple(M.shape) != (n_in, n_in):
+        raise ValueError(f"expected a {n_in} x {n_in} matrix")
+    if out is None:
+        out = torch.empty((n_out, n_out), dtype=torch.float64, device=M.device)
+    elif tuple(out.shape) != (n_out, n_out):
+        raise ValueError(f"out must be {n_out} x {n_out}")
+    _check(load().jk_sph_transform(pairs.handle, _SPH_DIR[direction], _dev_ptr(M), _dev_ptr(out),
+                                   _stream_ptr(stream)))
+    return out
+
+
+def jk_build_pure(pairs: ShellPairs, D_pure, precision: str = "fp64", stream=None):
+    """J and K over pure d/f shells for a pure-basis density (nsph x nsph):
+    D is taken to the Cartesian basis, built, and J, K taken back."""
+    Dc = sph_transform(pairs, D_pure, "to_cartesian", stream=stream)
+    J, K = jk_build(pairs, Dc, precision, stream=stream)
+    return sph_transform(pairs, J, "to_pure", stream=stream), sph_transform(pairs, K, "to_pure", stream=stream)
+
+
+def jk_grad_pure(pairs: ShellPairs, D_pure, precision: str = "fp64", out=None, stream=None):
+    """dE/dR at fixed pure-basis density: the Cartesian gradient at T D T^T."""
+    return jk_grad(pairs, sph_transform(pairs, D_pure, "to_cartesian", stream=stream), precision, out, stream)
 
 
 def jk_build_batched(pairs_list, Ds, Js=None, Ks=None, precision: str = "fp64", stream=None):

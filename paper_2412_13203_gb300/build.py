@@ -40,12 +40,15 @@ def build(force: bool = False, lmax: int = 3, jobs: int | None = None, verbose: 
     sys.path.insert(0, os.path.join(HERE, "codegen"))
     try:
         import md_codegen
+        import sph_codegen
     finally:
         sys.path.pop(0)
     os.makedirs(GEN, exist_ok=True)
     gen_files, _ = md_codegen.generate(GEN, lmax)
+    gen_files.append(sph_codegen.emit(GEN))
     hand = [os.path.join(CSRC, "runtime.cu")]
-    headers = [os.path.join(CSRC, "eri_device.cuh"), os.path.join(ROOT, "include", "gb300_eri.h")]
+    headers = [os.path.join(CSRC, "eri_device.cuh"), os.path.join(CSRC, "sph_transform.cuh"),
+               os.path.join(ROOT, "include", "gb300_eri.h")]
     srcs = hand + gen_files
     objs = []
     todo = []

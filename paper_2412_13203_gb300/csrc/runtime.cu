@@ -28,6 +28,7 @@
 
 #include "eri_device.cuh"
 #include "gb300_eri.h"
+#include "sph_transform.cuh"
 
 int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s);
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
@@ -37,6 +38,7 @@ int gb_grad_lmax();
 int gb_class_threads(int bra_cls, int ket_cls, int prec);
 int gb_class_split(int bra_cls, int ket_cls);
 extern "C" int gb_num_pair_classes();
+extern "C" int gb_sph_table(const double** coef, const int** off);
 
 namespace {
 
@@ -171,6 +173,12 @@ struct jk_pairs_s {
     DevBuf split_tot;                               // per class: FP32, FP64 quartets, FP32, FP64 items (last mixed build)
     DevBuf npre;                                    // exclusive prefix of primitive pairs over the kept pairs
     DevBuf scratch;                                 // small reductions
+    std::vector<int> shell_l;                       // host copy of every shell's l (caller's order)
+    int nsph = 0;                                   // basis size with pure d and f shells
+    DevBuf sph_shell;                               // int4 per shell: l, first Cartesian, first pure index, table offset
+    DevBuf sph_owner;                               // int per pure basis function: its shell
+    DevBuf sph_coef;                                // Cartesian-to-pure coefficient tables
+    bool sph_ready = false;
     std::vector<ProfRec> prof;
     ~jk_pairs_s() {
         for (auto& r : prof) {
@@ -874,6 +882,9 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     h->natom = atoms->natom;
     h->nshell = S;
     h->nbf = nbf;
+    h->shell_l.assign(shells->l, shells->l + S);
+    h->nsph = 0;
+    for (int s = 0; s < S; ++s) h->nsph += shells->l[s] >= 2 ? 2 * shells->l[s] + 1 : (shells->l[s] + 1) * (shells->l[s] + 2) / 2;
     h->thresh = thresh;
     // ---- upload
     DevBuf d_atom, d_l, d_np, d_off, d_bf, d_e, d_c, d_cn;
@@ -1879,6 +1890,37 @@ __global__ void k_fma_peak(int iters, T* sink) {
     if (r == (T)-12345) *sink = r;  // keeps the chains alive
 }
 
+// ------------------------------------------------------------------ pure shells
+// Device data of the Cartesian <-> pure transform, uploaded on first use: per
+// shell (l, first Cartesian index, first pure index), the owning shell of
+// every pure basis function, and the coefficient tables of the generated
+// sph_table.cu.  The Cartesian owners are the handle's bf_shell.
+int sph_prepare(jk_pairs_s* h, cudaStream_t st) {
+    if (h->sph_ready) return 0;
+    const double* coef = nullptr;
+    const int* off = nullptr;
+    const int lmax = gb_sph_table(&coef, &off);
+    if (lmax < gb::kSphLmax) return fail(JK_ERR_UNSUPPORTED, "pure-shell table stops below l = 3");
+    std::vector<int4> sh(h->nshell);
+    std::vector<int> owner(h->nsph);
+    int c = 0, p = 0;
+    for (int s = 0; s < h->nshell; ++s) {
+        const int l = h->shell_l[s];
+        const int np = l >= 2 ? 2 * l + 1 : (l + 1) * (l + 2) / 2;
+        sh[s] = make_int4(l, c, p, off[l]);
+        for (int k = 0; k < np; ++k) owner[p + k] = s;
+        c += (l + 1) * (l + 2) / 2;
+        p += np;
+    }
+    if (c != h->nbf || p != h->nsph) return fail(JK_ERR_INVALID, "pure-shell layout does not match the handle");
+    int rc;
+    if ((rc = upload(h->sph_shell, sh.data(), sh.size(), st))) return rc;
+    if ((rc = upload(h->sph_owner, owner.data(), owner.size(), st))) return rc;
+    if ((rc = upload(h->sph_coef, coef, (size_t)off[gb::kSphLmax + 1], st))) return rc;
+    h->sph_ready = true;
+    return 0;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -2239,6 +2281,44 @@ int jk_fma_peak(jk_precision prec, int iters, double* flops, void* cuda_stream) 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *flops = 2.0 * 8 * 16 * (double)iters * blocks * threads / (ms * 1e-3);
+    return JK_OK;
+}
+
+int jk_sph_nbf(jk_pairs h, int* nsph) {
+    if (!h || !nsph) return fail(JK_ERR_INVALID, "bad argument");
+    *nsph = h->nsph;
+    return JK_OK;
+}
+
+int jk_sph_transform(jk_pairs h, jk_sph_dir dir, const double* in, double* out, void* cuda_stream) {
+    g_err.clear();
+    if (!h || !in || !out) return fail(JK_ERR_INVALID, "null argument");
+    if (dir != JK_SPH_TO_CART && dir != JK_CART_TO_SPH) return fail(JK_ERR_INVALID, "direction");
+    const int n_in = dir == JK_SPH_TO_CART ? h->nsph : h->nbf;
+    const int n_out = dir == JK_SPH_TO_CART ? h->nbf : h->nsph;
+    const uintptr_t i0 = (uintptr_t)in, i1 = i0 + sizeof(double) * (size_t)n_in * n_in;
+    const uintptr_t o0 = (uintptr_t)out, o1 = o0 + sizeof(double) * (size_t)n_out * n_out;
+    if (i0 < o1 && o0 < i1) return fail(JK_ERR_INVALID, "in and out overlap");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int rc;
+    if ((rc = sph_prepare(h, st))) return rc;
+    gb::SphArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.n_in = n_in;
+    a.n_out = n_out;
+    a.dir = dir == JK_SPH_TO_CART ? 0 : 1;
+    a.owner = dir == JK_SPH_TO_CART ? h->bf_shell.as<int>() : h->sph_owner.as<int>();
+    a.shell = h->sph_shell.as<int4>();
+    a.coef = h->sph_coef.as<double>();
+    const long long total = (long long)n_out * n_out;
+    const unsigned grid = (unsigned)std::min<long long>(nblk(total, 256), (long long)h->nsm * 8);
+    gb::k_sph_transform<<<grid, 256, 0, st>>>(a);
+    CKL();
     return JK_OK;
 }
 
