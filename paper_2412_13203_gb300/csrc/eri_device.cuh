@@ -180,18 +180,6 @@ __device__ __forceinline__ void locate_row(const RowsView& rv, long long t, int&
     li = t - __ldg(rv.start + lo);
 }
 
-// Largest r with start[r] <= t (t < start[nrows]).
-__device__ __forceinline__ void locate_quartet(const RowsView& rv, long long t, int& bra, int& ket, int& row) {
-    int lo = 0, hi = rv.nrows;  // invariant: start[lo] <= t < start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(rv.start + mid) <= t) lo = mid; else hi = mid;
-    }
-    bra = __ldg(rv.bra + lo);
-    ket = __ldg(rv.ket0 + lo) + (int)(t - __ldg(rv.start + lo));
-    row = lo;
-}
-
 // ------------------------------------------------------------------ digestion
 // Fused J/K update of one unique shell quartet (ab|cd), acc[((a*NB+b)*NC+c)*ND+d],
 // already scaled by the degeneracy factor s.  With the eight permutational
