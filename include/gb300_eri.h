@@ -131,9 +131,12 @@ int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, vo
 /* Many independent molecules in one launch sequence (one persistent launch per
  * angular class over all molecules' work), optionally captured into a CUDA
  * graph (JK_OPT_GRAPH) that is replayed while the molecules, matrix pointers
- * and options stay the same.  D[i], J[i], K[i] are device pointers of
- * molecule i.  JK_MIXED: a split pass outside the graph selects the FP64
- * quartets as jk_build does and synchronises once to size the lists. */
+ * and options stay the same.  The launch plan is cached across calls by the
+ * identity of the handles (a handle built later never matches one freed
+ * before, even at the same address) and shellpairs_free of any of its handles
+ * releases it.  D[i], J[i], K[i] are device pointers of molecule i.
+ * JK_MIXED: a split pass outside the graph selects the FP64 quartets as
+ * jk_build does and synchronises once to size the lists. */
 int jk_build_batched(int nmol, const jk_pairs* pairs, const double* const* D, double* const* J,
                      double* const* K, jk_precision prec, void* cuda_stream);
 

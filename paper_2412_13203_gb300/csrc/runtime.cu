@@ -18,6 +18,7 @@
 //     atomics in the generated kernels.
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -146,6 +147,7 @@ struct ProfRec {
 }  // namespace
 
 struct jk_pairs_s {
+    unsigned long long serial = 0;                  // unique per handle ever built (never reused)
     int device = 0;
     int natom = 0, nshell = 0, nbf = 0;
     long long npair_all = 0, npair = 0, nprimpair = 0;
@@ -1344,6 +1346,7 @@ struct BatchClass {
 
 struct BatchPlan {
     std::vector<jk_pairs> mols;
+    std::vector<unsigned long long> serial;  // of every handle: a freed handle's address can come back
     std::vector<const double*> D;
     std::vector<double*> J, K;
     int prec = 0, device = 0, max_n = 0, graph = 0;
@@ -1358,6 +1361,7 @@ struct BatchPlan {
     long long launches = 0;        // kernels of the (captured) launch sequence
     long long launches_total = 0;  // plus the pre-pass of a mixed build
     ~BatchPlan() {
+        if (cs) cudaStreamSynchronize(cs);  // the plan's last launch sequence ends on cs
         if (exec) cudaGraphExecDestroy(exec);
         for (auto& x : ps) if (x) cudaStreamDestroy(x);
         if (cs) cudaStreamDestroy(cs);
@@ -1367,6 +1371,7 @@ struct BatchPlan {
     }
 };
 std::mutex g_batch_mu;
+std::atomic<unsigned long long> g_serial{0};
 std::unique_ptr<BatchPlan> g_plan;
 
 __global__ void k_offset_copy(const long long* src, int n, long long off, long long* dst) {
@@ -1747,12 +1752,14 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
     bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
                 g_plan->tau == g_opt.tau && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph;
     for (int m = 0; same && m < nmol; ++m)
-        same = g_plan->mols[m] == pairs[m] && g_plan->D[m] == D[m] && g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
+        same = g_plan->mols[m] == pairs[m] && g_plan->serial[m] == pairs[m]->serial && g_plan->D[m] == D[m] &&
+               g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
     int rc;
     if (!same) {
         g_plan.reset(new BatchPlan());
         BatchPlan& P = *g_plan;
         P.mols.assign(pairs, pairs + nmol);
+        for (int m = 0; m < nmol; ++m) P.serial.push_back(pairs[m]->serial);
         P.D.assign(D, D + nmol);
         P.J.assign(J, J + nmol);
         P.K.assign(K, K + nmol);
@@ -1944,6 +1951,7 @@ int shellpairs_build(const jk_atoms* atoms, const jk_shells* shells, double thre
         delete h;
         return rc;
     }
+    h->serial = ++g_serial;
     *out = h;
     return JK_OK;
 }
@@ -2322,6 +2330,13 @@ int jk_sph_transform(jk_pairs h, jk_sph_dir dir, const double* in, double* out, 
     return JK_OK;
 }
 
-void shellpairs_free(jk_pairs h) { delete h; }
+void shellpairs_free(jk_pairs h) {
+    if (!h) return;
+    {   // a cached batch plan that reads this handle's device arrays goes with it
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        if (g_plan && std::find(g_plan->mols.begin(), g_plan->mols.end(), h) != g_plan->mols.end()) g_plan.reset();
+    }
+    delete h;
+}
 
 }  // extern "C"
