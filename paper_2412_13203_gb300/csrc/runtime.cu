@@ -132,6 +132,7 @@ BoysTables g_boys[64];
 
 struct Options {
     double tau = 1e-2;
+    double eps = 0.0;  // density screening of mixed builds (0: off)
     double tsmall = 1.0;
     int check_sym = 0;
     int graph = 1;
@@ -573,54 +574,7 @@ __global__ void k_dsh(const double* D, int n, const int* bf_shell, int nshell, u
     }
 }
 
-// The largest |D| block a quartet's J and K updates touch: D_ab and D_cd
-// (Coulomb), D_ac, D_ad, D_bc, D_bd (exchange).
-__device__ __forceinline__ float quartet_dmax(const float* dsh, int nshell, int2 ab, int2 cd) {
-    const float* r_a = dsh + (size_t)ab.x * nshell;
-    const float* r_b = dsh + (size_t)ab.y * nshell;
-    float m = fmaxf(r_a[ab.y], dsh[(size_t)cd.x * nshell + cd.y]);
-    m = fmaxf(m, fmaxf(r_a[cd.x], r_a[cd.y]));
-    return fmaxf(m, fmaxf(r_b[cd.x], r_b[cd.y]));
-}
-
-// Mixed split of every row.  Kets are sorted by Q descending, so the kets with
-// Q_i Q_j max|D| >= tau (global bound) are a prefix; inside that prefix a
-// quartet stays FP64 only if its density-weighted bound Q_i Q_j max(D blocks it
-// touches) >= tau, else it is demoted to FP32.  Writes per-row quartet and
-// work-item counts of the three parts and adds the FP32 / FP64 quartet totals.
-__global__ void k_rows_split(const long long* start, const int* rbra, const int* rket0, int nrows, const double4* A,
-                             const double* dmax, double tau, const int4* info, const int2* psh, const float* dsh,
-                             int nshell, int P, long long* c64, long long* cdem, long long* c32, int* k32,
-                             long long* w64, long long* wdem, long long* w32, unsigned long long* qtot) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const int i = rbra[r];
-    const long long m = min(P, info[i].z);
-    const long long c = start[r + 1] - start[r];
-    const int s = rket0[r];
-    const double qi = A[i].w;
-    const double qg = qi * (*dmax);
-    int lo = s, hi = s + (int)c;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (qg * A[mid].w >= tau) lo = mid + 1; else hi = mid;
-    }
-    const int2 ab = psh[i];
-    long long n64 = 0;
-    for (int j = s; j < lo; ++j)
-        if (qi * A[j].w * (double)quartet_dmax(dsh, nshell, ab, psh[j]) >= tau) ++n64;
-    const long long nd = (lo - s) - n64, n32 = c - (lo - s);
-    c64[r] = n64;
-    cdem[r] = nd;
-    c32[r] = n32;
-    k32[r] = lo;
-    w64[r] = n64 * m;
-    wdem[r] = nd * m;
-    w32[r] = n32 * m;
-    atomicAdd(qtot, (unsigned long long)(n32 + nd));
-    atomicAdd(qtot + 1, (unsigned long long)n64);
-    atomicAdd(qtot + 7, (unsigned long long)nd);
-}
+#include "split_kernels.cuh"
 
 // Primitive quartets and (quartet x bra primitive pair) units of list rows.
 __global__ void k_list_primq(const long long* cnt, const long long* ofs, const int* klist, const int* rbra, int nrows,
@@ -633,23 +587,6 @@ __global__ void k_list_primq(const long long* cnt, const long long* ofs, const i
     for (long long k = 0; k < c; ++k) kp += info[klist[ofs[r] + k]].z;
     atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
     atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
-}
-
-// Second pass: the kets of every row's FP64 prefix into the FP64 and demoted
-// lists, at the row offsets l64 / ldem (exclusive prefixes of c64 / cdem).
-__global__ void k_rows_fill(const int* rbra, const int* rket0, const int* k32, int nrows, const double4* A, double tau,
-                            const int2* psh, const float* dsh, int nshell, const long long* l64, const long long* ldem,
-                            int* list64, int* listdem) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const int i = rbra[r];
-    const double qi = A[i].w;
-    const int2 ab = psh[i];
-    long long o64 = l64[r], od = ldem[r];
-    for (int j = rket0[r]; j < k32[r]; ++j) {
-        if (qi * A[j].w * (double)quartet_dmax(dsh, nshell, ab, psh[j]) >= tau) list64[o64++] = j;
-        else listdem[od++] = j;
-    }
 }
 
 // Work items of every row: quartets x min(P, K_ab) (bra primitive pairs of the
@@ -1207,7 +1144,7 @@ int split_count(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* spl
     if ((rc = cr.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
     k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(
         cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(), cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
-        h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell, gb_class_split(cr.bra_cls, cr.ket_cls),
+        g_opt.eps, h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell, gb_class_split(cr.bra_cls, cr.ket_cls),
         cr.c64.as<long long>(), cr.cdem.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>(), cr.w64.as<long long>(),
         cr.wdem.as<long long>(), cr.w32.as<long long>(), reinterpret_cast<unsigned long long*>(split_tot));
     CKL();
@@ -1229,7 +1166,7 @@ int split_fill(jk_pairs_s* h, ClassRows& cr, long long* split_tot, int* list64, 
     if ((rc = scan_into(cr.c64.as<long long>(), cr.l64.as<long long>(), n1, split_tot + 5, scr, st))) return rc;
     if ((rc = scan_into(cr.cdem.as<long long>(), cr.ldem.as<long long>(), n1, split_tot + 6, scr, st))) return rc;
     k_rows_fill<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.bra.as<int>(), cr.ket0.as<int>(), cr.k32.as<int>(), cr.nrows,
-                                                     h->A.as<double4>(), g_opt.tau, h->pair_sh.as<int2>(),
+                                                     h->A.as<double4>(), g_opt.tau, g_opt.eps, h->pair_sh.as<int2>(),
                                                      h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>(),
                                                      cr.ldem.as<long long>(), list64, listdem);
     CKL();
@@ -1350,7 +1287,7 @@ struct BatchPlan {
     std::vector<const double*> D;
     std::vector<double*> J, K;
     int prec = 0, device = 0, max_n = 0, graph = 0;
-    double tau = 0.0, tsmall = 0.0;
+    double tau = 0.0, eps = 0.0, tsmall = 0.0;
     long long nquartets = 0;
     DevBuf bm, dmax, split_tot;
     DevBuf list64, listdem;  // mixed: FP64 and demoted ket lists, one segment per class
@@ -1429,61 +1366,6 @@ __global__ void k_dsh_batched(const gb::BatchMol* bm) {
         const int i = (int)(k / n), j = (int)(k - (long long)i * n);
         atomicMax(reinterpret_cast<unsigned int*>(m.Dsh) + (size_t)m.bf_shell[i] * m.nshell + m.bf_shell[j],
                   __float_as_uint((float)fabs(m.D[k])));
-    }
-}
-
-// k_rows_split for batched rows (each row's molecule from rowmol).
-__global__ void k_rows_split_batched(const long long* start, const int* rbra, const int* rket0, const int* rowmol,
-                                     int nrows, const gb::BatchMol* bm, const unsigned long long* dmax, double tau,
-                                     int P, long long* c64, long long* cdem, long long* c32, int* k32, long long* w64,
-                                     long long* wdem, long long* w32, unsigned long long* qtot) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const gb::BatchMol& mol = bm[rowmol[r]];
-    const double4* A = mol.pairs.A;
-    const int i = rbra[r];
-    const long long ms = min(P, mol.pairs.info[i].z);
-    const long long c = start[r + 1] - start[r];
-    const int s = rket0[r];
-    const double qi = A[i].w;
-    const double qg = qi * __longlong_as_double((long long)dmax[rowmol[r]]);
-    int lo = s, hi = s + (int)c;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (qg * A[mid].w >= tau) lo = mid + 1; else hi = mid;
-    }
-    const int2 ab = mol.psh[i];
-    long long n64 = 0;
-    for (int j = s; j < lo; ++j)
-        if (qi * A[j].w * (double)quartet_dmax(mol.Dsh, mol.nshell, ab, mol.psh[j]) >= tau) ++n64;
-    const long long nd = (lo - s) - n64, n32 = c - (lo - s);
-    c64[r] = n64;
-    cdem[r] = nd;
-    c32[r] = n32;
-    k32[r] = lo;
-    w64[r] = n64 * ms;
-    wdem[r] = nd * ms;
-    w32[r] = n32 * ms;
-    atomicAdd(qtot, (unsigned long long)(n32 + nd));
-    atomicAdd(qtot + 1, (unsigned long long)n64);
-    atomicAdd(qtot + 7, (unsigned long long)nd);
-}
-
-// k_rows_fill for batched rows.
-__global__ void k_rows_fill_batched(const int* rbra, const int* rket0, const int* k32, const int* rowmol, int nrows,
-                                    const gb::BatchMol* bm, double tau, const long long* l64, const long long* ldem,
-                                    int* list64, int* listdem) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const gb::BatchMol& mol = bm[rowmol[r]];
-    const double4* A = mol.pairs.A;
-    const int i = rbra[r];
-    const double qi = A[i].w;
-    const int2 ab = mol.psh[i];
-    long long o64 = l64[r], od = ldem[r];
-    for (int j = rket0[r]; j < k32[r]; ++j) {
-        if (qi * A[j].w * (double)quartet_dmax(mol.Dsh, mol.nshell, ab, mol.psh[j]) >= tau) list64[o64++] = j;
-        else listdem[od++] = j;
     }
 }
 
@@ -1649,7 +1531,7 @@ int enqueue_batch(BatchPlan& P) {
             int* l64 = P.list64.as<int>() + bc.off64;
             int* ldm = P.listdem.as<int>() + bc.offdem;
             k_rows_fill_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(bc.bra.as<int>(), bc.ket0.as<int>(), bc.k32.as<int>(),
-                                                                    bc.rowmol.as<int>(), bc.nrows, bm, P.tau,
+                                                                    bc.rowmol.as<int>(), bc.nrows, bm, P.tau, P.eps,
                                                                     bc.l64.as<long long>(), bc.ldem.as<long long>(),
                                                                     l64, ldm);
             CKL();
@@ -1694,7 +1576,7 @@ int batch_prepass(BatchPlan& P, bool* relaid) {
         BatchClass& bc = P.cls[k];
         k_rows_split_batched<<<nblk(bc.nrows, 256), 256, 0, P.cs>>>(
             bc.start.as<long long>(), bc.bra.as<int>(), bc.ket0.as<int>(), bc.rowmol.as<int>(), bc.nrows, bm,
-            P.dmax.as<unsigned long long>(), P.tau, gb_class_split(bc.X, bc.Y), bc.c64.as<long long>(),
+            P.dmax.as<unsigned long long>(), P.tau, P.eps, gb_class_split(bc.X, bc.Y), bc.c64.as<long long>(),
             bc.cdem.as<long long>(), bc.c32.as<long long>(), bc.k32.as<int>(), bc.w64.as<long long>(),
             bc.wdem.as<long long>(), bc.w32.as<long long>(),
             reinterpret_cast<unsigned long long*>(P.split_tot.as<long long>() + kSplitSlots * k));
@@ -1750,7 +1632,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
     int dev = -1;
     CK(cudaGetDevice(&dev));
     bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
-                g_plan->tau == g_opt.tau && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph;
+                g_plan->tau == g_opt.tau && g_plan->eps == g_opt.eps && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph;
     for (int m = 0; same && m < nmol; ++m)
         same = g_plan->mols[m] == pairs[m] && g_plan->serial[m] == pairs[m]->serial && g_plan->D[m] == D[m] &&
                g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
@@ -1766,6 +1648,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
         P.prec = prec;
         P.device = dev;
         P.tau = g_opt.tau;
+        P.eps = g_opt.eps;
         P.tsmall = g_opt.tsmall;
         P.graph = g_opt.graph;
         if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
@@ -2100,6 +1983,10 @@ int jk_set_option(jk_option opt, double v) {
         case JK_OPT_CHECK_SYMMETRY: g_opt.check_sym = v != 0.0; return JK_OK;
         case JK_OPT_GRAPH: g_opt.graph = v != 0.0; return JK_OK;
         case JK_OPT_PROFILE: g_opt.profile = v != 0.0; return JK_OK;
+        case JK_OPT_DENSITY_SCREEN:
+            if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "density screening threshold");
+            g_opt.eps = v;
+            return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2112,6 +1999,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_CHECK_SYMMETRY: *v = g_opt.check_sym; return JK_OK;
         case JK_OPT_GRAPH: *v = g_opt.graph; return JK_OK;
         case JK_OPT_PROFILE: *v = g_opt.profile; return JK_OK;
+        case JK_OPT_DENSITY_SCREEN: *v = g_opt.eps; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }

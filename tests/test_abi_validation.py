@@ -205,3 +205,18 @@ def test_shellpairs_build_rejects_malformed_basis(lib, field, idx, value, code, 
     rc, h = build(lib, atoms, shells)
     assert rc == code and h.value is None
     assert word in err(lib)
+
+
+def test_density_screen_option(lib):
+    OPT_SCREEN = 5
+    v = C.c_double(-1.0)
+    assert lib.jk_get_option(OPT_SCREEN, C.byref(v)) == JK_OK and v.value == 0.0  # off by default
+    try:
+        assert lib.jk_set_option(OPT_SCREEN, 1e-9) == JK_OK
+        assert lib.jk_get_option(OPT_SCREEN, C.byref(v)) == JK_OK and v.value == 1e-9
+        for bad in (-1e-12, math.nan, math.inf):
+            assert lib.jk_set_option(OPT_SCREEN, bad) == JK_ERR_INVALID
+            assert "density screening" in err(lib)
+        assert lib.jk_get_option(OPT_SCREEN, C.byref(v)) == JK_OK and v.value == 1e-9
+    finally:
+        assert lib.jk_set_option(OPT_SCREEN, 0.0) == JK_OK

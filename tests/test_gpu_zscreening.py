@@ -1,0 +1,135 @@
+"""GPU parity of density screening in mixed builds (JK_OPT_DENSITY_SCREEN):
+the quartets the GPU keeps are exactly those the screening rule keeps
+(counted through jk_last_split), J and K equal the oracle's J and K over that
+quartet set, an incremental build J(D0) + J(D1 - D0) reproduces J(D1), and
+the batched form screens as the single-molecule form does."""
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TAU = 1e-2
+MARGIN = 1e-5  # the GPU's Q (quantised) and FP32 block maxima differ from the oracle's by < 1e-7 relative
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_13203_gb300 as g
+    g.load()
+    assert g.get_option("mixed_tau") == TAU
+    yield g
+    g.set_option("density_screen", 0.0)
+
+
+def _mol(seed):
+    return molgen.random_molecule(600 + seed, 4, [0, 0, 1, 2], 1, 3, 0.1, 50.0, layout="lattice", spacing=2.2)
+
+
+def _unique_quartets(S):
+    pairs = [(a, b) for a in range(S) for b in range(a + 1)]
+    return np.array([(a, b, c, d) for i, (a, b) in enumerate(pairs) for (c, d) in pairs[:i + 1]], np.int64)
+
+
+def _bounds(mol, D):
+    """Global and density-weighted bounds of every unique quartet (oracle Q)."""
+    Q = oracle.schwarz(mol)
+    off = np.concatenate([mol.shell_offsets(), [mol.nbf]])
+    S = mol.nshell
+    Db = np.array([[np.abs(D[off[a]:off[a + 1], off[b]:off[b + 1]]).max() for b in range(S)] for a in range(S)])
+    q = _unique_quartets(S)
+    a, b, c, d = q.T
+    qab, qcd = Q[a, b], Q[c, d]
+    glob = qab * np.abs(D).max() * qcd
+    w = qab * qcd * np.max([Db[a, b], Db[c, d], Db[a, c], Db[a, d], Db[b, c], Db[b, d]], axis=0)
+    return q, glob, w
+
+
+def _kept(glob, w, eps):
+    return (glob >= eps) & ((glob < TAU) | (w >= eps))
+
+
+def _pick_eps(glob, w, frac):
+    """A threshold near the `frac` quantile of the bounds with no bound within
+    MARGIN of it (nor of tau), so both sides classify every quartet alike."""
+    for e in np.quantile(w[w > 0], frac) * np.array([1.0, 1.13, 0.89, 1.27, 0.79, 1.41]):
+        close = lambda x, t: np.any(np.abs(x / t - 1.0) < MARGIN)  # noqa: E731
+        if not (close(glob, e) or close(w, e) or close(glob, TAU) or close(w, TAU)):
+            return float(e)
+    pytest.fail("no threshold with a clean margin")
+
+
+@pytest.mark.parametrize("seed,frac", [(1, 0.3), (2, 0.7)])
+def test_screened_build_matches_oracle_on_the_kept_quartets(g, seed, frac):
+    mol = _mol(seed)
+    D = molgen.density(mol, 700 + seed) * 1e-2
+    q, glob, w = _bounds(mol, D)
+    eps = _pick_eps(glob, w, frac)
+    keep = _kept(glob, w, eps)
+    assert 0 < keep.sum() < len(q)
+    pairs = g.ShellPairs(mol)
+    assert pairs.nquartets == len(q)
+    Dt = torch.from_numpy(D).cuda()
+    g.set_option("density_screen", eps)
+    try:
+        J, K = g.jk_build(pairs, Dt, "mixed")
+        n32, n64 = g.last_split(pairs)
+    finally:
+        g.set_option("density_screen", 0.0)
+    assert n32 + n64 == int(keep.sum())
+    Jo, Ko = oracle.jk_quartets(mol, D, q[keep].astype(np.int32))
+    assert float(np.abs(J.cpu().numpy() - Jo).max()) <= 1e-6
+    assert float(np.abs(K.cpu().numpy() - Ko).max()) <= 1e-6
+
+
+def test_incremental_build(g):
+    """J(D1) = J(D0) + J(D1 - D0): the difference density is small, so most of
+    its quartets are screened out; the skipped quartets' exact contribution
+    (oracle) bounds the error beside the mixed-precision target."""
+    mol = _mol(3)
+    D0 = molgen.density(mol, 703)
+    rng = np.random.default_rng(704)
+    X = rng.normal(0, 1e-5, D0.shape)
+    dD = X + X.T
+    D1 = D0 + dD
+    q, glob, w = _bounds(mol, dD)
+    eps = _pick_eps(glob, w, 0.5)
+    keep = _kept(glob, w, eps)
+    Js, Ks = oracle.jk_quartets(mol, dD, q[~keep].astype(np.int32))
+    skipped = max(np.abs(Js).max(), np.abs(Ks).max())
+    pairs = g.ShellPairs(mol)
+    J0, K0 = g.jk_build(pairs, torch.from_numpy(D0).cuda(), "mixed")
+    g.set_option("density_screen", eps)
+    try:
+        Jd, Kd = g.jk_build(pairs, torch.from_numpy(dD).cuda(), "mixed")
+        n32, n64 = g.last_split(pairs)
+    finally:
+        g.set_option("density_screen", 0.0)
+    assert n32 + n64 == int(keep.sum()) <= 0.6 * len(q)
+    Jo, Ko, _ = oracle.jk(mol, D1, mode="unique")
+    assert float(np.abs((J0 + Jd).cpu().numpy() - Jo).max()) <= 1e-6 + skipped
+    assert float(np.abs((K0 + Kd).cpu().numpy() - Ko).max()) <= 1e-6 + skipped
+
+
+def test_batched_screens_like_single(g):
+    mols = [_mol(4), _mol(5)]
+    Ds = [molgen.density(m, 800 + k) * 1e-2 for k, m in enumerate(mols)]
+    q, glob, w = _bounds(mols[0], Ds[0])
+    eps = _pick_eps(glob, w, 0.5)
+    plist = [g.ShellPairs(m) for m in mols]
+    Dts = [torch.from_numpy(D).cuda() for D in Ds]
+    g.set_option("density_screen", eps)
+    try:
+        Js, Ks = g.jk_build_batched(plist, Dts, precision="mixed")
+        single = [g.jk_build(p, D, "mixed") for p, D in zip(plist, Dts)]
+    finally:
+        g.set_option("density_screen", 0.0)
+    for (J, K), Jb, Kb in zip(single, Js, Ks):
+        scale = max(1.0, float(J.abs().max()))
+        assert float((Jb - J).abs().max()) <= 1e-10 * scale
+        assert float((Kb - K).abs().max()) <= 1e-10 * scale
