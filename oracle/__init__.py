@@ -3,7 +3,8 @@
 Only the tests, the package smoke check and the benchmark's CPU-baseline leg
 import this package; the GPU library never does.  It wraps the plain FP64
 Obara-Saika/HRR C++ code in ``eri_oracle.cpp`` (built with g++ and OpenMP)
-through ctypes, a small numpy RHF for H2 in ``scf.py`` and the pure
+through ctypes, the one-electron integrals (Obara-Saika, any l) in
+``one_electron.py``, a small numpy RHF in ``scf.py`` and the pure
 (solid-harmonic) d/f transform in ``spherical.py``.
 
 Parity status per function (what pins each one, see the ``-m "not gpu"``
@@ -12,7 +13,9 @@ recursion), quartets (closed-form (ss|ss), Gauss-Legendre quadrature of the
 1/r12 integral for s/p/d classes, 8-fold symmetry, Schwarz), J/K (all-quartet
 vs unique-quartet bookkeeping, symmetry, positivity, translation), energy
 (H2 STO-3G textbook value), gradient (central finite differences and
-translational invariance), pure shells (harmonicity, definite |m| and
+translational invariance), one-electron S, T, V (Gauss-Hermite quadrature,
+the first-derivative kinetic form, the Gaussian transform of 1/r, closed s
+forms, definiteness), pure shells (harmonicity, definite |m| and
 reflection parity, orthonormality, one-centre rotational invariance).  No
 function is left unpinned.
 """

@@ -1,52 +1,18 @@
-"""Closed-shell Hartree-Fock for small s-only molecules (test infrastructure).
+"""Closed-shell Hartree-Fock (test infrastructure).
 
-Used only to pin the oracle's two-electron integrals and J/K to the textbook
-H2 / STO-3G worked example (R = 1.4 bohr), the SCF structure the paper
-describes in Sec. 2.1: build the Fock matrix from the current orbitals, form
-the density, evaluate the energy, repeat until the density is stable.
-
-One-electron integrals use the closed forms for s Gaussians:
-  S = (pi/p)^(3/2) exp(-mu R_AB^2)
-  T = mu (3 - 2 mu R_AB^2) (pi/p)^(3/2) exp(-mu R_AB^2)
-  V = -Z_C 2 pi / p exp(-mu R_AB^2) F_0(p |P - C|^2)
-with p = a + b, mu = a b / p, P = (a A + b B) / p.
+Pins the oracle's integrals and J/K to the textbook H2 / STO-3G worked
+example (R = 1.4 bohr), and is the reference SCF for the GPU driver: the SCF
+structure the paper describes in Sec. 2.1 -- build the Fock matrix from the
+current orbitals, form the density, evaluate the energy, repeat until the
+density is stable.  Plain Roothaan iterations with symmetric orthogonalisation
+X = S^(-1/2); the one-electron integrals come from one_electron.py.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import boys, jk, normalize
-
-
-def one_electron(mol):
-    if np.any(mol.shell_l != 0):
-        raise ValueError("s shells only")
-    c = normalize(mol)
-    S = np.zeros((mol.nshell, mol.nshell))
-    T = np.zeros_like(S)
-    V = np.zeros_like(S)
-    for i in range(mol.nshell):
-        A = mol.xyz[mol.shell_atom[i]]
-        for j in range(mol.nshell):
-            B = mol.xyz[mol.shell_atom[j]]
-            for u in range(mol.shell_nprim[i]):
-                a = mol.exps[mol.shell_prim_offset[i] + u]
-                ca = c[mol.shell_prim_offset[i] + u]
-                for v in range(mol.shell_nprim[j]):
-                    b = mol.exps[mol.shell_prim_offset[j] + v]
-                    cb = c[mol.shell_prim_offset[j] + v]
-                    p = a + b
-                    mu = a * b / p
-                    R2 = float(np.dot(A - B, A - B))
-                    Kab = np.exp(-mu * R2)
-                    P = (a * A + b * B) / p
-                    s = (np.pi / p) ** 1.5 * Kab
-                    S[i, j] += ca * cb * s
-                    T[i, j] += ca * cb * mu * (3.0 - 2.0 * mu * R2) * s
-                    for Cn, Z in zip(mol.xyz, mol.charges):
-                        PC2 = float(np.dot(P - Cn, P - Cn))
-                        V[i, j] += -Z * ca * cb * 2.0 * np.pi / p * Kab * boys(0, p * PC2)[0]
-    return S, T, V
+from . import jk
+from .one_electron import one_electron  # noqa: F401  (re-exported)
 
 
 def nuclear_repulsion(mol) -> float:
