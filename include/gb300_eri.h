@@ -237,6 +237,16 @@ int jk_profile(jk_pairs pairs, int max_rows, double* rows, int* nrows);
  * with CUDA events over `iters` dependent-chain iterations per thread. */
 int jk_fma_peak(jk_precision prec, int iters, double* flops_per_s, void* cuda_stream);
 
+/* One-electron integrals for the SCF around the J/K build (Sec. 2.1: the Fock
+ * matrix is the one-electron part plus J - K/2): overlap S, kinetic energy T
+ * and nuclear attraction V = -sum_C Z_C <a| 1/|r - R_C| |b>, with the nuclei
+ * at the atoms given to shellpairs_build and charges[natom] (HOST, read during
+ * the call).  S, T, V: DEVICE nbf x nbf row-major float64, caller-owned,
+ * overwritten; the elements of shell pairs dropped by the Schwarz threshold
+ * are 0 (build the handle with thresh 0 for the complete matrices).
+ * Asynchronous on cuda_stream. */
+int jk_one_electron(jk_pairs pairs, const double* charges, double* S, double* T, double* V, void* cuda_stream);
+
 /* Pure (real solid-harmonic) d and f shells.  The integrals of Sec. 2.2
  * (Eq. 1) are over Cartesian components; a basis with pure d/f shells is
  * served by transforming matrices between the two bases:

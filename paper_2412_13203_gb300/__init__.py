@@ -43,7 +43,8 @@ EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_bui
            "jk_energy_noalloc",
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
-           "jk_set_tuning", "jk_split_stats", "jk_sph_nbf", "jk_sph_transform"]
+           "jk_set_tuning", "jk_split_stats", "jk_sph_nbf", "jk_sph_transform",
+           "jk_one_electron"]
 
 
 def load():
@@ -75,6 +76,7 @@ def load():
         lib.jk_split_stats.argtypes = [vp, C.c_int, i64p, C.POINTER(C.c_int)]
         lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
+        lib.jk_one_electron.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.jk_sph_nbf.argtypes = [vp, C.POINTER(C.c_int)]
         lib.jk_sph_transform.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.shellpairs_free.argtypes = [vp]
@@ -185,6 +187,21 @@ def jk_grad(pairs: ShellPairs, D, precision: str = "fp64", out=None, stream=None
         out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
     _check(load().jk_grad(pairs.handle, _dev_ptr(D), _dev_ptr(out), _PREC[precision], _stream_ptr(stream)))
     return out
+
+
+def one_electron(pairs: ShellPairs, charges, stream=None, device=None):
+    """Overlap S, kinetic T and nuclear attraction V (float64 CUDA tensors,
+    nbf x nbf) with nuclear charges[natom] at the handle's atoms."""
+    import torch
+    z = np.ascontiguousarray(charges, dtype=np.float64)
+    if z.shape != (pairs.natom,):
+        raise ValueError(f"expected {pairs.natom} charges")
+    n = pairs.nbf
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    S, T, V = (torch.empty((n, n), dtype=torch.float64, device=dev) for _ in range(3))
+    _check(load().jk_one_electron(pairs.handle, C.c_void_p(z.ctypes.data), _dev_ptr(S), _dev_ptr(T), _dev_ptr(V),
+                                  _stream_ptr(stream)))
+    return S, T, V
 
 
 _SPH_DIR = {"to_cartesian": 0, "to_pure": 1}

@@ -48,7 +48,7 @@ def build(force: bool = False, lmax: int = 3, jobs: int | None = None, verbose: 
     gen_files.append(sph_codegen.emit(GEN))
     hand = [os.path.join(CSRC, "runtime.cu")]
     headers = [os.path.join(CSRC, "eri_device.cuh"), os.path.join(CSRC, "sph_transform.cuh"),
-               os.path.join(CSRC, "split_kernels.cuh"),
+               os.path.join(CSRC, "split_kernels.cuh"), os.path.join(CSRC, "one_electron.cuh"),
                os.path.join(ROOT, "include", "gb300_eri.h")]
     srcs = hand + gen_files
     objs = []

@@ -30,6 +30,7 @@
 #include "eri_device.cuh"
 #include "gb300_eri.h"
 #include "sph_transform.cuh"
+#include "one_electron.cuh"
 
 int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s);
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
@@ -176,6 +177,7 @@ struct jk_pairs_s {
     DevBuf split_tot;                               // per class: FP32, FP64 quartets, FP32, FP64 items (last mixed build)
     DevBuf npre;                                    // exclusive prefix of primitive pairs over the kept pairs
     DevBuf scratch;                                 // small reductions
+    DevBuf charges;                                 // nuclear charges of the last jk_one_electron
     std::vector<int> shell_l;                       // host copy of every shell's l (caller's order)
     int nsph = 0;                                   // basis size with pure d and f shells
     DevBuf sph_shell;                               // int4 per shell: l, first Cartesian, first pure index, table offset
@@ -2177,6 +2179,41 @@ int jk_fma_peak(jk_precision prec, int iters, double* flops, void* cuda_stream) 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *flops = 2.0 * 8 * 16 * (double)iters * blocks * threads / (ms * 1e-3);
+    return JK_OK;
+}
+
+int jk_one_electron(jk_pairs h, const double* charges, double* S, double* T, double* V, void* cuda_stream) {
+    g_err.clear();
+    if (!h || !charges || !S || !T || !V) return fail(JK_ERR_INVALID, "null argument");
+    for (int i = 0; i < h->natom; ++i)
+        if (!std::isfinite(charges[i])) return fail(JK_ERR_INVALID, "non-finite nuclear charge");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int rc;
+    if ((rc = upload(h->charges, charges, (size_t)h->natom, st))) return rc;
+    const size_t n2 = (size_t)h->nbf * h->nbf;
+    CK(cudaMemsetAsync(S, 0, sizeof(double) * n2, st));
+    CK(cudaMemsetAsync(T, 0, sizeof(double) * n2, st));
+    CK(cudaMemsetAsync(V, 0, sizeof(double) * n2, st));
+    if (h->npair > 0) {
+        gb::OneElArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.pairs = view_of(h);
+        a.lab = h->pair_lab.as<int2>();
+        a.boys = g_boys[h->device].tab.as<double>();
+        a.xyz = h->xyz.as<double>();
+        a.Z = h->charges.as<double>();
+        a.natom = h->natom;
+        a.nbf = h->nbf;
+        a.S = S;
+        a.T = T;
+        a.V = V;
+        const unsigned grid = (unsigned)std::min<long long>(nblk(h->npair, 128), (long long)h->nsm * 16);
+        gb::k_one_electron<<<grid, 128, 0, st>>>(a);
+        CKL();
+    }
     return JK_OK;
 }
 

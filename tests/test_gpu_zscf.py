@@ -1,0 +1,100 @@
+"""GPU parity of the one-electron kernel (jk_one_electron) against the
+oracle's Obara-Saika S, T, V, and of the SCF driver around jk_build against
+the oracle's RHF and the H2 / STO-3G textbook example."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import molgen
+import oracle
+from oracle import one_electron as oe
+from oracle import scf as oscf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "h2_sto3g.json")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_13203_gb300 as g
+    g.load()
+    return g
+
+
+def _h2_polarised(R=1.4):
+    """H2 / STO-3G plus one p (exponent 1.1) and one d (0.8) shell per atom."""
+    m = molgen.h2_sto3g(R)
+    ls, atom, npr, off = list(m.shell_l), list(m.shell_atom), list(m.shell_nprim), list(m.shell_prim_offset)
+    exps, coefs = list(m.exps), list(m.coefs)
+    for a in range(2):
+        for l, e in ((1, 1.1), (2, 0.8)):
+            ls.append(l); atom.append(a); npr.append(1); off.append(len(exps)); exps.append(e); coefs.append(1.0)
+    o = np.argsort(atom, kind="stable")
+    ls, atom, npr, off = (np.array(x, np.int32)[o] for x in (ls, atom, npr, off))
+    return molgen.Molecule(m.xyz.copy(), atom, ls, npr, off, np.array(exps), np.array(coefs), np.array([1.0, 1.0]))
+
+
+@pytest.mark.parametrize("seed,shells,natom", [(1, [0, 1], 3), (3, [3, 1], 2), (5, [0, 1, 2, 3], 2)])
+def test_one_electron_matches_oracle(g, seed, shells, natom):
+    mol = molgen.random_molecule(950 + seed, natom, shells, 1, 3, 0.1, 20.0, layout="lattice", spacing=1.7)
+    z = np.arange(1, natom + 1, dtype=np.float64) * 1.5
+    mol.charges = z
+    pairs = g.ShellPairs(mol)
+    S, T, V = (M.cpu().numpy() for M in g.one_electron(pairs, z))
+    So, To, Vo = oe.one_electron(mol)
+    for M, Mo in ((S, So), (T, To), (V, Vo)):
+        np.testing.assert_allclose(M, Mo, rtol=0, atol=1e-12 * np.abs(Mo).max())
+
+
+def test_one_electron_of_a_screened_handle(g):
+    """Elements of pairs the Schwarz threshold drops are 0; the rest match."""
+    mol = molgen.random_molecule(960, 4, [0, 1], 1, 2, 0.5, 20.0, layout="lattice", spacing=4.0)
+    z = np.full(4, 2.0)
+    mol.charges = z
+    pairs = g.ShellPairs(mol, 1e-6)
+    npair_all = mol.nshell * (mol.nshell + 1) // 2
+    assert 0 < pairs.npairs < npair_all
+    S, _, V = (M.cpu().numpy() for M in g.one_electron(pairs, z))
+    So, _, Vo = oe.one_electron(mol)
+    kept = S != 0.0
+    assert (~kept).any()
+    np.testing.assert_allclose(S[kept], So[kept], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(V[kept], Vo[kept], rtol=0, atol=1e-12 * np.abs(Vo).max())
+    np.testing.assert_array_equal(V[~kept], 0.0)
+
+
+def test_scf_h2_sto3g_textbook(g):
+    from paper_2412_13203_gb300 import scf
+    gold = json.load(open(GOLDEN))
+    mol = molgen.h2_sto3g(gold["R_bohr"])
+    r = scf.rhf(mol, mol.charges, nocc=1)
+    assert r.converged
+    assert round(r.energy, 4) == gold["E_total"]
+    assert round(r.electronic, 4) == gold["E_electronic"]
+    Eo, _, _ = oscf.rhf(mol, 1)
+    assert abs(r.energy - Eo) <= 1e-10
+
+
+@pytest.mark.parametrize("diis", [0, 6])
+def test_scf_polarised_h2_matches_oracle(g, diis):
+    from paper_2412_13203_gb300 import scf
+    mol = _h2_polarised()
+    r = scf.rhf(mol, mol.charges, nocc=1, diis=diis)
+    assert r.converged
+    Eo, _, Po = oscf.rhf(mol, 1)
+    assert abs(r.energy - Eo) <= 1e-9
+    assert float(np.abs(r.D.cpu().numpy() - Po).max()) <= 1e-6
+
+
+def test_scf_mixed_precision(g):
+    from paper_2412_13203_gb300 import scf
+    mol = _h2_polarised(1.5)
+    e64 = scf.rhf(mol, mol.charges, nocc=1).energy
+    emx = scf.rhf(mol, mol.charges, nocc=1, precision="mixed").energy
+    assert abs(emx - e64) <= 1e-6
