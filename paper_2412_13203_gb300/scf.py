@@ -12,14 +12,23 @@ on the same device, and the nuclear repulsion is summed on the host.
 Roothaan iterations from the core guess (D = 0) with DIIS extrapolation
 (Pulay's commutator error FDS - SDF on the last `diis` Fock matrices, from
 the second iteration on); `diis=0` gives plain Roothaan iterations.
+
+Incremental Fock builds (`incremental_eps`): J and K are linear in D, so
+J(D_n) = J(D_m) + J(D_n - D_m); the difference density shrinks as the SCF
+converges, and with density screening (JK_OPT_DENSITY_SCREEN = eps) the build
+of J(D_n - D_m) runs only the quartets whose density-weighted bound reaches
+eps.  Every `rebuild` iterations, and for the final energy, J and K are built
+from the full density again.  Density screening acts in the mixed build;
+an FP64 incremental build uses it with tau = 0 (every kept quartet in FP64).
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from contextlib import contextmanager
+from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import ShellPairs, jk_build, one_electron
+from . import ShellPairs, get_option, jk_build, last_split, one_electron, set_option
 
 
 @dataclass
@@ -32,6 +41,21 @@ class SCFResult:
     D: object                 # total density (CUDA tensor, nbf x nbf)
     orbital_energies: object  # CUDA tensor
     C: object                 # orbital coefficients (CUDA tensor, nbf x nbf)
+    quartets: list = field(default_factory=list)  # shell quartets evaluated per iteration
+
+
+@contextmanager
+def _screened(eps, precision):
+    """Density screening at eps for the builds inside (restores the options)."""
+    old_eps, old_tau = get_option("density_screen"), get_option("mixed_tau")
+    set_option("density_screen", eps)
+    if precision == "fp64":
+        set_option("mixed_tau", 0.0)
+    try:
+        yield
+    finally:
+        set_option("density_screen", old_eps)
+        set_option("mixed_tau", old_tau)
 
 
 def nuclear_repulsion(xyz, charges) -> float:
@@ -45,11 +69,13 @@ def nuclear_repulsion(xyz, charges) -> float:
 
 
 def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "fp64", maxiter: int = 100,
-        e_tol: float = 1e-10, d_tol: float = 1e-8, diis: int = 6, pairs: ShellPairs | None = None) -> SCFResult:
+        e_tol: float = 1e-10, d_tol: float = 1e-8, diis: int = 6, pairs: ShellPairs | None = None,
+        incremental_eps: float | None = None, rebuild: int = 8) -> SCFResult:
     """Restricted Hartree-Fock for `nocc` doubly occupied orbitals.  `mol`
     carries the geometry and shells as for ShellPairs; `charges[natom]` are
     the nuclear charges; `thresh` the Schwarz threshold of the pair build
-    (None: no screening, so that S, T and V are complete)."""
+    (None: no screening, so that S, T and V are complete); `incremental_eps`
+    switches on incremental, density-screened Fock builds."""
     import torch
     if pairs is None:
         pairs = ShellPairs(mol, thresh)
@@ -61,13 +87,27 @@ def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "
     D = torch.zeros((n, n), dtype=torch.float64, device=S.device)
     J = torch.empty_like(D)
     K = torch.empty_like(D)
+    Jd = torch.empty_like(D)
+    Kd = torch.empty_like(D)
+    D_built = None  # density J and K currently belong to
+    quartets = []
     e_old = None
     focks, errs = [], []
     converged = False
     eps = Cmo = None
     it = 0
     for it in range(1, maxiter + 1):
-        jk_build(pairs, D, precision, J, K)
+        if incremental_eps and D_built is not None and (it - 1) % rebuild != 0:
+            with _screened(incremental_eps, precision):
+                jk_build(pairs, D - D_built, "mixed", Jd, Kd)
+                n32, n64 = last_split(pairs)
+            J += Jd
+            K += Kd
+            quartets.append(n32 + n64)
+        else:
+            jk_build(pairs, D, precision, J, K)
+            quartets.append(pairs.nquartets)
+        D_built = D
         F = H + J - 0.5 * K
         e_el = 0.5 * float(torch.sum(D * (H + F)))
         if diis and it > 1:  # D = 0 of the first iteration commutes trivially: no DIIS vector
@@ -102,4 +142,4 @@ def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "
     jk_build(pairs, D, precision, J, K)
     e_el = 0.5 * float(torch.sum(D * (2.0 * H + J - 0.5 * K)))
     enuc = nuclear_repulsion(mol.xyz, charges)
-    return SCFResult(e_el + enuc, e_el, enuc, it, converged, D, eps, Cmo)
+    return SCFResult(e_el + enuc, e_el, enuc, it, converged, D, eps, Cmo, quartets)

@@ -98,3 +98,35 @@ def test_scf_mixed_precision(g):
     e64 = scf.rhf(mol, mol.charges, nocc=1).energy
     emx = scf.rhf(mol, mol.charges, nocc=1, precision="mixed").energy
     assert abs(emx - e64) <= 1e-6
+
+
+def _hchain(n, d):
+    """n hydrogens on a line, spacing d bohr: STO-3G s plus one p (exponent 1.0) per atom."""
+    b = molgen.h2_sto3g(1.4)
+    e, c = b.exps[:3], b.coefs[:3]
+    ls, atom, npr, off, exps, coefs = [], [], [], [], [], []
+    for a in range(n):
+        for l, ee, cc in ((0, e, c), (1, np.array([1.0]), np.array([1.0]))):
+            ls.append(l); atom.append(a); npr.append(len(ee)); off.append(len(exps))
+            exps += list(ee); coefs += list(cc)
+    return molgen.Molecule(np.array([[0.0, 0.0, d * i] for i in range(n)]), np.array(atom, np.int32),
+                           np.array(ls, np.int32), np.array(npr, np.int32), np.array(off, np.int32),
+                           np.array(exps), np.array(coefs), np.ones(n))
+
+
+def test_scf_incremental_density_screening(g):
+    """Incremental Fock builds J(D_n) = J(D_m) + J(D_n - D_m) with density
+    screening at 1e-10 reach the full SCF's energy while the difference
+    builds skip quartets (H6 chain, where distant pairs have small bounds)."""
+    from paper_2412_13203_gb300 import scf
+    mol = _hchain(6, 2.0)
+    z = np.ones(6)
+    tau0 = g.get_option("mixed_tau")
+    full = scf.rhf(mol, z, nocc=3)
+    inc = scf.rhf(mol, z, nocc=3, incremental_eps=1e-10)
+    assert full.converged and inc.converged
+    Eo, _, _ = oscf.rhf(mol, 3)
+    assert abs(full.energy - Eo) <= 1e-9
+    assert abs(inc.energy - full.energy) <= 1e-8
+    assert min(inc.quartets) < 0.8 * full.quartets[0]
+    assert g.get_option("density_screen") == 0.0 and g.get_option("mixed_tau") == tau0
