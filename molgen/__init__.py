@@ -232,3 +232,41 @@ def h2_sto3g(R: float = 1.4) -> Molecule:
                     np.array([3, 3], np.int32), np.array([0, 3], np.int32),
                     np.concatenate([e, e]), np.concatenate([c, c]),
                     charges=np.array([1.0, 1.0]))
+
+
+def h2_polarised(R: float = 1.4) -> Molecule:
+    """H2 / STO-3G (h2_sto3g) plus one p shell (exponent 1.1) and one d shell
+    (exponent 0.8) per atom, shells listed atom by atom."""
+    m = h2_sto3g(R)
+    ls, atom, npr, off = list(m.shell_l), list(m.shell_atom), list(m.shell_nprim), list(m.shell_prim_offset)
+    exps, coefs = list(m.exps), list(m.coefs)
+    for a in range(2):
+        for l, e in ((1, 1.1), (2, 0.8)):
+            ls.append(l)
+            atom.append(a)
+            npr.append(1)
+            off.append(len(exps))
+            exps.append(e)
+            coefs.append(1.0)
+    o = np.argsort(atom, kind="stable")
+    ls, atom, npr, off = (np.array(x, np.int32)[o] for x in (ls, atom, npr, off))
+    return Molecule(m.xyz.copy(), atom, ls, npr, off, np.array(exps), np.array(coefs), np.array([1.0, 1.0]))
+
+
+def h_chain(n: int, spacing: float) -> Molecule:
+    """n hydrogens on the z axis, `spacing` bohr apart: STO-3G s (h2_sto3g)
+    plus one p shell (exponent 1.0) per atom."""
+    b = h2_sto3g(1.4)
+    e, c = b.exps[:3], b.coefs[:3]
+    ls, atom, npr, off, exps, coefs = [], [], [], [], [], []
+    for a in range(n):
+        for l, ee, cc in ((0, e, c), (1, np.array([1.0]), np.array([1.0]))):
+            ls.append(l)
+            atom.append(a)
+            npr.append(len(ee))
+            off.append(len(exps))
+            exps += list(ee)
+            coefs += list(cc)
+    return Molecule(np.array([[0.0, 0.0, spacing * i] for i in range(n)]), np.array(atom, np.int32),
+                    np.array(ls, np.int32), np.array(npr, np.int32), np.array(off, np.int32),
+                    np.array(exps), np.array(coefs), np.ones(n))

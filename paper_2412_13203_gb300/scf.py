@@ -20,6 +20,10 @@ of J(D_n - D_m) runs only the quartets whose density-weighted bound reaches
 eps.  Every `rebuild` iterations, and for the final energy, J and K are built
 from the full density again.  Density screening acts in the mixed build;
 an FP64 incremental build uses it with tau = 0 (every kept quartet in FP64).
+
+Pure d and f shells (`pure=True`): S and H are taken to the pure basis once
+(T^T S T, T^T H T), the SCF runs there, and every Fock build transforms the
+density to the Cartesian basis and J, K back (jk_sph_transform).
 """
 from __future__ import annotations
 
@@ -28,7 +32,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import ShellPairs, get_option, jk_build, last_split, one_electron, set_option
+from . import ShellPairs, get_option, jk_build, last_split, one_electron, set_option, sph_transform
 
 
 @dataclass
@@ -70,20 +74,34 @@ def nuclear_repulsion(xyz, charges) -> float:
 
 def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "fp64", maxiter: int = 100,
         e_tol: float = 1e-10, d_tol: float = 1e-8, diis: int = 6, pairs: ShellPairs | None = None,
-        incremental_eps: float | None = None, rebuild: int = 8) -> SCFResult:
+        incremental_eps: float | None = None, rebuild: int = 8, pure: bool = False) -> SCFResult:
     """Restricted Hartree-Fock for `nocc` doubly occupied orbitals.  `mol`
     carries the geometry and shells as for ShellPairs; `charges[natom]` are
     the nuclear charges; `thresh` the Schwarz threshold of the pair build
     (None: no screening, so that S, T and V are complete); `incremental_eps`
-    switches on incremental, density-screened Fock builds."""
+    switches on incremental, density-screened Fock builds; `pure` runs the
+    SCF over pure d and f shells (D, C and the orbital count are then those of
+    the pure basis)."""
     import torch
     if pairs is None:
         pairs = ShellPairs(mol, thresh)
     S, T, V = one_electron(pairs, charges)
     H = T + V
+    if pure:
+        S = sph_transform(pairs, S, "to_pure")
+        H = sph_transform(pairs, H, "to_pure")
+
+    def build(Dm, prec, Jo, Ko):
+        """J and K of density Dm (in the SCF's basis) into Jo, Ko."""
+        if not pure:
+            jk_build(pairs, Dm, prec, Jo, Ko)
+            return
+        Jc, Kc = jk_build(pairs, sph_transform(pairs, Dm, "to_cartesian"), prec)
+        sph_transform(pairs, Jc, "to_pure", out=Jo)
+        sph_transform(pairs, Kc, "to_pure", out=Ko)
     w, U = torch.linalg.eigh(S)
     X = (U * w.rsqrt()) @ U.T
-    n = pairs.nbf
+    n = pairs.nsph if pure else pairs.nbf
     D = torch.zeros((n, n), dtype=torch.float64, device=S.device)
     J = torch.empty_like(D)
     K = torch.empty_like(D)
@@ -99,13 +117,13 @@ def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "
     for it in range(1, maxiter + 1):
         if incremental_eps and D_built is not None and (it - 1) % rebuild != 0:
             with _screened(incremental_eps, precision):
-                jk_build(pairs, D - D_built, "mixed", Jd, Kd)
+                build(D - D_built, "mixed", Jd, Kd)
                 n32, n64 = last_split(pairs)
             J += Jd
             K += Kd
             quartets.append(n32 + n64)
         else:
-            jk_build(pairs, D, precision, J, K)
+            build(D, precision, J, K)
             quartets.append(pairs.nquartets)
         D_built = D
         F = H + J - 0.5 * K
@@ -139,7 +157,7 @@ def rhf(mol, charges, nocc: int, thresh: float | None = None, precision: str = "
             break
         e_old = e_el
     # energy of the final density
-    jk_build(pairs, D, precision, J, K)
+    build(D, precision, J, K)
     e_el = 0.5 * float(torch.sum(D * (2.0 * H + J - 0.5 * K)))
     enuc = nuclear_repulsion(mol.xyz, charges)
     return SCFResult(e_el + enuc, e_el, enuc, it, converged, D, eps, Cmo, quartets)

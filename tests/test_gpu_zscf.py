@@ -27,19 +27,6 @@ def g():
     return g
 
 
-def _h2_polarised(R=1.4):
-    """H2 / STO-3G plus one p (exponent 1.1) and one d (0.8) shell per atom."""
-    m = molgen.h2_sto3g(R)
-    ls, atom, npr, off = list(m.shell_l), list(m.shell_atom), list(m.shell_nprim), list(m.shell_prim_offset)
-    exps, coefs = list(m.exps), list(m.coefs)
-    for a in range(2):
-        for l, e in ((1, 1.1), (2, 0.8)):
-            ls.append(l); atom.append(a); npr.append(1); off.append(len(exps)); exps.append(e); coefs.append(1.0)
-    o = np.argsort(atom, kind="stable")
-    ls, atom, npr, off = (np.array(x, np.int32)[o] for x in (ls, atom, npr, off))
-    return molgen.Molecule(m.xyz.copy(), atom, ls, npr, off, np.array(exps), np.array(coefs), np.array([1.0, 1.0]))
-
-
 @pytest.mark.parametrize("seed,shells,natom", [(1, [0, 1], 3), (3, [3, 1], 2), (5, [0, 1, 2, 3], 2)])
 def test_one_electron_matches_oracle(g, seed, shells, natom):
     mol = molgen.random_molecule(950 + seed, natom, shells, 1, 3, 0.1, 20.0, layout="lattice", spacing=1.7)
@@ -84,7 +71,7 @@ def test_scf_h2_sto3g_textbook(g):
 @pytest.mark.parametrize("diis", [0, 6])
 def test_scf_polarised_h2_matches_oracle(g, diis):
     from paper_2412_13203_gb300 import scf
-    mol = _h2_polarised()
+    mol = molgen.h2_polarised()
     r = scf.rhf(mol, mol.charges, nocc=1, diis=diis)
     assert r.converged
     Eo, _, Po = oscf.rhf(mol, 1)
@@ -94,24 +81,10 @@ def test_scf_polarised_h2_matches_oracle(g, diis):
 
 def test_scf_mixed_precision(g):
     from paper_2412_13203_gb300 import scf
-    mol = _h2_polarised(1.5)
+    mol = molgen.h2_polarised(1.5)
     e64 = scf.rhf(mol, mol.charges, nocc=1).energy
     emx = scf.rhf(mol, mol.charges, nocc=1, precision="mixed").energy
     assert abs(emx - e64) <= 1e-6
-
-
-def _hchain(n, d):
-    """n hydrogens on a line, spacing d bohr: STO-3G s plus one p (exponent 1.0) per atom."""
-    b = molgen.h2_sto3g(1.4)
-    e, c = b.exps[:3], b.coefs[:3]
-    ls, atom, npr, off, exps, coefs = [], [], [], [], [], []
-    for a in range(n):
-        for l, ee, cc in ((0, e, c), (1, np.array([1.0]), np.array([1.0]))):
-            ls.append(l); atom.append(a); npr.append(len(ee)); off.append(len(exps))
-            exps += list(ee); coefs += list(cc)
-    return molgen.Molecule(np.array([[0.0, 0.0, d * i] for i in range(n)]), np.array(atom, np.int32),
-                           np.array(ls, np.int32), np.array(npr, np.int32), np.array(off, np.int32),
-                           np.array(exps), np.array(coefs), np.ones(n))
 
 
 def test_scf_incremental_density_screening(g):
@@ -119,7 +92,7 @@ def test_scf_incremental_density_screening(g):
     screening at 1e-10 reach the full SCF's energy while the difference
     builds skip quartets (H6 chain, where distant pairs have small bounds)."""
     from paper_2412_13203_gb300 import scf
-    mol = _hchain(6, 2.0)
+    mol = molgen.h_chain(6, 2.0)
     z = np.ones(6)
     tau0 = g.get_option("mixed_tau")
     full = scf.rhf(mol, z, nocc=3)
@@ -130,3 +103,15 @@ def test_scf_incremental_density_screening(g):
     assert abs(inc.energy - full.energy) <= 1e-8
     assert min(inc.quartets) < 0.8 * full.quartets[0]
     assert g.get_option("density_screen") == 0.0 and g.get_option("mixed_tau") == tau0
+
+
+def test_scf_pure_shells(g):
+    """SCF over pure d shells against the oracle's pure-basis RHF (integrals
+    with every index transformed)."""
+    from paper_2412_13203_gb300 import scf
+    mol = molgen.h2_polarised()
+    r = scf.rhf(mol, mol.charges, nocc=1, pure=True)
+    assert r.converged and r.D.shape == (18, 18)
+    Ep, _, Pp = oscf.rhf(mol, 1, pure=True)
+    assert abs(r.energy - Ep) <= 1e-9
+    assert float(np.abs(r.D.cpu().numpy() - Pp).max()) <= 1e-6

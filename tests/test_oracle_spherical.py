@@ -179,3 +179,17 @@ def test_legendre_recursion():
             rhs[p] = rhs.get(p, 0) - n * c
         assert lhs == {p: c for p, c in rhs.items() if c != 0}
     assert sp.legendre(0) == {0: Fraction(1)}
+
+
+def test_pure_scf_is_variational():
+    """The pure functions span a subspace of the Cartesian ones (each d or f
+    shell loses its r^2 s or r^2 p combination), so the pure-basis RHF energy
+    lies above the Cartesian one; for s and p shells the two are identical."""
+    from oracle import scf
+    mol = molgen.h2_polarised()
+    e_cart, _, _ = scf.rhf(mol, 1)
+    e_pure, _, P = scf.rhf(mol, 1, pure=True)
+    assert e_cart < e_pure < e_cart + 1e-2
+    assert P.shape == (18, 18)
+    h2 = molgen.h2_sto3g(1.4)
+    assert scf.rhf(h2, 1, pure=True)[0] == pytest.approx(scf.rhf(h2, 1)[0], abs=1e-13)
