@@ -220,3 +220,14 @@ def test_density_screen_option(lib):
         assert lib.jk_get_option(OPT_SCREEN, C.byref(v)) == JK_OK and v.value == 1e-9
     finally:
         assert lib.jk_set_option(OPT_SCREEN, 0.0) == JK_OK
+
+
+def test_new_entry_points_reject_null_arguments(lib):
+    buf = (C.c_double * 4)()
+    p = C.cast(buf, C.c_void_p)
+    n = C.c_int(-7)
+    assert lib.jk_sph_nbf(None, C.byref(n)) == JK_ERR_INVALID and n.value == -7
+    assert lib.jk_sph_transform(None, 0, p, p, None) == JK_ERR_INVALID
+    assert "null" in err(lib)
+    assert lib.jk_one_electron(None, p, p, p, p, None) == JK_ERR_INVALID
+    assert "null" in err(lib)
