@@ -1,7 +1,12 @@
 """Command-line driver: one seeded workload, J/K (or gradient) builds on the
 GPU, timings printed.  Used for profiling captures.
 
-    python -m paper_2412_13203_gb300.run_jk --config 1 --prec fp64 [--natom 8] [--repeat 2] [--grad]
+    python -m paper_2412_13203_gb300.run_jk --config 1 --prec fp64 [--natom 8] [--repeat 2]
+        [--grad | --pure | --one-electron] [--screen EPS]
+
+--pure builds J/K of the workload with its d shells pure (the density taken
+to the pure basis first); --one-electron times jk_one_electron (unit
+nuclear charges); --screen sets density screening for mixed builds.
 """
 from __future__ import annotations
 
@@ -22,7 +27,11 @@ def main(argv=None):
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--grad", action="store_true")
+    ap.add_argument("--pure", action="store_true")
+    ap.add_argument("--one-electron", action="store_true")
+    ap.add_argument("--screen", type=float, default=0.0)
     a = ap.parse_args(argv)
+    import numpy as np
     import torch
     import molgen
     import paper_2412_13203_gb300 as g
@@ -34,10 +43,21 @@ def main(argv=None):
     print(f"pairs {time.perf_counter() - t:.3f}s nbf {pairs.nbf} npairs {pairs.npairs} quartets {pairs.nquartets} "
           f"primitive quartets {pairs.nprimquartets}", flush=True)
     Dt = torch.from_numpy(D).cuda()
+    g.set_option("density_screen", a.screen)
+    if a.pure:
+        Dt = g.sph_transform(pairs, Dt, "to_pure")
     for r in range(a.repeat):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        if a.grad:
+        if a.one_electron:
+            S, T, V = g.one_electron(pairs, np.ones(pairs.natom))
+            torch.cuda.synchronize()
+            print(f"one-electron {r} {time.perf_counter() - t:.4f}s tr S {float(S.trace()):.6f}", flush=True)
+        elif a.pure:
+            J, K = g.jk_build_pure(pairs, Dt, a.prec)
+            torch.cuda.synchronize()
+            print(f"jk pure {a.prec} {r} {time.perf_counter() - t:.4f}s E {g.jk_energy(Dt, J, K)!r}", flush=True)
+        elif a.grad:
             gr = g.jk_grad(pairs, Dt, a.prec)
             torch.cuda.synchronize()
             print(f"grad {r} {time.perf_counter() - t:.4f}s |g|max {float(gr.abs().max()):.6e}", flush=True)
