@@ -124,8 +124,9 @@ int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision
  * dEdR[natom*3] (float64, device) is overwritten.  Derivative integrals by the
  * shift rule d phi_a/dA_i = 2 alpha phi_{a+1_i} - a_i phi_{a-1_i} on centres
  * A, B and C; the D centre by translational invariance.  Both precisions run
- * the FP64 derivative kernels, which are compiled for shells up to d: a handle
- * with f shells returns JK_ERR_UNSUPPORTED. */
+ * the FP64 derivative kernels, compiled for every class up to (ff|ff); a
+ * library built for a lower angular momentum returns JK_ERR_UNSUPPORTED for
+ * classes above it. */
 int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, void* cuda_stream);
 
 /* Many independent molecules in one launch sequence (one persistent launch per

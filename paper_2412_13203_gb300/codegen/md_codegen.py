@@ -928,6 +928,20 @@ def _store_axis_array(E, em, name, li, lj, E_axis):
                 E(f"{name}[{(i * (lj + 1) + j) * T + t}] = {em.val(sv)};")
 
 
+def use_grad_chunk(bra, ket):
+    """Derivative kernels of classes with an f shell: one thread per (work
+    item, Cartesian component c of the ket's first shell), as the J/K chunked
+    form, so that the per-thread arrays hold NAB x ND (not NAB x NC x ND)
+    values and the R cube is filled by the rolled recursion.  In one piece
+    the (ff|ff) derivative kernel needs a 410 KB stack frame per thread."""
+    return max(bra + ket) >= 3
+
+
+def grad_threads(bra, ket):
+    """Threads per work item of a derivative kernel."""
+    return ncart(ket[0]) if use_grad_chunk(bra, ket) else 1
+
+
 def gen_grad_kernel(bra, ket):
     """FP64 nuclear-gradient kernel of one class.
 
@@ -955,9 +969,17 @@ def gen_grad_kernel(bra, ket):
     name = class_name(bra, ket)
     TB = la + lb + 3      # t range of the bra arrays (i <= la+1, j <= lb+1)
     TK = lc + ld + 2      # t range of the ket arrays (i <= lc+1, j <= ld)
+    chunk = use_grad_chunk(bra, ket)
+    NCDx = nd if chunk else NCD  # ket component pairs per thread
     E(f"__global__ void __launch_bounds__(128) eri_grad_{name}_f64(const gb::GradArgs args) {{")
-    E("const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
-    E("if (tid >= args.total) return;")
+    if chunk:
+        E("const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
+        E(f"if (gtid >= args.total * {nc}) return;")
+        E(f"const long long tid = gtid / {nc};")
+        E(f"const int cthr = (int)(gtid - tid * {nc});")
+    else:
+        E("const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
+        E("if (tid >= args.total) return;")
     # work items as in the J/K kernels: a quartet split into min(P, K_ab) items
     # over its bra primitive pairs, heaviest rows (largest ket primitive count,
     # at the end of the range) first so that the launch tail is light
@@ -981,17 +1003,20 @@ def gen_grad_kernel(bra, ket):
     E("if (ib.x == ib.y) s *= 0.5;")
     E("if (ik.x == ik.y) s *= 0.5;")
     E("if (bra == ket) s *= 0.5;")
-    E(f"double G[{NAB * NCD}];")
+    E(f"double G[{NAB * NCDx}];")
     E(f"for (int ab = 0; ab < {NAB}; ++ab) {{")
     E(f"  const int a = ib.x + ab / {nb}, b = ib.y + ab % {nb};")
-    E(f"  for (int cd = 0; cd < {NCD}; ++cd) {{")
-    E(f"    const int c = ik.x + cd / {nd}, d = ik.y + cd % {nd};")
-    E("    G[ab * %d + cd] = s * (4.0 * Dm[(size_t)a * n + b] * Dm[(size_t)c * n + d] - Dm[(size_t)a * n + c] * Dm[(size_t)b * n + d] - Dm[(size_t)a * n + d] * Dm[(size_t)b * n + c]);" % NCD)
+    E(f"  for (int cd = 0; cd < {NCDx}; ++cd) {{")
+    if chunk:
+        E("    const int c = ik.x + cthr, d = ik.y + cd;")
+    else:
+        E(f"    const int c = ik.x + cd / {nd}, d = ik.y + cd % {nd};")
+    E("    G[ab * %d + cd] = s * (4.0 * Dm[(size_t)a * n + b] * Dm[(size_t)c * n + d] - Dm[(size_t)a * n + c] * Dm[(size_t)b * n + d] - Dm[(size_t)a * n + d] * Dm[(size_t)b * n + c]);" % NCDx)
     E("  }")
     E("}")
     E("double gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gC[3] = {0, 0, 0};")
-    E(f"double X[{H1 * NCD}];")
-    E(f"double XC[{3 * H0 * NCD}];")
+    E(f"double X[{H1 * NCDx}];")
+    E(f"double XC[{3 * H0 * NCDx}];")
     E(f"double Rc[{S * S * S}];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
     E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
@@ -1002,8 +1027,8 @@ def gen_grad_kernel(bra, ket):
     for ax in "xyz":
         Eb = gen_E_axis(em, f"gb{ax}", la + 1, lb + 1, Sym(name=f"PA{ax}"), Sym(name=f"PB{ax}"), inv2p)
         _store_axis_array(E, em, f"eb{ax}", la + 1, lb + 1, Eb)
-    E(f"for (int i = 0; i < {H1 * NCD}; ++i) X[i] = 0.0;")
-    E(f"for (int i = 0; i < {3 * H0 * NCD}; ++i) XC[i] = 0.0;")
+    E(f"for (int i = 0; i < {H1 * NCDx}; ++i) X[i] = 0.0;")
+    E(f"for (int i = 0; i < {3 * H0 * NCDx}; ++i) XC[i] = 0.0;")
     E("for (int jq = 0; jq < ik.z; ++jq) {")
     E("const double4 qa = pairs.pp[ik.w + jq]; const double2 qb = pairs.pp2[ik.w + jq];")
     E("const double q = qa.w, kq = qb.x, inv2q = qb.y, gam2 = 2.0 * pairs.alpha[ik.w + jq];")
@@ -1021,16 +1046,22 @@ def gen_grad_kernel(bra, ket):
     E("const double m2r = -2 * rho;")
     E(f"double F[{L1 + 1}];")
     E(f"gb::boys_f64<{L1}>(T, F, boys);")
-    R = gen_R(em, L1, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
-    for (t, u, v), sv in R.items():
-        E(f"Rc[{(t * S + u) * S + v}] = {em.val(sv)};")
-    E(f"for (int cd = 0; cd < {NCD}; ++cd) {{")
-    E(f"  const int c = cd / {nd}, d = cd % {nd};")
+    if chunk:
+        gen_R_rolled(em, L1, False)
+    else:
+        R = gen_R(em, L1, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
+        for (t, u, v), sv in R.items():
+            E(f"Rc[{(t * S + u) * S + v}] = {em.val(sv)};")
+    E(f"for (int cd = 0; cd < {NCDx}; ++cd) {{")
+    if chunk:
+        E("  const int c = cthr, d = cd;")
+    else:
+        E(f"  const int c = cd / {nd}, d = cd % {nd};")
     E(f"  const int cx = c_comp_{lc}[3 * c], cy = c_comp_{lc}[3 * c + 1], cz = c_comp_{lc}[3 * c + 2];")
     E(f"  const int dx = c_comp_{ld}[3 * d], dy = c_comp_{ld}[3 * d + 1], dz = c_comp_{ld}[3 * d + 2];")
     # X over H1
     for k in range(H1):
-        E(f"  double xh{k} = X[{k * NCD} + cd];")
+        E(f"  double xh{k} = X[{k * NCDx} + cd];")
     E("  for (int tau = 0; tau <= cx + dx; ++tau) {")
     E(f"    const double ex = ekx[(cx * {ld + 1} + dx) * {TK} + tau];")
     E("    for (int nu = 0; nu <= cy + dy; ++nu) {")
@@ -1042,13 +1073,13 @@ def gen_grad_kernel(bra, ket):
         E(f"        xh{k} = fma(e, Rb[{(t * S + u) * S + v}], xh{k});")
     E("  }}}")
     for k in range(H1):
-        E(f"  X[{k * NCD} + cd] = xh{k};")
+        E(f"  X[{k * NCDx} + cd] = xh{k};")
     # XC for the three directions
     for di, ax in enumerate("xyz"):
         cc = {"x": ("cx", "dx"), "y": ("cy", "dy"), "z": ("cz", "dz")}
         E("  {")
         for k in range(H0):
-            E(f"  double xc{k} = XC[{(di * H0 + k) * NCD} + cd];")
+            E(f"  double xc{k} = XC[{(di * H0 + k) * NCDx} + cd];")
         rng = {a: (f"{cc[a][0]} + {cc[a][1]}" + (" + 1" if a == ax else "")) for a in "xyz"}
         idx = {"x": "tau", "y": "nu", "z": "phi"}
 
@@ -1070,7 +1101,7 @@ def gen_grad_kernel(bra, ket):
             E(f"        xc{k} = fma(e, Rb[{(t * S + u) * S + v}], xc{k});")
         E("  }}}")
         for k in range(H0):
-            E(f"  XC[{(di * H0 + k) * NCD} + cd] = xc{k};")
+            E(f"  XC[{(di * H0 + k) * NCDx} + cd] = xc{k};")
         E("  }")
     E("}")  # cd
     E("}  // ket primitives")
@@ -1082,8 +1113,8 @@ def gen_grad_kernel(bra, ket):
     E(f"  const int bx_ = c_comp_{lb}[3 * b], by_ = c_comp_{lb}[3 * b + 1], bz_ = c_comp_{lb}[3 * b + 2];")
     E("  const int ai[3] = {ax_, ay_, az_}, bi[3] = {bx_, by_, bz_};")
     E("  const double* ebv[3] = {ebx, eby, ebz};")
-    E(f"  for (int cd = 0; cd < {NCD}; ++cd) {{")
-    E(f"    const double g = G[ab * {NCD} + cd];")
+    E(f"  for (int cd = 0; cd < {NCDx}; ++cd) {{")
+    E(f"    const double g = G[ab * {NCDx} + cd];")
     E("    if (g == 0.0) continue;")
     # plain bra E over H0 for the C derivative; derivative bra E over H1 for A and B
     E("    for (int dir = 0; dir < 3; ++dir) {")
@@ -1107,11 +1138,11 @@ def gen_grad_kernel(bra, ket):
     E("        }")
     E("        const int tot = t + u + v;")
     E("        const int h = tot * (tot + 1) * (tot + 2) / 6 + (tot - t) * (tot - t + 1) / 2 + (tot - t - u);")
-    E(f"        const double xv = X[h * {NCD} + cd];")
+    E(f"        const double xv = X[h * {NCDx} + cd];")
     E("        vA = fma(fA, xv, vA);")
     E("        vB = fma(fB, xv, vB);")
     E(f"        if (tot <= {la + lb} && t <= ai[0] + bi[0] && u <= ai[1] + bi[1] && v <= ai[2] + bi[2])")
-    E(f"          vC = fma(f0, XC[(dir * {H0} + h) * {NCD} + cd], vC);")
+    E(f"          vC = fma(f0, XC[(dir * {H0} + h) * {NCDx} + cd], vC);")
     E("      }")
     E("      gA[dir] = fma(g, vA, gA[dir]);")
     E("      gB[dir] = fma(g, vB, gB[dir]);")
@@ -1132,7 +1163,7 @@ def gen_grad_kernel(bra, ket):
 int launch_grad_{name}(const gb::GradArgs& a, cudaStream_t s) {{
   if (a.total <= 0) return 0;
   const int bs = 128;
-  eri_grad_{name}_f64<<<(unsigned)((a.total + bs - 1) / bs), bs, 0, s>>>(a);
+  eri_grad_{name}_f64<<<(unsigned)((a.total{f" * {nc}" if chunk else ""} + bs - 1) / bs), bs, 0, s>>>(a);
   return (int)cudaGetLastError();
 }}""")
     return "\n".join(em.lines) + "\n"
@@ -1268,7 +1299,7 @@ def class_pairs(lmax):
     return [(pcs[i], pcs[j]) for i in range(len(pcs)) for j in range(i + 1)]
 
 
-GRAD_LMAX = 2  # derivative kernels are generated for shells up to d
+GRAD_LMAX = 3  # derivative kernels for every class (f classes in the chunked form)
 
 
 def generate(outdir, lmax=LMAX, nfiles=None):
@@ -1337,11 +1368,14 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
         fn = os.path.join(outdir, f"md_classes_{k}.cu")
         _write_if_changed(fn, "".join(src))
         files.append(fn)
-    # gradient kernels (rolled loops, compact), spread over a few TUs
-    ngf = 4
+    # gradient kernels, spread over translation units by generated code size
+    ngf = max(4, len(gqs) // 5)
     gbins = [[] for _ in range(ngf)]
-    for i, (bra, ket) in enumerate(sorted(gqs, key=lambda x: -sum(x[0] + x[1]))):
-        gbins[i % ngf].append((bra, ket))
+    gload = [0] * ngf
+    for bra, ket in sorted(gqs, key=lambda x: -len(gen_grad_kernel(*x))):
+        k = gload.index(min(gload))
+        gbins[k].append((bra, ket))
+        gload[k] += len(gen_grad_kernel(bra, ket))
     for k, items in enumerate(gbins):
         if not items:
             continue

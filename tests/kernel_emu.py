@@ -66,8 +66,9 @@ def _sources(lmax, only=None, ntu=8):
             sw_cases.append(f"    case {pcs.index(bra)}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(count * {nthr}); "
                             f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); return 0;")
         if (bra, ket) in gqs:
-            grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)total; ++blockIdx.x) "
-                              f"eri_grad_{name}_f64(g); return 0;")
+            gthr = mg.grad_threads(bra, ket)  # threads per work item (chunked f classes: ket components)
+            grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(total * {gthr}); "
+                              f"++blockIdx.x) eri_grad_{name}_f64(g); return 0;")
     src = ['#include "eri_device.cuh"', "#include <vector>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,

@@ -115,15 +115,6 @@ def test_f_classes_mixed(g):
     assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-6
 
 
-def test_gradient_rejects_f_shells(g):
-    mol = molgen.random_molecule(33, 2, [0, 3], 1, 1, 0.5, 5.0, layout="lattice", spacing=2.0)
-    pairs = g.ShellPairs(mol)
-    D = torch.from_numpy(molgen.density(mol, 34)).cuda()
-    with pytest.raises(g.JKError) as e:
-        g.jk_grad(pairs, D, "fp64")
-    assert e.value.code == -5
-
-
 @pytest.mark.parametrize("seed,shells,natom,kmax", [(41, [0, 1, 2], 3, 3), (42, [2, 2, 1], 2, 4), (43, [2, 0, 1, 2], 3, 2)])
 def test_all_fp32_kernels_against_oracle(g, seed, shells, natom, kmax):
     """Every quartet through the FP32 kernels (cutoff above every bound): the

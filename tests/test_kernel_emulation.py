@@ -43,6 +43,19 @@ def test_emulated_gradient():
     assert np.abs(g - go).max() <= 1e-10 * max(1.0, np.abs(go).max())
 
 
+@pytest.mark.parametrize("seed,shells", [(69, [0, 3]), (70, [3, 1]), (71, [2, 3])])
+def test_emulated_gradient_f_classes(seed, shells):
+    """Derivative kernels of classes with an f shell (one thread per work item
+    and ket component, rolled R) against the oracle's analytic gradient."""
+    mol, D = _mol(seed, shells, 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=3)
+    g = pr.grad()
+    go = oracle.grad(mol, D, mode="unique")
+    scale = max(1.0, np.abs(go).max())
+    assert np.abs(g - go).max() <= 1e-10 * scale, np.abs(g - go).max()
+    assert np.abs(g.sum(axis=0)).max() <= 1e-10 * scale
+
+
 @pytest.mark.parametrize("seed,shells", [(65, [0, 3]), (66, [1, 3])])
 def test_emulated_f_classes(seed, shells):
     """Classes with an f shell (one thread per ket component, rolled R)."""
