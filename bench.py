@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-single-seconds", type=float, default=4.0)
     return ap.parse_args()
 
 
@@ -63,6 +64,23 @@ def oracle_sample_rate(mol, D, thresh, seconds, seed=77):
     oracle.jk_quartets(mol, D, q)
     dt = time.perf_counter() - t
     return n / dt, n, dt, oracle.num_threads()
+
+
+def oracle_single_thread_rate(seconds):
+    """The same bounded oracle sample on one host thread, in a child process
+    started with OMP_NUM_THREADS=1 (this process's OpenMP pool is already
+    sized); None if the child fails."""
+    code = ("import json, bench, molgen; mol, D = molgen.config(bench.CONFIG); "
+            f"print(json.dumps(bench.oracle_sample_rate(mol, D, molgen.CONFIG_THRESH[bench.CONFIG], {seconds!r})))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+        rate, n, dt, thr = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+    return {"value": rate, "unit": "quartets/s", "cores": thr,
+            "sample": f"{n} random screened unique shell quartets of the same workload ({dt:.1f} s)"}
 
 
 def run_reference(args):
@@ -334,7 +352,8 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             rate, n, dt, thr = oracle_sample_rate(mol, D, thresh, args.cpu_seconds)
             cpu = {"value": rate, "unit": "quartets/s", "cores": thr, "kind": "oracle",
-                   "sample": f"{n} random screened unique shell quartets of the same workload ({dt:.1f} s)"}
+                   "sample": f"{n} random screened unique shell quartets of the same workload ({dt:.1f} s)",
+                   "single_thread": oracle_single_thread_rate(args.cpu_single_seconds)}
         out = {
             "metric": METRIC, "value": nq * world / (t_mx * 1e-3), "unit": "quartets/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mx, "higher_is_better": True,
