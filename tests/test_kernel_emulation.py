@@ -56,7 +56,7 @@ def test_emulated_gradient_f_classes(seed, shells):
     assert np.abs(g.sum(axis=0)).max() <= 1e-10 * scale
 
 
-@pytest.mark.parametrize("seed,shells", [(65, [0, 3]), (66, [1, 3])])
+@pytest.mark.parametrize("seed,shells", [(65, [0, 3]), (66, [1, 3]), (72, [0, 1, 2, 3])])
 def test_emulated_f_classes(seed, shells):
     """Classes with an f shell (one thread per ket component, rolled R)."""
     mol, D = _mol(seed, shells, 2, 2)
