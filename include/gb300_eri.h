@@ -248,6 +248,11 @@ int jk_fma_peak(jk_precision prec, int iters, double* flops_per_s, void* cuda_st
  * Asynchronous on cuda_stream. */
 int jk_one_electron(jk_pairs pairs, const double* charges, double* S, double* T, double* V, void* cuda_stream);
 
+/* Limits compiled into this library (host, no device work): the highest
+ * shell angular momentum shellpairs_build accepts and the highest one
+ * jk_grad differentiates (both JK_LMAX = 3 in the default build). */
+int jk_limits(int* lmax, int* grad_lmax);
+
 /* Pure (real solid-harmonic) d and f shells.  The integrals of Sec. 2.2
  * (Eq. 1) are over Cartesian components; a basis with pure d/f shells is
  * served by transforming matrices between the two bases:

@@ -44,7 +44,7 @@ EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_bui
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
            "jk_set_tuning", "jk_split_stats", "jk_sph_nbf", "jk_sph_transform",
-           "jk_one_electron"]
+           "jk_one_electron", "jk_limits"]
 
 
 def load():
@@ -77,6 +77,7 @@ def load():
         lib.jk_profile.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
         lib.jk_one_electron.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.jk_limits.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int)]
         lib.jk_sph_nbf.argtypes = [vp, C.POINTER(C.c_int)]
         lib.jk_sph_transform.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.shellpairs_free.argtypes = [vp]
@@ -187,6 +188,13 @@ def jk_grad(pairs: ShellPairs, D, precision: str = "fp64", out=None, stream=None
         out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
     _check(load().jk_grad(pairs.handle, _dev_ptr(D), _dev_ptr(out), _PREC[precision], _stream_ptr(stream)))
     return out
+
+
+def limits() -> dict:
+    """Compiled limits: {"lmax": highest shell l, "grad_lmax": highest l of jk_grad}."""
+    a, b = C.c_int(), C.c_int()
+    _check(load().jk_limits(C.byref(a), C.byref(b)))
+    return {"lmax": a.value, "grad_lmax": b.value}
 
 
 def one_electron(pairs: ShellPairs, charges, stream=None, device=None):

@@ -2217,6 +2217,15 @@ int jk_one_electron(jk_pairs h, const double* charges, double* S, double* T, dou
     return JK_OK;
 }
 
+int jk_limits(int* lmax, int* grad_lmax) {
+    if (!lmax || !grad_lmax) return fail(JK_ERR_INVALID, "null argument");
+    int l = 0;
+    while ((l + 2) * (l + 3) / 2 <= gb_num_pair_classes()) ++l;  // pair classes compiled: (lmax+1)(lmax+2)/2
+    *lmax = l;
+    *grad_lmax = gb_grad_lmax();
+    return JK_OK;
+}
+
 int jk_sph_nbf(jk_pairs h, int* nsph) {
     if (!h || !nsph) return fail(JK_ERR_INVALID, "bad argument");
     *nsph = h->nsph;

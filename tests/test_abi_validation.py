@@ -231,3 +231,9 @@ def test_new_entry_points_reject_null_arguments(lib):
     assert "null" in err(lib)
     assert lib.jk_one_electron(None, p, p, p, p, None) == JK_ERR_INVALID
     assert "null" in err(lib)
+
+
+def test_limits(lib):
+    import paper_2412_13203_gb300 as g
+    assert g.limits() == {"lmax": 3, "grad_lmax": 3}
+    assert lib.jk_limits(None, None) == JK_ERR_INVALID
