@@ -387,18 +387,27 @@ def _autograd():
         placed at the atom positions ``xyz`` (a [natom, 3] float64 tensor).
 
         Forward: shellpairs_build at xyz + jk_build + jk_energy.  Backward:
-        dE/dxyz from jk_grad (the adjoint kernel), dE/dD = J - K/2."""
+        dE/dxyz from jk_grad (the adjoint kernel), dE/dD = J - K/2.  With
+        ``pure`` D is a density over pure d/f shells: the build runs on
+        T D T^T and J, K are taken back to the pure basis (T does not depend
+        on the geometry, so dE/dxyz is the Cartesian gradient at T D T^T)."""
 
         @staticmethod
-        def forward(ctx, xyz, D, mol, thresh=None, precision="fp64"):
+        def forward(ctx, xyz, D, mol, thresh=None, precision="fp64", pure=False):
             import copy
             m = copy.copy(mol)
             m.xyz = xyz.detach().cpu().numpy().astype(np.float64)
             pairs = ShellPairs(m, thresh)
             Dc = D.detach().contiguous()
-            J, K = jk_build(pairs, Dc, precision)
+            if pure:
+                Dx = sph_transform(pairs, Dc, "to_cartesian")
+                Jx, Kx = jk_build(pairs, Dx, precision)
+                J, K = sph_transform(pairs, Jx, "to_pure"), sph_transform(pairs, Kx, "to_pure")
+                g = jk_grad(pairs, Dx, precision)
+            else:
+                J, K = jk_build(pairs, Dc, precision)
+                g = jk_grad(pairs, Dc, precision)
             E = jk_energy(Dc, J, K)
-            g = jk_grad(pairs, Dc, precision)
             pairs.free()
             ctx.save_for_backward(g, J, K)
             return torch.tensor(E, dtype=torch.float64, device=xyz.device)
@@ -408,7 +417,7 @@ def _autograd():
             g, J, K = ctx.saved_tensors
             gx = (gout * g).to(g.device)
             gD = gout * (J - 0.5 * K)
-            return gx, gD, None, None, None
+            return gx, gD, None, None, None, None
 
     return JKEnergy
 
@@ -416,9 +425,10 @@ def _autograd():
 _JKE = None
 
 
-def jk_energy_fn(xyz, D, mol, thresh=None, precision="fp64"):
-    """Differentiable E = tr(DJ)/2 - tr(DK)/4 (torch.autograd.Function)."""
+def jk_energy_fn(xyz, D, mol, thresh=None, precision="fp64", pure=False):
+    """Differentiable E = tr(DJ)/2 - tr(DK)/4 (torch.autograd.Function); D
+    over pure d/f shells if ``pure``."""
     global _JKE
     if _JKE is None:
         _JKE = _autograd()
-    return _JKE.apply(xyz, D, mol, thresh, precision)
+    return _JKE.apply(xyz, D, mol, thresh, precision, pure)

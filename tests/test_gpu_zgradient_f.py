@@ -44,3 +44,23 @@ def test_pure_gradient_with_f_shells(g):
     go = oracle.grad(mol, T @ Dp @ T.T, mode="unique")
     scale = max(1.0, np.abs(go).max())
     assert np.abs(gg - go).max() <= 1.6e-9 * scale
+
+
+def test_autograd_pure_with_f_shells(g):
+    """jk_energy_fn over pure d/f shells: E, dE/dxyz and dE/dD against the
+    oracle's pure-basis J/K and its gradient at T D T^T."""
+    from oracle import spherical as sp
+    mol = molgen.random_molecule(339, 2, [0, 1, 2, 3], 1, 2, 0.2, 20.0, layout="lattice", spacing=2.0)
+    T = sp.transform_matrix(mol)
+    C = np.random.default_rng(340).normal(0, 0.1, (T.shape[1], 5))
+    Dp = C @ C.T
+    xyz = torch.tensor(mol.xyz, dtype=torch.float64, device="cuda", requires_grad=True)
+    Dt = torch.tensor(Dp, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = g.jk_energy_fn(xyz, Dt, mol, pure=True)
+    E.backward()
+    Jo, Ko = sp.jk_pure(mol, Dp)
+    Eo = 0.5 * np.sum(Dp * Jo) - 0.25 * np.sum(Dp * Ko)
+    assert abs(float(E.detach()) - Eo) <= 1.6e-9 * max(1.0, abs(Eo))
+    go = oracle.grad(mol, T @ Dp @ T.T, mode="unique")
+    assert np.abs(xyz.grad.cpu().numpy() - go).max() <= 1.6e-9 * max(1.0, np.abs(go).max())
+    assert np.abs(Dt.grad.cpu().numpy() - (Jo - 0.5 * Ko)).max() <= 1.6e-9 * max(1.0, np.abs(Jo).max())
