@@ -177,13 +177,14 @@ typedef enum {
     JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous) */
     JK_OPT_GRAPH = 3,            /* nonzero: jk_build_batched captures and replays a CUDA graph */
     JK_OPT_PROFILE = 4,          /* nonzero: jk_build records CUDA events around every class launch */
-    JK_OPT_DENSITY_SCREEN = 5    /* mixed builds (single and batched): skip a shell quartet whose
-                                  * density-weighted bound Q_ab Q_cd max|D| (global max, or over the six
-                                  * D blocks it reads where that bound reaches tau) is below this value
-                                  * (default 0: no quartet is skipped).  For incremental builds,
-                                  * J(D) = J(D_prev) + J(D - D_prev): the difference density makes the
-                                  * bounds small, so most quartets are skipped.  Skipped quartets are
-                                  * counted in neither part of jk_last_split. */
+    JK_OPT_DENSITY_SCREEN = 5    /* mixed builds (single and batched): skip a shell quartet whose bound
+                                  * Q_ab Q_cd max|D| is below this value, with max|D| over the whole
+                                  * matrix, and, for the quartets whose global bound reaches tau, over
+                                  * the six D blocks the quartet reads (default 0: nothing is skipped).
+                                  * For incremental builds, J(D) = J(D_prev) + J(D - D_prev): the
+                                  * difference density makes the bounds small, so many quartets are
+                                  * skipped.  Skipped quartets are counted in neither part of
+                                  * jk_last_split. */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);
