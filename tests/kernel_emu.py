@@ -212,7 +212,7 @@ class Problem:
     runtime lays them out (pairs canonicalised l_a >= l_b, grouped by class;
     for bra class = ket class only kets up to the bra)."""
 
-    def __init__(self, mol, D, oracle, lmax=2, own_classes=False):
+    def __init__(self, mol, D, oracle, lmax=2, own_classes=False, q_order=False):
         self.mol, self.lmax = mol, lmax
         c = oracle.normalize(mol)
         l, K, off, atom = mol.shell_l, mol.shell_nprim, mol.shell_prim_offset, mol.shell_atom
@@ -224,8 +224,11 @@ class Problem:
             for j in range(i + 1):
                 a, b = (j, i) if l[j] > l[i] else (i, j)
                 pairs.append((self.pcs.index((int(l[a]), int(l[b]))), a, b))
-        pairs.sort()
         Q = oracle.schwarz(mol)
+        if q_order:  # as the runtime: inside a class by Schwarz factor, largest first
+            pairs.sort(key=lambda x: (x[0], -Q[x[1], x[2]], x[1], x[2]))
+        else:
+            pairs.sort()
         info, A, B, pp, pp2, ppf, ppf2, alpha, atoms = [], [], [], [], [], [], [], [], []
         s2 = math.sqrt(2 * math.pi ** 2.5)
         for cls, a, b in pairs:

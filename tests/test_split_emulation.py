@@ -54,8 +54,8 @@ extern "C" void emu_fill(const int* rbra, const int* rket0, const int* k32, int 
 """
 
 
-@pytest.fixture(scope="module")
-def lib():
+def build_split_lib():
+    """Compile (cached by source hash) and load the split-kernel emulation library."""
     os.makedirs(BUILD, exist_ok=True)
     drv = os.path.join(BUILD, "driver.cpp")
     with open(drv, "w") as f:
@@ -77,6 +77,11 @@ def lib():
                             + [vp] * 8)
     L.emu_fill.argtypes = [vp, vp, vp, C.c_int, vp, C.c_double, C.c_double, vp, vp, C.c_int, vp, vp, vp, vp]
     return L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return build_split_lib()
 
 
 def _rows(seed, nshell=12, npair=40, nrows=25):
