@@ -38,3 +38,32 @@ def test_library_loads_and_reports_errors():
     rc = lib.shellpairs_info(None, None, None, None, None)
     assert rc == -1 and b"null" in lib.jk_last_error()
     assert lib.jk_set_option(0, -1.0) == -1
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """A C99 program includes the header, links the library and calls host-only
+    entry points (no GPU needed): the boundary is usable without C++ or torch."""
+    from paper_2412_13203_gb300 import build
+    lib = build.build()
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "gb300_eri.h"
+int main(void) {
+    int lmax = -1, glmax = -1;
+    double tau = 0.0;
+    if (jk_limits(&lmax, &glmax) != JK_OK) return 1;
+    if (jk_get_option(JK_OPT_MIXED_TAU, &tau) != JK_OK) return 2;
+    if (shellpairs_info(NULL, NULL, NULL, NULL, NULL) != JK_ERR_INVALID) return 3;
+    if (strlen(jk_last_error()) == 0) return 4;
+    printf("%d %d %g\n", lmax, glmax, tau);
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"), str(src),
+                    lib, "-o", str(exe), f"-Wl,-rpath,{os.path.dirname(lib)}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out
+    assert out.stdout.split() == ["3", "3", "0.01"]
