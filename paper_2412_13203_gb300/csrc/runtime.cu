@@ -1,10 +1,13 @@
 // Host runtime and C ABI of the screened-ERI / J-K library (include/gb300_eri.h).
 //
-// Everything on the data path runs in the kernels of this file and of the
-// generated per-class ERI kernels: coefficient normalisation, primitive
-// Gaussian products, Schwarz factors, the pair sort, the quartet-row
-// enumeration, J/K digestion, symmetrisation and the energy reduction.  The
-// host only validates arguments, sizes launches and reads back a few counts.
+// Everything on the data path runs in the kernels of this file, of the
+// headers it includes (split_kernels.cuh: the mixed-precision split and
+// density screening; sph_transform.cuh: the Cartesian <-> pure transform;
+// one_electron.cuh: S, T, V) and of the generated per-class ERI and
+// derivative kernels: coefficient normalisation, primitive Gaussian
+// products, Schwarz factors, the pair sort, the quartet-row enumeration, J/K
+// digestion, symmetrisation and the energy reduction.  The host only
+// validates arguments, sizes launches and reads back a few counts.
 //
 // Paper mapping (arXiv 2412.13203):
 //   Block Constructor stage 1 (Sec. 4): every basis-function pair, sorted by
