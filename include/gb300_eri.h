@@ -8,7 +8,9 @@
  * contracted on the fly with a density matrix into the Coulomb and exchange
  * matrices of a Fock build,
  *   J_mn = sum_ls (mn|ls) D_ls,     K_mn = sum_ls (ml|ns) D_ls,
- * and the nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D.
+ * and the nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D.  Around
+ * that path: density screening for incremental builds, the one-electron
+ * integrals of the SCF (Sec. 2.1) and the transform to pure d/f shells.
  * The atomic J/K reduction is the one of Sec. 6 ("each thread employs atomic
  * operations"), the pair/quartet blocking that of Sec. 4 (Block Constructor,
  * stages 1-2).
@@ -22,7 +24,8 @@
  *     contracted axial component x^l has unit norm.  Callers pass raw
  *     coefficients.
  *   - Screening: a shell quartet is evaluated iff Q_ab * Q_cd >= thresh,
- *     Q_ab = sqrt(max_i |(ab|ab)_ii|) (plain Schwarz; thresh <= 0 keeps all).
+ *     Q_ab = sqrt(max_i |(ab|ab)_ii|) (plain Schwarz; thresh <= 0 keeps all);
+ *     mixed builds can also screen by density (JK_OPT_DENSITY_SCREEN).
  *   - Matrices D, J, K are nbf x nbf, row-major, contiguous float64 in DEVICE
  *     memory owned by the caller.  D must be symmetric (not checked unless
  *     JK_OPT_CHECK_SYMMETRY is set).  J and K are overwritten.

@@ -35,3 +35,15 @@ def test_config0_spacing():
     mol, _ = molgen.config(0)
     d = np.linalg.norm(mol.xyz[:, None] - mol.xyz[None], axis=-1) + 10 * np.eye(4)
     assert d.min() >= 1.8 and mol.xyz.min() >= 0 and mol.xyz.max() <= 6
+
+
+def test_small_scf_molecules():
+    import molgen
+    h2 = molgen.h2_polarised()
+    assert list(h2.shell_l) == [0, 1, 2, 0, 1, 2] and list(h2.shell_atom) == [0, 0, 0, 1, 1, 1]
+    assert h2.nbf == 20 and list(h2.charges) == [1.0, 1.0]
+    np.testing.assert_array_equal(h2.exps[:3], molgen.h2_sto3g().exps[:3])
+    ch = molgen.h_chain(5, 1.8)
+    assert ch.natom == 5 and ch.nbf == 5 * 4 and ch.nshell == 10
+    np.testing.assert_allclose(np.diff(ch.xyz[:, 2]), 1.8)
+    assert np.all(ch.shell_prim_offset[1:] > ch.shell_prim_offset[:-1])
