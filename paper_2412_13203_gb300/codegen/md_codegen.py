@@ -1197,7 +1197,7 @@ def _r_children(node, axis):
     return kids
 
 
-def r_path(targets, lam=None):
+def r_path(targets, lam=None, rng=None):
     """Nodes R^(n)_{tuv} needed to reach `targets` through the recursion
     R^(n)_{k} = (k_i - 1) R^(n+1)_{k - 2e_i} + X_i R^(n+1)_{k - e_i}.
 
@@ -1205,7 +1205,9 @@ def r_path(targets, lam=None):
     then v).  Otherwise the greedy search of the paper's Graph Compiler
     (Sec. 5, Algorithm 1): going down from the highest total angular momentum,
     every node takes the axis ("recurrence position") of least cost
-    (new - reused) + lam * (angular momentum of the new nodes).
+    (new - reused) + lam * (angular momentum of the new nodes).  rng (a
+    random.Random): every node takes a random valid axis instead, the
+    baseline the paper compares its search with.
     Returns {node: axis or None}."""
     chosen = {}
     todo = set(targets)
@@ -1218,7 +1220,9 @@ def r_path(targets, lam=None):
                 chosen[node] = None
                 continue
             axes = [i for i in range(3) if node[1 + i] > 0]
-            if lam is None:
+            if rng is not None:
+                best = rng.choice(axes)
+            elif lam is None:
                 best = axes[0]
             else:
                 def cost(i):
@@ -1274,10 +1278,12 @@ def r_path_flops(chosen):
     return sum(0 if ax is None else len(_r_children(n, ax)) for n, ax in chosen.items())
 
 
-def path_report(lmax=2, lams=(0.0, 0.5, 1.0, 2.0)):
+def path_report(lmax=2, lams=(0.0, 0.5, 1.0, 2.0), random_paths=0):
     """Per class: R recursion operations of the kernels as emitted (fixed
-    order, per FP32 range kernel where the class has them) and with the
-    greedy path search at the best lam."""
+    order, per FP32 range kernel where the class has them), with the greedy
+    path search at the best lam and, if random_paths > 0, the mean over that
+    many random paths (seeded).  Rows (class, fixed, greedy[, random])."""
+    import random
     rows = []
     for bra, ket in class_pairs(lmax):
         groups = crange_groups(bra, ket)
@@ -1285,7 +1291,12 @@ def path_report(lmax=2, lams=(0.0, 0.5, 1.0, 2.0)):
         sets = [None] if not groups else [[c * nd + d for c in range(c0, c1) for d in range(nd)] for c0, c1 in groups]
         fixed = sum(r_path_flops(r_path(r_targets(bra, ket, cds))) for cds in sets)
         greedy = sum(min(r_path_flops(r_path(r_targets(bra, ket, cds), lam)) for lam in lams) for cds in sets)
-        rows.append((class_name(bra, ket), fixed, greedy))
+        row = (class_name(bra, ket), fixed, greedy)
+        if random_paths:
+            rnd = sum(r_path_flops(r_path(r_targets(bra, ket, cds), rng=random.Random(1000 * k + j)))
+                      for k in range(random_paths) for j, cds in enumerate(sets)) / random_paths
+            row += (rnd,)
+        rows.append(row)
     return rows
 
 
