@@ -40,19 +40,29 @@ def test_one_electron_matches_oracle(g, seed, shells, natom):
 
 
 def test_one_electron_of_a_screened_handle(g):
-    """Elements of pairs the Schwarz threshold drops are 0; the rest match."""
+    """Elements of pairs the Schwarz threshold drops (Q_ab Q_max < thresh) are
+    0; the elements of every kept pair match the oracle."""
     mol = molgen.random_molecule(960, 4, [0, 1], 1, 2, 0.5, 20.0, layout="lattice", spacing=4.0)
     z = np.full(4, 2.0)
     mol.charges = z
-    pairs = g.ShellPairs(mol, 1e-6)
-    npair_all = mol.nshell * (mol.nshell + 1) // 2
-    assert 0 < pairs.npairs < npair_all
+    thresh = 1e-6
+    Q = oracle.schwarz(mol)
+    qq = Q * Q.max()
+    assert not np.any(np.abs(qq / thresh - 1.0) < 1e-6)  # no pair on the boundary
+    pairs = g.ShellPairs(mol, thresh)
+    S_, L_ = mol.nshell, mol.shell_l
+    assert pairs.npairs == sum(1 for a in range(S_) for b in range(a + 1) if qq[a, b] >= thresh) < S_ * (S_ + 1) // 2
+    off = np.concatenate([mol.shell_offsets(), [mol.nbf]])
+    kept = np.zeros((mol.nbf, mol.nbf), bool)
+    for a in range(S_):
+        for b in range(S_):
+            kept[off[a]:off[a + 1], off[b]:off[b + 1]] = qq[a, b] >= thresh
     S, _, V = (M.cpu().numpy() for M in g.one_electron(pairs, z))
     So, _, Vo = oe.one_electron(mol)
-    kept = S != 0.0
     assert (~kept).any()
     np.testing.assert_allclose(S[kept], So[kept], rtol=0, atol=1e-12)
     np.testing.assert_allclose(V[kept], Vo[kept], rtol=0, atol=1e-12 * np.abs(Vo).max())
+    np.testing.assert_array_equal(S[~kept], 0.0)
     np.testing.assert_array_equal(V[~kept], 0.0)
 
 
