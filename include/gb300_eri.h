@@ -35,6 +35,12 @@
  * Errors: every function returns JK_OK (0) or a negative status; the message
  * of the last failure on the calling thread is returned by jk_last_error().
  * No exception crosses this boundary.
+ *
+ * Device state: the library keeps per-device tables (the Boys-function grid,
+ * the device address of jk_energy_noalloc's scratch) for the life of the
+ * process.  They, and every handle, do not survive cudaDeviceReset: after a
+ * reset of a device, call no entry point of this library on it again in the
+ * same process.
  */
 #ifndef GB300_ERI_H
 #define GB300_ERI_H
@@ -115,7 +121,11 @@ int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartet
  * the digestion dot products, from centre differences formed in FP64 --
  * and each digested sum is added to J and K in FP64 (split accumulation);
  * the other quartets, the Boys function at small T, the Schwarz factors and
- * the final J/K symmetrisation stay FP64.  The bound is density-weighted:
+ * the final J/K symmetrisation stay FP64.  JK_FP64 accumulates J' and K'
+ * with compensation (each update split into a multiple of 2^-32, summed
+ * exactly while partial sums stay below 2^21, and a remainder summed
+ * separately; handle-owned nbf x nbf scratch), so the result does not depend
+ * on the order of the atomic updates beyond ~1e-20 per element.  The bound is density-weighted:
  * Q_ab Q_cd times the largest |D| element of the six shell blocks of D the
  * quartet's J and K updates read.  A JK_MIXED build synchronises the stream
  * once, after its split pass, to size its quartet lists; JK_FP64 builds are
@@ -131,6 +141,39 @@ int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision
  * library built for a lower angular momentum returns JK_ERR_UNSUPPORTED for
  * classes above it. */
 int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, void* cuda_stream);
+
+/* Multi-GPU split of one molecule (Sec. 4, stage 2: quartet blocks are
+ * independent; Sec. 7 runs them over several GPUs).  The quartet rows of
+ * every angular class are cut into nparts contiguous ranges of equal
+ * algorithmic cost (the generator's operation count of each row's primitive
+ * quartets and bra primitive pairs), so every part holds the same share of
+ * every class, within the cost of one row.  jk_build_part computes J and K
+ * (device, nbf x nbf, overwritten, symmetrised) from the quartets of part
+ * `part` only; the sum of the nparts results is the full J and K (an
+ * all-reduce across GPUs).  jk_grad_part likewise for dE/dR.  Precision and
+ * stream as jk_build / jk_grad; the first call with a new nparts computes the
+ * partition (one synchronisation) and caches it on the handle.
+ * part outside [0, nparts) or nparts < 1: JK_ERR_INVALID. */
+int jk_build_part(jk_pairs pairs, int part, int nparts, const double* D, double* J, double* K,
+                  jk_precision prec, void* cuda_stream);
+int jk_grad_part(jk_pairs pairs, int part, int nparts, const double* D, double* dEdR,
+                 jk_precision prec, void* cuda_stream);
+
+/* The partition rule used above, on the host (no device work): n consecutive
+ * units of cost[n] (HOST, >= 0, finite) into nparts contiguous ranges;
+ * bounds[nparts + 1] (HOST) receives 0 = b_0 <= b_1 <= ... <= b_nparts = n,
+ * b_p the first unit at which the running cost reaches p/nparts of the total
+ * (equal counts if the total is 0).  Every range then costs total/nparts
+ * within the largest single cost.  JK_ERR_INVALID for a negative or
+ * non-finite cost or nparts < 1. */
+int jk_partition(int64_t n, const double* cost, int nparts, int64_t* bounds);
+
+/* The row partition of a handle for nparts parts (host, synchronous on first
+ * use): up to max_rows rows of 8 int64 -- bra class, ket class, part, first
+ * row, end row, work items, algorithmic cost of the part, largest single-row
+ * cost of the class -- for every class with work and every part.  *nrows
+ * receives the number of rows. */
+int jk_part_rows(jk_pairs pairs, int nparts, int max_rows, int64_t* rows, int* nrows);
 
 /* Many independent molecules in one launch sequence (one persistent launch per
  * angular class over all molecules' work), optionally captured into a CUDA
@@ -177,7 +220,9 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 typedef enum {
     JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys in FP64 for T < tsmall (default 1.0) */
-    JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous) */
+    JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous):
+                                  * JK_ERR_NOT_SYMMETRIC if not, JK_ERR_INVALID if D holds a NaN or
+                                  * an infinity */
     JK_OPT_GRAPH = 3,            /* nonzero: jk_build_batched captures and replays a CUDA graph */
     JK_OPT_PROFILE = 4,          /* nonzero: jk_build records CUDA events around every class launch */
     JK_OPT_DENSITY_SCREEN = 5    /* mixed builds (single and batched): skip a shell quartet whose bound

@@ -44,7 +44,7 @@ EXPORTS = ["shellpairs_build", "shellpairs_info", "jk_build", "jk_grad", "jk_bui
            "jk_set_option", "jk_get_option", "jk_last_split", "shellpairs_free", "jk_last_error",
            "jk_class_stats", "jk_profile", "jk_fma_peak", "jk_last_launches", "jk_autotune", "jk_tuning",
            "jk_set_tuning", "jk_split_stats", "jk_sph_nbf", "jk_sph_transform",
-           "jk_one_electron", "jk_limits"]
+           "jk_one_electron", "jk_limits", "jk_build_part", "jk_grad_part", "jk_partition", "jk_part_rows"]
 
 
 def load():
@@ -78,6 +78,10 @@ def load():
         lib.jk_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), vp]
         lib.jk_one_electron.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.jk_limits.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.jk_build_part.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
+        lib.jk_grad_part.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp]
+        lib.jk_partition.argtypes = [C.c_int64, C.POINTER(C.c_double), C.c_int, i64p]
+        lib.jk_part_rows.argtypes = [vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int)]
         lib.jk_sph_nbf.argtypes = [vp, C.POINTER(C.c_int)]
         lib.jk_sph_transform.argtypes = [vp, C.c_int, vp, vp, vp]
         lib.shellpairs_free.argtypes = [vp]
@@ -188,6 +192,104 @@ def jk_grad(pairs: ShellPairs, D, precision: str = "fp64", out=None, stream=None
         out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
     _check(load().jk_grad(pairs.handle, _dev_ptr(D), _dev_ptr(out), _PREC[precision], _stream_ptr(stream)))
     return out
+
+
+def jk_build_part(pairs: ShellPairs, D, part: int, nparts: int, precision: str = "fp64", J=None, K=None,
+                  stream=None):
+    """J and K from the quartet rows of part ``part`` of ``nparts`` (every
+    class cut into cost-balanced row ranges); the parts sum to jk_build."""
+    import torch
+    n = pairs.nbf
+    if tuple(D.shape) != (n, n):
+        raise ValueError("D must be nbf x nbf")
+    if J is None:
+        J = torch.empty((n, n), dtype=torch.float64, device=D.device)
+    if K is None:
+        K = torch.empty((n, n), dtype=torch.float64, device=D.device)
+    _check(load().jk_build_part(pairs.handle, int(part), int(nparts), _dev_ptr(D), _dev_ptr(J), _dev_ptr(K),
+                                _PREC[precision], _stream_ptr(stream)))
+    return J, K
+
+
+def jk_grad_part(pairs: ShellPairs, D, part: int, nparts: int, precision: str = "fp64", out=None, stream=None):
+    """dE/dR [natom, 3] from the quartet rows of part ``part`` of ``nparts``."""
+    import torch
+    if out is None:
+        out = torch.empty((pairs.natom, 3), dtype=torch.float64, device=D.device)
+    _check(load().jk_grad_part(pairs.handle, int(part), int(nparts), _dev_ptr(D), _dev_ptr(out), _PREC[precision],
+                               _stream_ptr(stream)))
+    return out
+
+
+def partition(cost, nparts: int) -> np.ndarray:
+    """The library's partition rule on the host (no device work): bounds
+    [nparts + 1] of contiguous ranges of equal cost, within one unit's cost."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    b = np.zeros(int(nparts) + 1, dtype=np.int64)
+    _check(load().jk_partition(int(c.shape[0]), c.ctypes.data_as(C.POINTER(C.c_double)), int(nparts),
+                               b.ctypes.data_as(C.POINTER(C.c_int64))))
+    return b
+
+
+def part_rows(pairs: ShellPairs, nparts: int):
+    """Row partition of a handle: per class and part, (first row, end row,
+    work items, cost, largest row cost of the class)."""
+    cap = 64 * int(nparts)
+    buf = (C.c_int64 * (8 * cap))()
+    n = C.c_int()
+    _check(load().jk_part_rows(pairs.handle, int(nparts), cap, buf, C.byref(n)))
+    out = []
+    for k in range(min(n.value, cap)):
+        r = buf[8 * k:8 * k + 8]
+        out.append(dict(cls=PAIR_CLASS_NAMES[r[0]] + "|" + PAIR_CLASS_NAMES[r[1]], part=r[2], r0=r[3], r1=r[4],
+                        items=r[5], cost=r[6], max_row_cost=r[7]))
+    return out
+
+
+def allreduce_jk(J, K, group=None):
+    """Sum partial J and K over the ranks of ``group`` (torch.distributed,
+    NCCL for CUDA tensors, gloo for CPU ones) in one collective: the two
+    matrices are reduced as one stacked buffer when they are views of it."""
+    import torch
+    import torch.distributed as dist
+    base = J._base if J._base is not None and J._base is K._base else None
+    if base is not None and base.is_contiguous() and base.numel() == J.numel() + K.numel():
+        dist.all_reduce(base, op=dist.ReduceOp.SUM, group=group)
+    else:
+        JK = torch.stack([J, K])
+        dist.all_reduce(JK, op=dist.ReduceOp.SUM, group=group)
+        J.copy_(JK[0])
+        K.copy_(JK[1])
+    return J, K
+
+
+def jk_build_distributed(pairs: ShellPairs, D, precision: str = "fp64", group=None, stream=None):
+    """One molecule's J and K over the ranks of a torch.distributed group:
+    rank r builds part r of world (cost-balanced quartet rows of every
+    class), then one all-reduce sums the parts.  Without an initialised
+    group of more than one rank this is jk_build."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return jk_build(pairs, D, precision, stream=stream)
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    n = pairs.nbf
+    JK = torch.empty((2, n, n), dtype=torch.float64, device=D.device)
+    J, K = JK[0], JK[1]
+    jk_build_part(pairs, D, rank, world, precision, J=J, K=K, stream=stream)
+    allreduce_jk(J, K, group)
+    return J, K
+
+
+def jk_grad_distributed(pairs: ShellPairs, D, precision: str = "fp64", group=None, stream=None):
+    """dE/dR of one molecule over the ranks of a group: a part per rank, one
+    all-reduce (sum) of the [natom, 3] gradient."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return jk_grad(pairs, D, precision, stream=stream)
+    g = jk_grad_part(pairs, D, dist.get_rank(group), dist.get_world_size(group), precision, stream=stream)
+    dist.all_reduce(g, op=dist.ReduceOp.SUM, group=group)
+    return g
 
 
 def limits() -> dict:
@@ -387,7 +489,8 @@ def _autograd():
         placed at the atom positions ``xyz`` (a [natom, 3] float64 tensor).
 
         Forward: shellpairs_build at xyz + jk_build + jk_energy.  Backward:
-        dE/dxyz from jk_grad (the adjoint kernel), dE/dD = J - K/2.  With
+        dE/dxyz from jk_grad (the adjoint kernel, run only when xyz requires
+        a gradient; the handle is kept until then), dE/dD = J - K/2.  With
         ``pure`` D is a density over pure d/f shells: the build runs on
         T D T^T and J, K are taken back to the pure basis (T does not depend
         on the geometry, so dE/dxyz is the Cartesian gradient at T D T^T)."""
@@ -403,20 +506,29 @@ def _autograd():
                 Dx = sph_transform(pairs, Dc, "to_cartesian")
                 Jx, Kx = jk_build(pairs, Dx, precision)
                 J, K = sph_transform(pairs, Jx, "to_pure"), sph_transform(pairs, Kx, "to_pure")
-                g = jk_grad(pairs, Dx, precision)
             else:
+                Dx = Dc
                 J, K = jk_build(pairs, Dc, precision)
-                g = jk_grad(pairs, Dc, precision)
             E = jk_energy(Dc, J, K)
-            pairs.free()
-            ctx.save_for_backward(g, J, K)
+            # the adjoint kernel runs in backward, and only if xyz needs a gradient
+            if ctx.needs_input_grad[0]:
+                ctx.pairs, ctx.Dx, ctx.precision = pairs, Dx, precision
+            else:
+                pairs.free()
+                ctx.pairs = None
+            ctx.save_for_backward(J, K)
             return torch.tensor(E, dtype=torch.float64, device=xyz.device)
 
         @staticmethod
         def backward(ctx, gout):
-            g, J, K = ctx.saved_tensors
-            gx = (gout * g).to(g.device)
-            gD = gout * (J - 0.5 * K)
+            J, K = ctx.saved_tensors
+            gx = None
+            if ctx.pairs is not None:
+                g = jk_grad(ctx.pairs, ctx.Dx, ctx.precision)
+                ctx.pairs.free()
+                ctx.pairs, ctx.Dx = None, None
+                gx = (gout * g).to(g.device)
+            gD = gout * (J - 0.5 * K) if ctx.needs_input_grad[1] else None
             return gx, gD, None, None, None, None
 
     return JKEnergy

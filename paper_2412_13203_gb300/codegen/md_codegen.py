@@ -778,17 +778,17 @@ def gen_class_kernels(bra, ket):
         if chunk:
             body, st = gen_quartet_body_chunk(bra, ket, real)
             variants.append(("", body, f"gb::digest_chunk<{na}, {nb}, {nc}, {nd}>(acc, ci, ib.x, ib.y, ik.x, ik.y, "
-                                       f"{{dm}}, Jm, Km, nbf);", na * nb * nd))
+                                       f"{{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * nd))
         elif prec == "f32" and crange_groups(bra, ket):
             for c0, c1 in crange_groups(bra, ket):
                 cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
                 body, st = gen_quartet_body(bra, ket, real, True, cds)
                 variants.append((f"_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, ib.x, "
-                                                  f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);", na * nb * len(cds)))
+                                                  f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * len(cds)))
         else:
             body, st = gen_quartet_body(bra, ket, real, flat)
             variants.append(("", body, f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
-                                       f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, nbf);", na * nb * nc * nd))
+                                       f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * nc * nd))
         if prec == "f64":
             stats = st
         if real == "float":
@@ -809,7 +809,10 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   // first shell).  Items are taken from the end: the rows are ordered by
   // ascending ket primitive count, so the heaviest work goes first and the
   // tail of the launch is light.
-  const long long total = args.rows.start[args.rows.nrows] * {nch};
+  // a launch may cover a sub-range of a class's rows (partial builds): its work
+  // items are start[0] .. start[nrows] - 1
+  const long long base = args.rows.start[0];
+  const long long total = (args.rows.start[args.rows.nrows] - base) * {nch};
   const double* __restrict__ boys = args.boys;
   const float* __restrict__ boysf = args.boysf;
   const float tsmall = args.tsmall;
@@ -817,8 +820,9 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
        tid += (long long)gridDim.x * blockDim.x) {{
   const long long rt = total - 1 - tid;
-  const long long qt = rt / {nch};
-  const int ci = (int)(rt - qt * {nch});
+  const long long qq = rt / {nch};
+  const int ci = (int)(rt - qq * {nch});
+  const long long qt = base + qq;
   (void)ci;
   int row;
   long long li;
@@ -829,11 +833,14 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   const float* Dfm = args.Df;
   double* Jm = args.J;
   double* Km = args.K;
+  double* Jlm = args.Jlo;
+  double* Klm = args.Klo;
   int nbf = args.nbf;
-  (void)Dm; (void)Dfm;
+  (void)Dm; (void)Dfm; (void)Jlm; (void)Klm;
   if (args.mols) {{
     const gb::BatchMol& bm = args.mols[args.row_mol[row]];
     pairs = bm.pairs; Dm = bm.D; Dfm = bm.Df; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
+    Jlm = bm.Jlo; Klm = bm.Klo;
   }}
   const int4 ib = pairs.info[bra];
   const int nsplit = min({P}, ib.z);
@@ -986,7 +993,7 @@ def gen_grad_kernel(bra, ket):
     P = split_of(bra, ket)
     E("int row;")
     E("long long li;")
-    E("gb::locate_row(args.rows, args.total - 1 - tid, row, li);")
+    E("gb::locate_row(args.rows, args.base + args.total - 1 - tid, row, li);")
     E("const int bra = __ldg(args.rows.bra + row);")
     E("const gb::PairsView& pairs = args.pairs;")
     E("const double* __restrict__ boys = args.boys;")

@@ -59,6 +59,8 @@ struct BatchMol {
     int nshell;
     double* J;
     double* K;
+    double* Jlo;              // compensated accumulation of FP64 builds (nullptr: plain atomics)
+    double* Klo;
     int nbf;
 };
 
@@ -72,6 +74,8 @@ struct JKArgs {
     const float* Df;          // FP32 copy of D (mixed builds: digestion of the FP32 quartets)
     double* J;                // accumulates J' (J = J' + J'^T afterwards)
     double* K;                // accumulates K'
+    double* Jlo;              // FP64 builds: remainders of the split accumulation (see jk_add);
+    double* Klo;              // nullptr: plain FP64 atomics (mixed builds)
     int nbf;
     const BatchMol* mols;     // batched launches: per-molecule data (nullptr: single molecule above)
     const int* row_mol;       // batched launches: molecule of every row
@@ -80,7 +84,8 @@ struct JKArgs {
 struct GradArgs {
     PairsView pairs;
     RowsView rows;
-    long long total;
+    long long base;           // first work item of the launch (rows.start[0]; 0 for a whole class)
+    long long total;          // work items of the launch
     const double* boys;
     const double* D;
     int nbf;
@@ -181,6 +186,31 @@ __device__ __forceinline__ void locate_row(const RowsView& rv, long long t, int&
 }
 
 // ------------------------------------------------------------------ digestion
+// One J'/K' update.  FP64 builds pass lo arrays and accumulate with
+// compensation: the value is split into vh, a multiple of 2^-32 (round to
+// nearest through v + C - C with C = 1.5 * 2^20), and the exact remainder
+// v - vh (|v - vh| <= 2^-33).  The multiples add up in X without rounding as
+// long as every partial sum stays below 2^21 in magnitude; the remainders add
+// up in lo with a rounding error below 1e-25 per update.  X + lo is then the
+// sum of the updates to about 1e-20, whatever order the atomics land in
+// (plain FP64 atomics round every update to the element's ulp, and 1e6 updates
+// of an element of size 4 can drift by 1e-10).  Mixed builds (lo null) and
+// FP32 quartets add plainly.
+constexpr double kSplitC = 1572864.0;  // 1.5 * 2^20: ulp 2^-32
+
+template <class R>
+__device__ __forceinline__ void jk_add(double* X, double* lo, size_t i, double v) {
+    if constexpr (sizeof(R) == sizeof(double)) {
+        if (lo) {
+            const double vh = __dsub_rn(__dadd_rn(v, kSplitC), kSplitC);
+            atomicAdd(X + i, vh);
+            atomicAdd(lo + i, __dsub_rn(v, vh));
+            return;
+        }
+    }
+    atomicAdd(X + i, v);
+}
+
 // Fused J/K update of one unique shell quartet (ab|cd), acc[((a*NB+b)*NC+c)*ND+d],
 // already scaled by the degeneracy factor s.  With the eight permutational
 // images and a symmetric D,
@@ -193,7 +223,8 @@ __device__ __forceinline__ void locate_row(const RowsView& rv, long long t, int&
 // in FP64 by the atomics).
 template <int NA, int NB, int NC, int ND, class R>
 __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int fd,
-                                       const R* __restrict__ D, double* J, double* K, int n) {
+                                       const R* __restrict__ D, double* J, double* K, double* Jlo,
+                                       double* Klo, int n) {
     // J'_ab
 #pragma unroll
     for (int a = 0; a < NA; ++a)
@@ -205,7 +236,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fc + c) * n + fd + d), v);
-            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+            jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
         }
     // J'_cd
 #pragma unroll
@@ -218,7 +249,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fb + b), v);
-            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
+            jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
         }
     // K'_ac and K'_ad
 #pragma unroll
@@ -231,7 +262,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
@@ -241,7 +272,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
     }
     // K'_bc and K'_bd
@@ -255,7 +286,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
@@ -265,7 +296,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
     }
 }
@@ -276,7 +307,8 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 // launch; the ranges' updates add up to the full one).
 template <int NA, int NB, int NC, int ND, int C0, int C1, class R>
 __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int fc, int fd,
-                                              const R* __restrict__ D, double* J, double* K, int n) {
+                                              const R* __restrict__ D, double* J, double* K, double* Jlo,
+                                       double* Klo, int n) {
     constexpr int NCR = C1 - C0;
 #define GB_ACC(a, b, c, d) acc[(((a) * NB + (b)) * NCR + ((c) - C0)) * ND + (d)]
 #pragma unroll
@@ -288,7 +320,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int c = C0; c < C1; ++c)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fc + c) * n + fd + d), v);
-            atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+            jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
         }
 #pragma unroll
     for (int c = C0; c < C1; ++c)
@@ -299,7 +331,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int b = 0; b < NB; ++b) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fb + b), v);
-            atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
+            jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
         }
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
@@ -310,7 +342,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {  // K'_ad
@@ -319,7 +351,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
     }
 #pragma unroll
@@ -331,7 +363,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {  // K'_bd
@@ -340,7 +372,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
     }
 #undef GB_ACC
@@ -351,14 +383,15 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 // lives in local memory there anyway).
 template <int NA, int NB, int NC, int ND, class R>
 __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc, int fd,
-                                            const R* __restrict__ D, double* J, double* K, int n) {
+                                            const R* __restrict__ D, double* J, double* K, double* Jlo,
+                                       double* Klo, int n) {
 #pragma unroll 1
     for (int ab = 0; ab < NA * NB; ++ab) {
         const int a = ab / NB, b = ab % NB;
         R v = 0;
         for (int cd = 0; cd < NC * ND; ++cd)
             v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fc + cd / ND) * n + fd + cd % ND), v);
-        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+        jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
     }
 #pragma unroll 1
     for (int cd = 0; cd < NC * ND; ++cd) {
@@ -366,7 +399,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
         R v = 0;
         for (int ab = 0; ab < NA * NB; ++ab)
             v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
-        atomicAdd(J + (size_t)(fc + c) * n + fd + d, 2.0 * (double)v);
+        jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
     }
 #pragma unroll 1
     for (int a = 0; a < NA; ++a)
@@ -376,7 +409,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             for (int b = 0; b < NB; ++b)
                 for (int d = 0; d < ND; ++d)
                     vac = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
-            atomicAdd(K + (size_t)(fa + a) * n + fc + c, (double)vac);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)vac);
         }
 #pragma unroll 1
     for (int a = 0; a < NA; ++a)
@@ -386,7 +419,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             for (int b = 0; b < NB; ++b)
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
 #pragma unroll 1
     for (int b = 0; b < NB; ++b)
@@ -396,7 +429,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             for (int a = 0; a < NA; ++a)
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fc + c, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll 1
     for (int b = 0; b < NB; ++b)
@@ -406,7 +439,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             for (int a = 0; a < NA; ++a)
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
 }
 
@@ -416,21 +449,22 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
 // restricted to that c; the chunks of a quartet add up to the full update.
 template <int NA, int NB, int NC, int ND, class R>
 __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int fb, int fc, int fd,
-                                             const R* __restrict__ D, double* J, double* K, int n) {
+                                             const R* __restrict__ D, double* J, double* K, double* Jlo,
+                                       double* Klo, int n) {
     const int c = fc + ci;
 #pragma unroll 1
     for (int ab = 0; ab < NA * NB; ++ab) {  // J'_ab
         const int a = ab / NB, b = ab % NB;
         R v = 0;
         for (int d = 0; d < ND; ++d) v = fma(acc[ab * ND + d], __ldg(D + (size_t)c * n + fd + d), v);
-        atomicAdd(J + (size_t)(fa + a) * n + fb + b, 2.0 * (double)v);
+        jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
     }
 #pragma unroll 1
     for (int d = 0; d < ND; ++d) {  // J'_cd
         R v = 0;
         for (int ab = 0; ab < NA * NB; ++ab)
             v = fma(acc[ab * ND + d], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
-        atomicAdd(J + (size_t)c * n + fd + d, 2.0 * (double)v);
+        jk_add<R>(J, Jlo, (size_t)c * n + fd + d, (double)(v + v));
     }
 #pragma unroll 1
     for (int a = 0; a < NA; ++a) {
@@ -438,11 +472,11 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
         for (int b = 0; b < NB; ++b)
             for (int d = 0; d < ND; ++d)
                 vac = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
-        atomicAdd(K + (size_t)(fa + a) * n + c, (double)vac);
+        jk_add<R>(K, Klo, (size_t)(fa + a) * n + c, (double)vac);
         for (int d = 0; d < ND; ++d) {  // K'_ad
             R v = 0;
             for (int b = 0; b < NB; ++b) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + c), v);
-            atomicAdd(K + (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
     }
 #pragma unroll 1
@@ -451,11 +485,11 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
         for (int a = 0; a < NA; ++a)
             for (int d = 0; d < ND; ++d)
                 vbc = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), vbc);
-        atomicAdd(K + (size_t)(fb + b) * n + c, (double)vbc);
+        jk_add<R>(K, Klo, (size_t)(fb + b) * n + c, (double)vbc);
         for (int d = 0; d < ND; ++d) {  // K'_bd
             R v = 0;
             for (int a = 0; a < NA; ++a) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + c), v);
-            atomicAdd(K + (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
     }
 }

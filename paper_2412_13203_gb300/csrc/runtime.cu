@@ -164,8 +164,15 @@ struct jk_pairs_s {
     DevBuf pair_sh;                                 // int2 per pair: shells a, b (caller's order)
     DevBuf bf_shell;                                // int per basis function: its shell
     DevBuf Dsh;                                     // float [nshell^2]: max |D| per shell block (mixed)
+    DevBuf Jlo, Klo;                                // FP64 builds: remainders of the compensated J'/K' sums
+    int part_n = 0;                                 // row partition cached for part_n parts (partial builds)
+    std::vector<std::vector<int>> part_rows;        // per class: part_n + 1 row bounds
+    std::vector<std::vector<long long>> part_items; // per class: work-item prefix (istart) at those bounds
+    std::vector<std::vector<double>> part_cost;     // per class: algorithmic cost of every part, then the
+                                                    // largest single-row cost of the class
     DevBuf list64, listdem;                         // mixed: FP64 and demoted (FP32) ket lists
     std::vector<long long> list_off64, list_offd;   // per class: first entry in list64 / listdem
+    std::vector<int> last_r0, last_r1;              // per class: rows of the last mixed build (partial builds)
     DevBuf pair_lab;                                // int2 per pair: la, lb
     DevBuf xyz;                                     // atoms
     std::vector<int> cls_start;                     // [ncls + 1] pair ranges per class
@@ -564,6 +571,19 @@ __global__ void k_rows_primq(const long long* cnt, const int* rbra, const int* r
     atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
 }
 
+// Algorithmic cost of every row: the generator's operation count of its
+// primitive quartets (fq each) and of its (quartet x bra primitive pair)
+// units (fb each); the weight of the row partition of partial builds.
+__global__ void k_row_cost(const long long* start, const int* rbra, const int* rket0, int nrows, const int4* info,
+                           const long long* npre, long long fq, long long fb, double* cost) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long c = start[r + 1] - start[r];
+    const long long kab = info[rbra[r]].z;
+    const long long kp = c > 0 ? npre[rket0[r] + c] - npre[rket0[r]] : 0;
+    cost[r] = (double)(fq * kp * kab + fb * c * kab);
+}
+
 __global__ void k_np_of(const int4* info, long long n, long long* np) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) np[k] = info[k].z;
@@ -617,15 +637,22 @@ __global__ void k_absmax(const double* x, long long n, unsigned long long* out, 
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// max |x - x^T| (bits of a non-negative double); a NaN or infinite element
+// makes it NaN (sticky: NaN - anything is NaN, and the NaN bit pattern is
+// above every finite one for the integer maximum).
 __global__ void k_asym(const double* x, int n, unsigned long long* out) {
     double m = 0.0;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * n;
          t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t / n), j = (int)(t % n);
-        m = fmax(m, fabs(x[(size_t)i * n + j] - x[(size_t)j * n + i]));
+        const double d = fabs(x[(size_t)i * n + j] - x[(size_t)j * n + i]);
+        if (isnan(d) || d > m) m = d;
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    for (int o = 16; o > 0; o >>= 1) {
+        const double d = __shfl_xor_sync(0xffffffffu, m, o);
+        if (isnan(d) || d > m) m = d;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(fabs(m)));
 }
 
 // J = J' + J'^T in place (one thread per unordered index pair).
@@ -638,6 +665,22 @@ __global__ void k_symmetrize(double* X, int n) {
     const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
     if (i == j) { X[a] *= 2.0; return; }
     const double v = X[a] + X[b];
+    X[a] = v;
+    X[b] = v;
+}
+
+// J = J' + J'^T in place for a compensated build: J' is X + lo (the exact
+// multiples and the remainders of jk_add); the multiples of both triangles are
+// added first (exactly, for sums below 2^21), then the remainders.
+__global__ void k_symmetrize_lo(double* X, const double* lo, int n) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)n * (n + 1) / 2;
+    if (t >= tot) return;
+    int i, j;
+    decode_pair(t, i, j);
+    const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
+    if (i == j) { X[a] = 2.0 * X[a] + 2.0 * lo[a]; return; }
+    const double v = (X[a] + X[b]) + (lo[a] + lo[b]);
     X[a] = v;
     X[b] = v;
 }
@@ -1091,20 +1134,28 @@ int grid_for(long long total, int block, int qpt, int nsm) {
     return (int)g;
 }
 
+// One class kernel over the rows [r0, r0 + nrows) of a class (nrows < 0: to the
+// end of the class); start / ket0 / kofs are the class's per-row arrays of this
+// launch (indexed by row, offset here), klist its explicit ket list.  Jlo/Klo:
+// compensated accumulation (FP64 builds) or nullptr.
 int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
                  long long total_hint, const double* D, double* J, double* K, cudaStream_t st,
-                 const gb::BatchMol* mols = nullptr, const int* row_mol = nullptr, int nrows_override = -1,
-                 const long long* kofs = nullptr, const int* klist = nullptr) {
+                 int nrows = -1, const long long* kofs = nullptr, const int* klist = nullptr, int r0 = 0,
+                 double* Jlo = nullptr, double* Klo = nullptr) {
     if (total_hint <= 0) return 0;
+    const int nr = nrows >= 0 ? nrows : cr.nrows - r0;
+    if (nr <= 0) return 0;
     gb::JKArgs a;
     std::memset(&a, 0, sizeof(a));
     a.pairs = view_of(h);
-    a.rows.nrows = nrows_override >= 0 ? nrows_override : cr.nrows;
-    a.rows.start = start;
-    a.rows.bra = cr.bra.as<int>();
-    a.rows.ket0 = ket0;
-    a.rows.kofs = kofs;
+    a.rows.nrows = nr;
+    a.rows.start = start + r0;
+    a.rows.bra = cr.bra.as<int>() + r0;
+    a.rows.ket0 = ket0 ? ket0 + r0 : nullptr;
+    a.rows.kofs = kofs ? kofs + r0 : nullptr;
     a.rows.klist = klist;
+    a.Jlo = Jlo;
+    a.Klo = Klo;
     a.boys = g_boys[h->device].tab.as<double>();
     a.boysf = g_boys[h->device].tabf.as<float>();
     a.tsmall = (float)g_opt.tsmall;
@@ -1113,8 +1164,6 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.J = J;
     a.K = K;
     a.nbf = h->nbf;
-    a.mols = mols;
-    a.row_mol = row_mol;
     const TuneCfg& tc = cr.tune[prec];
     const int grid = grid_for(total_hint * gb_class_threads(cr.bra_cls, cr.ket_cls, prec), tc.block, tc.qpt, h->nsm);
     ProfRec* pr = nullptr;
@@ -1136,10 +1185,13 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     return 0;
 }
 
-// Mixed split of one class, first phase (counts): per-row quartet and item
-// counts of the FP64 list, the demoted list and the FP32 suffix; the quartet
-// totals are added into split_tot[0..1] (FP32 incl. demoted, FP64).
-int split_count(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* split_tot, cudaStream_t st) {
+// Mixed split of the rows [r0, r1) of one class, first phase (counts): per-row
+// quartet and item counts of the FP64 list, the demoted list and the FP32
+// suffix; the quartet totals are added into split_tot[0..1] (FP32 incl.
+// demoted, FP64).  The per-row arrays are sized for the whole class and
+// written at the rows' own indices (with a zero after row r1 - 1).
+int split_count(jk_pairs_s* h, ClassRows& cr, int r0, int r1, const double* dmax, long long* split_tot,
+                cudaStream_t st) {
     int rc;
     const long long n1 = cr.nrows + 1;
     for (DevBuf* b : {&cr.c64, &cr.c32, &cr.cdem, &cr.w64, &cr.w32, &cr.wdem, &cr.s64, &cr.s32, &cr.sdem, &cr.l64,
@@ -1147,39 +1199,122 @@ int split_count(jk_pairs_s* h, ClassRows& cr, const double* dmax, long long* spl
         if ((rc = b->alloc(sizeof(long long) * n1))) return rc;
     if ((rc = cr.k32.alloc(sizeof(int) * cr.nrows))) return rc;
     if ((rc = cr.scr.alloc(sizeof(long long) * (scan_scratch_len(n1) + 1)))) return rc;
-    k_rows_split<<<nblk(cr.nrows, 256), 256, 0, st>>>(
-        cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(), cr.nrows, h->A.as<double4>(), dmax, g_opt.tau,
-        g_opt.eps, h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell, gb_class_split(cr.bra_cls, cr.ket_cls),
-        cr.c64.as<long long>(), cr.cdem.as<long long>(), cr.c32.as<long long>(), cr.k32.as<int>(), cr.w64.as<long long>(),
-        cr.wdem.as<long long>(), cr.w32.as<long long>(), reinterpret_cast<unsigned long long*>(split_tot));
+    const int nr = r1 - r0;
+    k_rows_split<<<nblk(nr, 256), 256, 0, st>>>(
+        cr.start.as<long long>() + r0, cr.bra.as<int>() + r0, cr.ket0.as<int>() + r0, nr, h->A.as<double4>(), dmax,
+        g_opt.tau, g_opt.eps, h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell,
+        gb_class_split(cr.bra_cls, cr.ket_cls), cr.c64.as<long long>() + r0, cr.cdem.as<long long>() + r0,
+        cr.c32.as<long long>() + r0, cr.k32.as<int>() + r0, cr.w64.as<long long>() + r0,
+        cr.wdem.as<long long>() + r0, cr.w32.as<long long>() + r0, reinterpret_cast<unsigned long long*>(split_tot));
     CKL();
     for (DevBuf* b : {&cr.c64, &cr.c32, &cr.cdem, &cr.w64, &cr.w32, &cr.wdem})
-        CK(cudaMemsetAsync(b->as<long long>() + cr.nrows, 0, 8, st));
+        CK(cudaMemsetAsync(b->as<long long>() + r1, 0, 8, st));
     h->launches += 1;
     return 0;
 }
 
-// Second phase: item prefixes (s64, sdem, s32; totals into split_tot[2..4]),
-// list offsets (l64, ldem; totals into split_tot[5..6]) and the list fill.
-int split_fill(jk_pairs_s* h, ClassRows& cr, long long* split_tot, int* list64, int* listdem, cudaStream_t st) {
+// Second phase over the same rows: item prefixes (s64, sdem, s32; totals into
+// split_tot[2..4]), list offsets (l64, ldem; totals into split_tot[5..6]) and
+// the list fill.  The prefixes start at 0 at row r0.
+int split_fill(jk_pairs_s* h, ClassRows& cr, int r0, int r1, long long* split_tot, int* list64, int* listdem,
+               cudaStream_t st) {
     int rc;
-    const long long n1 = cr.nrows + 1;
+    const long long n1 = r1 - r0 + 1;
     long long* scr = cr.scr.as<long long>();
-    if ((rc = scan_into(cr.w32.as<long long>(), cr.s32.as<long long>(), n1, split_tot + 2, scr, st))) return rc;
-    if ((rc = scan_into(cr.w64.as<long long>(), cr.s64.as<long long>(), n1, split_tot + 3, scr, st))) return rc;
-    if ((rc = scan_into(cr.wdem.as<long long>(), cr.sdem.as<long long>(), n1, split_tot + 4, scr, st))) return rc;
-    if ((rc = scan_into(cr.c64.as<long long>(), cr.l64.as<long long>(), n1, split_tot + 5, scr, st))) return rc;
-    if ((rc = scan_into(cr.cdem.as<long long>(), cr.ldem.as<long long>(), n1, split_tot + 6, scr, st))) return rc;
-    k_rows_fill<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.bra.as<int>(), cr.ket0.as<int>(), cr.k32.as<int>(), cr.nrows,
-                                                     h->A.as<double4>(), g_opt.tau, g_opt.eps, h->pair_sh.as<int2>(),
-                                                     h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>(),
-                                                     cr.ldem.as<long long>(), list64, listdem);
+    if ((rc = scan_into(cr.w32.as<long long>() + r0, cr.s32.as<long long>() + r0, n1, split_tot + 2, scr, st))) return rc;
+    if ((rc = scan_into(cr.w64.as<long long>() + r0, cr.s64.as<long long>() + r0, n1, split_tot + 3, scr, st))) return rc;
+    if ((rc = scan_into(cr.wdem.as<long long>() + r0, cr.sdem.as<long long>() + r0, n1, split_tot + 4, scr, st)))
+        return rc;
+    if ((rc = scan_into(cr.c64.as<long long>() + r0, cr.l64.as<long long>() + r0, n1, split_tot + 5, scr, st))) return rc;
+    if ((rc = scan_into(cr.cdem.as<long long>() + r0, cr.ldem.as<long long>() + r0, n1, split_tot + 6, scr, st)))
+        return rc;
+    const int nr = r1 - r0;
+    k_rows_fill<<<nblk(nr, 256), 256, 0, st>>>(cr.bra.as<int>() + r0, cr.ket0.as<int>() + r0, cr.k32.as<int>() + r0, nr,
+                                               h->A.as<double4>(), g_opt.tau, g_opt.eps, h->pair_sh.as<int2>(),
+                                               h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>() + r0,
+                                               cr.ldem.as<long long>() + r0, list64, listdem);
     CKL();
     h->launches += 1 + 5 * scan_launches(n1);
     return 0;
 }
 
-int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_precision prec, cudaStream_t st) {
+// Host: cost-balanced split of n consecutive units into nparts contiguous
+// ranges (bounds[0] = 0 <= ... <= bounds[nparts] = n): bounds[p] is the first
+// unit at which the running cost reaches p/nparts of the total, so every part
+// costs total/nparts within the cost of one unit.  Zero total: equal counts.
+int partition_costs(long long n, const double* cost, int nparts, long long* bounds) {
+    if (n < 0 || nparts < 1 || (n > 0 && !cost) || !bounds) return fail(JK_ERR_INVALID, "partition arguments");
+    std::vector<double> pre((size_t)n + 1, 0.0);
+    for (long long i = 0; i < n; ++i) {
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i])) return fail(JK_ERR_INVALID, "partition cost negative or not finite");
+        pre[i + 1] = pre[i] + cost[i];
+    }
+    const double T = pre[n];
+    bounds[0] = 0;
+    bounds[nparts] = n;
+    for (int p = 1; p < nparts; ++p) {
+        if (T > 0.0) {
+            const double t = T * ((double)p / nparts);
+            bounds[p] = (long long)(std::lower_bound(pre.begin(), pre.end(), t) - pre.begin());
+        } else {
+            bounds[p] = (long long)((double)n * p / nparts);
+        }
+        bounds[p] = std::max(bounds[p], bounds[p - 1]);
+    }
+    return 0;
+}
+
+// Row partition of every class for `nparts` parts (cached on the handle): the
+// rows of each class are cut by their algorithmic cost, so that every part
+// holds the same share of every class.  One synchronisation per new nparts.
+int ensure_partition(jk_pairs_s* h, int nparts, cudaStream_t st) {
+    if (h->part_n == nparts) return 0;
+    h->part_n = 0;
+    h->part_rows.assign(h->rows.size(), {});
+    h->part_items.assign(h->rows.size(), {});
+    h->part_cost.assign(h->rows.size(), std::vector<double>(nparts + 1, 0.0));
+    DevBuf d_cost;
+    int rc;
+    for (size_t k = 0; k < h->rows.size(); ++k) {
+        const ClassRows& cr = h->rows[k];
+        std::vector<int>& rb = h->part_rows[k];
+        std::vector<long long>& ib = h->part_items[k];
+        rb.assign(nparts + 1, 0);
+        ib.assign(nparts + 1, 0);
+        if (cr.nrows <= 0 || cr.total <= 0) {
+            for (int p = 0; p <= nparts; ++p) rb[p] = p == nparts ? cr.nrows : 0;
+            continue;
+        }
+        int fq = 0, fb = 0;
+        gb_class_flops(cr.bra_cls, cr.ket_cls, &fq, &fb);
+        if ((rc = d_cost.alloc(sizeof(double) * cr.nrows))) return rc;
+        k_row_cost<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                        cr.nrows, h->info.as<int4>(), h->npre.as<long long>(), fq, fb,
+                                                        d_cost.as<double>());
+        CKL();
+        std::vector<double> cost(cr.nrows);
+        std::vector<long long> istart(cr.nrows + 1);
+        CK(cudaMemcpyAsync(cost.data(), d_cost.p, sizeof(double) * cr.nrows, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(istart.data(), cr.istart.p, sizeof(long long) * (cr.nrows + 1), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<long long> b(nparts + 1);
+        if ((rc = partition_costs(cr.nrows, cost.data(), nparts, b.data()))) return rc;
+        for (int p = 0; p <= nparts; ++p) {
+            rb[p] = (int)b[p];
+            ib[p] = istart[b[p]];
+        }
+        std::vector<double>& pc = h->part_cost[k];
+        for (int p = 0; p < nparts; ++p)
+            for (long long r = b[p]; r < b[p + 1]; ++r) pc[p] += cost[r];
+        pc[nparts] = *std::max_element(cost.begin(), cost.end());
+    }
+    h->part_n = nparts;
+    return 0;
+}
+
+// J and K of the rows of part `part` of `nparts` (nparts = 1: the whole build).
+int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_precision prec, cudaStream_t st,
+                  int part = 0, int nparts = 1) {
     const int n = h->nbf;
     int rc;
     if ((rc = h->scratch.alloc(64))) return rc;
@@ -1192,10 +1327,19 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         CK(cudaStreamSynchronize(st));
         double m;
         std::memcpy(&m, &b, 8);
-        if (m > 0.0) return fail(JK_ERR_NOT_SYMMETRIC, "D is not symmetric (max |D - D^T| = " + std::to_string(m) + ")");
+        if (!(m == 0.0)) {
+            if (std::isnan(m)) return fail(JK_ERR_INVALID, "D holds a non-finite element");
+            return fail(JK_ERR_NOT_SYMMETRIC, "D is not symmetric (max |D - D^T| = " + std::to_string(m) + ")");
+        }
     }
-    CK(cudaMemsetAsync(J, 0, sizeof(double) * n * n, st));
-    CK(cudaMemsetAsync(K, 0, sizeof(double) * n * n, st));
+    if (nparts > 1 && (rc = ensure_partition(h, nparts, st))) return rc;
+    auto range = [&](size_t k, int& r0, int& r1) {
+        if (nparts > 1) { r0 = h->part_rows[k][part]; r1 = h->part_rows[k][part + 1]; }
+        else { r0 = 0; r1 = h->rows[k].nrows; }
+    };
+    const size_t n2 = (size_t)n * n;
+    CK(cudaMemsetAsync(J, 0, sizeof(double) * n2, st));
+    CK(cudaMemsetAsync(K, 0, sizeof(double) * n2, st));
     for (auto& r : h->prof) {
         if (r.e0) cudaEventDestroy(r.e0);
         if (r.e1) cudaEventDestroy(r.e1);
@@ -1203,18 +1347,32 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
     h->prof.clear();
     h->launches = 0;
     h->last_prec = prec;
+    double* Jlo = nullptr;
+    double* Klo = nullptr;
     if (prec == JK_FP64) {
-        for (const ClassRows& cr : h->rows)
-            if ((rc = launch_class(h, cr, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), cr.itotal, D, J, K, st)))
+        if ((rc = h->Jlo.alloc(sizeof(double) * n2))) return rc;
+        if ((rc = h->Klo.alloc(sizeof(double) * n2))) return rc;
+        Jlo = h->Jlo.as<double>();
+        Klo = h->Klo.as<double>();
+        CK(cudaMemsetAsync(Jlo, 0, sizeof(double) * n2, st));
+        CK(cudaMemsetAsync(Klo, 0, sizeof(double) * n2, st));
+        for (size_t k = 0; k < h->rows.size(); ++k) {
+            const ClassRows& cr = h->rows[k];
+            int r0, r1;
+            range(k, r0, r1);
+            const long long items = nparts > 1 ? h->part_items[k][part + 1] - h->part_items[k][part] : cr.itotal;
+            if ((rc = launch_class(h, cr, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), items, D, J, K, st, r1 - r0,
+                                   nullptr, nullptr, r0, Jlo, Klo)))
                 return rc;
+        }
     } else {
         const int ncr = (int)h->rows.size();
         const size_t nst = (size_t)kSplitSlots * std::max(1, ncr);
         if ((rc = h->split_tot.alloc(sizeof(long long) * nst))) return rc;
         CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * nst, st));
-        if ((rc = h->Df.alloc(sizeof(float) * (size_t)n * n))) return rc;
+        if ((rc = h->Df.alloc(sizeof(float) * n2))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
-        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>(), h->Df.as<float>());
+        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n2, h->scratch.as<unsigned long long>(), h->Df.as<float>());
         CKL();
         // max |D| per shell block, for the density-weighted FP64 selection
         const size_t ns2 = (size_t)h->nshell * h->nshell;
@@ -1224,10 +1382,13 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         CKL();
         h->launches += 2;
         const double* dmax = reinterpret_cast<const double*>(h->scratch.p);
-        for (int k = 0; k < ncr; ++k)
-            if (h->rows[k].total > 0 &&
-                (rc = split_count(h, h->rows[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st)))
+        std::vector<int> R0(ncr), R1(ncr);
+        for (int k = 0; k < ncr; ++k) {
+            range(k, R0[k], R1[k]);
+            if (h->rows[k].total > 0 && R1[k] > R0[k] &&
+                (rc = split_count(h, h->rows[k], R0[k], R1[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st)))
                 return rc;
+        }
         // list sizes: one host synchronisation per mixed build
         std::vector<long long> cnt(nst);
         CK(cudaMemcpyAsync(cnt.data(), h->split_tot.p, sizeof(long long) * nst, cudaMemcpyDeviceToHost, st));
@@ -1241,25 +1402,34 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         if ((rc = h->listdem.alloc(sizeof(int) * std::max(1LL, offd[ncr])))) return rc;
         for (int k = 0; k < ncr; ++k) {
             ClassRows& cr = h->rows[k];
-            if (cr.total <= 0) continue;
+            const int r0 = R0[k], r1 = R1[k];
+            if (cr.total <= 0 || r1 <= r0) continue;
             int* l64 = h->list64.as<int>() + off64[k];
             int* ldm = h->listdem.as<int>() + offd[k];
-            if ((rc = split_fill(h, cr, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st))) return rc;
-            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, nullptr, nullptr,
-                                   -1, cr.l64.as<long long>(), l64)))
+            if ((rc = split_fill(h, cr, r0, r1, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st))) return rc;
+            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
+                                   cr.l64.as<long long>(), l64, r0)))
                 return rc;
-            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st)))
+            if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st, r1 - r0,
+                                   nullptr, nullptr, r0)))
                 return rc;
-            if ((rc = launch_class(h, cr, 1, cr.sdem.as<long long>(), nullptr, cr.itotal, D, J, K, st, nullptr, nullptr,
-                                   -1, cr.ldem.as<long long>(), ldm)))
+            if ((rc = launch_class(h, cr, 1, cr.sdem.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
+                                   cr.ldem.as<long long>(), ldm, r0)))
                 return rc;
         }
         h->list_off64 = off64;
         h->list_offd = offd;
+        h->last_r0 = R0;
+        h->last_r1 = R1;
     }
     const long long tri = (long long)n * (n + 1) / 2;
-    k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
-    k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(K, n);
+    if (Jlo) {
+        k_symmetrize_lo<<<nblk(tri, 256), 256, 0, st>>>(J, Jlo, n);
+        k_symmetrize_lo<<<nblk(tri, 256), 256, 0, st>>>(K, Klo, n);
+    } else {
+        k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(J, n);
+        k_symmetrize<<<nblk(tri, 256), 256, 0, st>>>(K, n);
+    }
     CKL();
     h->launches += 2;
     return 0;
@@ -1332,6 +1502,7 @@ __global__ void k_zero_batched(const gb::BatchMol* bm) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
         m.J[i] = 0.0;
         m.K[i] = 0.0;
+        if (m.Jlo) { m.Jlo[i] = 0.0; m.Klo[i] = 0.0; }
     }
 }
 
@@ -1343,6 +1514,13 @@ __global__ void k_sym_batched(const gb::BatchMol* bm) {
         int i, j;
         decode_pair(t, i, j);
         const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
+        if (m.Jlo) {  // compensated FP64 build: fold the remainders in (as k_symmetrize_lo)
+            if (i == j) { m.J[a] = 2.0 * m.J[a] + 2.0 * m.Jlo[a]; m.K[a] = 2.0 * m.K[a] + 2.0 * m.Klo[a]; continue; }
+            const double vj = (m.J[a] + m.J[b]) + (m.Jlo[a] + m.Jlo[b]);
+            const double vk = (m.K[a] + m.K[b]) + (m.Klo[a] + m.Klo[b]);
+            m.J[a] = vj; m.J[b] = vj; m.K[a] = vk; m.K[b] = vk;
+            continue;
+        }
         if (i == j) { m.J[a] *= 2.0; m.K[a] *= 2.0; continue; }
         const double vj = m.J[a] + m.J[b], vk = m.K[a] + m.K[b];
         m.J[a] = vj; m.J[b] = vj; m.K[a] = vk; m.K[b] = vk;
@@ -1394,6 +1572,13 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
         host[m].nshell = h->nshell;
         host[m].J = P.J[m];
         host[m].K = P.K[m];
+        if (P.prec == JK_FP64) {  // compensated accumulation, as jk_build
+            const size_t n2 = (size_t)h->nbf * h->nbf;
+            if ((rc = h->Jlo.alloc(sizeof(double) * n2))) return rc;
+            if ((rc = h->Klo.alloc(sizeof(double) * n2))) return rc;
+            host[m].Jlo = h->Jlo.as<double>();
+            host[m].Klo = h->Klo.as<double>();
+        }
         host[m].nbf = h->nbf;
         P.max_n = std::max(P.max_n, h->nbf);
         P.nquartets += h->nquartets;
@@ -1714,7 +1899,7 @@ int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec
         for (int rep = 0; rep < 2; ++rep) {  // first run warms caches and clocks
             CK(cudaEventRecord(e0, st));
             if ((rc = launch_class(h, *it.cr, prec, it.cr->istart.as<long long>(), it.cr->ket0.as<int>(), it.total, D,
-                                   J, K, st, nullptr, nullptr, it.nrows)))
+                                   J, K, st, it.nrows)))
                 return rc;
             CK(cudaEventRecord(e1, st));
         }
@@ -1902,9 +2087,15 @@ int jk_energy_noalloc(int nbf, const double* D, const double* J, const double* K
 }
 
 int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* cuda_stream) {
+    return jk_grad_part(h, 0, 1, D, dEdR, prec, cuda_stream);
+}
+
+int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR, jk_precision prec,
+                 void* cuda_stream) {
     g_err.clear();
     if (!h || !D || !dEdR) return fail(JK_ERR_INVALID, "null argument");
     if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(JK_ERR_INVALID, "part outside [0, nparts)");
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
@@ -1915,19 +2106,28 @@ int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* 
             if (cr.total > 0 && cr.bra_cls >= gcls)
                 return fail(JK_ERR_UNSUPPORTED, "gradients are compiled for shells up to l = " + std::to_string(gl));
     }
+    int rc;
+    if (nparts > 1 && (rc = ensure_partition(h, nparts, st))) return rc;
     // both precisions run the FP64 derivative kernels
     CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * h->natom, st));
     h->launches = 0;
-    for (const ClassRows& cr : h->rows) {
+    for (size_t k = 0; k < h->rows.size(); ++k) {
+        const ClassRows& cr = h->rows[k];
         if (cr.total <= 0) continue;
+        const int r0 = nparts > 1 ? h->part_rows[k][part] : 0;
+        const int r1 = nparts > 1 ? h->part_rows[k][part + 1] : cr.nrows;
+        const long long i0 = nparts > 1 ? h->part_items[k][part] : 0;
+        const long long i1 = nparts > 1 ? h->part_items[k][part + 1] : cr.itotal;
+        if (r1 <= r0 || i1 <= i0) continue;
         gb::GradArgs a;
         std::memset(&a, 0, sizeof(a));
         a.pairs = view_of(h);
-        a.rows.nrows = cr.nrows;
-        a.rows.start = cr.istart.as<long long>();  // work items, as the J/K kernels
-        a.rows.bra = cr.bra.as<int>();
-        a.rows.ket0 = cr.ket0.as<int>();
-        a.total = cr.itotal;
+        a.rows.nrows = r1 - r0;
+        a.rows.start = cr.istart.as<long long>() + r0;  // work items, as the J/K kernels
+        a.rows.bra = cr.bra.as<int>() + r0;
+        a.rows.ket0 = cr.ket0.as<int>() + r0;
+        a.base = i0;
+        a.total = i1 - i0;
         a.boys = g_boys[h->device].tab.as<double>();
         a.D = D;
         a.nbf = h->nbf;
@@ -1937,6 +2137,51 @@ int jk_grad(jk_pairs h, const double* D, double* dEdR, jk_precision prec, void* 
         if (e) return fail(JK_ERR_CUDA, std::string("gradient kernel launch: ") + cudaGetErrorString((cudaError_t)e));
         h->launches += 1;
     }
+    return JK_OK;
+}
+
+int jk_build_part(jk_pairs h, int part, int nparts, const double* D, double* J, double* K, jk_precision prec,
+                  void* cuda_stream) {
+    g_err.clear();
+    if (!h || !D || !J || !K) return fail(JK_ERR_INVALID, "null argument");
+    if (prec != JK_FP64 && prec != JK_MIXED) return fail(JK_ERR_INVALID, "precision");
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(JK_ERR_INVALID, "part outside [0, nparts)");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    return jk_build_impl(h, D, J, K, prec, static_cast<cudaStream_t>(cuda_stream), part, nparts);
+}
+
+int jk_partition(int64_t n, const double* cost, int nparts, int64_t* bounds) {
+    g_err.clear();
+    static_assert(sizeof(int64_t) == sizeof(long long), "int64_t is long long");
+    return partition_costs((long long)n, cost, nparts, reinterpret_cast<long long*>(bounds));
+}
+
+int jk_part_rows(jk_pairs h, int nparts, int max_rows, int64_t* rows, int* nrows) {
+    g_err.clear();
+    if (!h || !nrows || nparts < 1 || (max_rows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(JK_ERR_INVALID, "handle belongs to another device");
+    int rc;
+    if ((rc = ensure_partition(h, nparts, nullptr))) return rc;
+    int k = 0;
+    for (size_t ci = 0; ci < h->rows.size(); ++ci) {
+        const ClassRows& cr = h->rows[ci];
+        if (cr.total <= 0) continue;
+        for (int p = 0; p < nparts; ++p, ++k) {
+            if (k >= max_rows) continue;
+            int64_t* r = rows + 8 * k;
+            r[0] = cr.bra_cls; r[1] = cr.ket_cls; r[2] = p;
+            r[3] = h->part_rows[ci][p];
+            r[4] = h->part_rows[ci][p + 1];
+            r[5] = h->part_items[ci][p + 1] - h->part_items[ci][p];
+            r[6] = (int64_t)h->part_cost[ci][p];
+            r[7] = (int64_t)h->part_cost[ci][nparts];
+        }
+    }
+    *nrows = k;
     return JK_OK;
 }
 
@@ -2108,18 +2353,22 @@ int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
         if (cr.total <= 0) continue;
         if (k < max_rows) {
             // FP32: the contiguous suffix (c32 from k32) plus the demoted list;
-            // FP64: the FP64 list
+            // FP64: the FP64 list (over the rows the build ran: all, or a part's)
             CK(cudaMemset(acc.p, 0, 4 * sizeof(unsigned long long)));
-            k_rows_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c32.as<long long>(), cr.bra.as<int>(), cr.k32.as<int>(),
-                                                       cr.nrows, h->info.as<int4>(), h->npre.as<long long>(),
-                                                       acc.as<unsigned long long>());
-            k_list_primq<<<nblk(cr.nrows, 256), 256>>>(cr.cdem.as<long long>(), cr.ldem.as<long long>(),
-                                                       h->listdem.as<int>() + h->list_offd[ri], cr.bra.as<int>(),
-                                                       cr.nrows, h->info.as<int4>(), acc.as<unsigned long long>());
-            k_list_primq<<<nblk(cr.nrows, 256), 256>>>(cr.c64.as<long long>(), cr.l64.as<long long>(),
-                                                       h->list64.as<int>() + h->list_off64[ri], cr.bra.as<int>(),
-                                                       cr.nrows, h->info.as<int4>(), acc.as<unsigned long long>() + 2);
-            CKL();
+            const int r0 = ri < h->last_r0.size() ? h->last_r0[ri] : 0;
+            const int nr = (ri < h->last_r1.size() ? h->last_r1[ri] : cr.nrows) - r0;
+            if (nr > 0) {
+                k_rows_primq<<<nblk(nr, 256), 256>>>(cr.c32.as<long long>() + r0, cr.bra.as<int>() + r0,
+                                                     cr.k32.as<int>() + r0, nr, h->info.as<int4>(),
+                                                     h->npre.as<long long>(), acc.as<unsigned long long>());
+                k_list_primq<<<nblk(nr, 256), 256>>>(cr.cdem.as<long long>() + r0, cr.ldem.as<long long>() + r0,
+                                                     h->listdem.as<int>() + h->list_offd[ri], cr.bra.as<int>() + r0,
+                                                     nr, h->info.as<int4>(), acc.as<unsigned long long>());
+                k_list_primq<<<nblk(nr, 256), 256>>>(cr.c64.as<long long>() + r0, cr.l64.as<long long>() + r0,
+                                                     h->list64.as<int>() + h->list_off64[ri], cr.bra.as<int>() + r0,
+                                                     nr, h->info.as<int4>(), acc.as<unsigned long long>() + 2);
+                CKL();
+            }
             unsigned long long v[4];
             long long q2[2];
             CK(cudaMemcpy(v, acc.p, sizeof(v), cudaMemcpyDeviceToHost));

@@ -52,3 +52,5 @@ inline int __float2int_rn(float x) { return (int)std::nearbyint(x); }
 inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }
 inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
 inline unsigned int __float_as_uint(float x) { unsigned int r; std::memcpy(&r, &x, 4); return r; }
+inline double __dadd_rn(double a, double b) { return a + b; }
+inline double __dsub_rn(double a, double b) { return a - b; }

@@ -1,8 +1,18 @@
 """Parity at the benchmark's full size (32-atom lattice, 480 Cartesian basis
-functions, Schwarz 1e-10) in the configuration bench.py times: one sampled
-row of J and K (an s shell, all 480 columns) from the oracle, which sums the
-definition over every (not only unique) screened shell quartet, against the
-GPU FP64 and mixed builds."""
+functions, Schwarz 1e-10) in the configuration bench.py times: every element
+of J and K and the energy E = tr(DJ)/2 - tr(DK)/4 of the GPU FP64 and mixed
+builds against the oracle's (tests/golden/jk_32atom.npz, written by
+tests/golden/make_jk_32atom.py from the CPU oracle alone: Obara-Saika/HRR over
+every screened unique quartet with compensated sums).
+
+Targets: FP64 build within 1e-10 Eh of the oracle on every J and K element and
+on E; mixed build within 1e-6 Eh.  Quartets whose Schwarz product lies within
+a relative 1e-8 of the threshold could be kept on one side and dropped on
+the other (Q is computed by different algorithms on the two sides); each such
+quartet moves an element by at most 2 thresh max|D|, an allowance counted
+separately (zero flips is the expected count)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +21,8 @@ import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "jk_32atom.npz")
 
 
 @pytest.fixture(scope="module")
@@ -22,34 +34,52 @@ def g():
     return g
 
 
-def test_bench_workload_sampled_row(g):
+def golden():
+    z = np.load(GOLD)
+    n = int(z["nbf"])
+    iu = np.triu_indices(n)
+    J = np.zeros((n, n))
+    K = np.zeros((n, n))
+    J[iu] = z["J_upper"]
+    K[iu] = z["K_upper"]
+    J = J + np.triu(J, 1).T
+    K = K + np.triu(K, 1).T
+    return J, K, float(z["E"]), int(z["kept"]), float(z["thresh"])
+
+
+def boundary_allowance(mol, D, thresh):
+    """2 thresh max|D| per unique quartet whose Schwarz product is within a
+    relative 1e-8 of the threshold (counted from the oracle's Q)."""
+    Q = oracle.schwarz(mol)
+    iu = np.tril_indices(mol.nshell)
+    q = np.sort(Q[iu])
+    lo = np.searchsorted(q, thresh * (1 - 1e-8) / np.maximum(q, 1e-300), side="left")
+    hi = np.searchsorted(q, thresh * (1 + 1e-8) / np.maximum(q, 1e-300), side="right")
+    nflip = int(np.sum(hi - lo))
+    return nflip, 2.0 * thresh * float(np.abs(D).max()) * nflip
+
+
+def test_bench_workload_every_element(g):
     mol, D = molgen.config(1)
     thresh = molgen.CONFIG_THRESH[1]
+    Jo, Ko, Eo, kept, th = golden()
+    assert th == thresh and Jo.shape == D.shape
     pairs = g.ShellPairs(mol, thresh)
+    assert pairs.nquartets == kept
     Dt = torch.from_numpy(D).cuda()
-    J64, K64 = g.jk_build(pairs, Dt, "fp64")
-    J64, K64 = J64.cpu().numpy(), K64.cpu().numpy()
+    nflip, allow = boundary_allowance(mol, D, thresh)
+    J, K = g.jk_build(pairs, Dt, "fp64")
+    E = g.jk_energy(Dt, J, K)
+    J, K = J.cpu().numpy(), K.cpu().numpy()
+    eJ, eK, eE = np.abs(J - Jo).max(), np.abs(K - Ko).max(), abs(E - Eo)
+    print(f"FP64: max|dJ| {eJ:.3e} max|dK| {eK:.3e} |dE| {eE:.3e} (E {Eo:.6f}, flips {nflip})")
+    assert eJ <= 1e-10 + allow and eK <= 1e-10 + allow, (eJ, eK)
+    assert eE <= 1e-10 + allow * np.abs(D).sum(), eE
+    assert np.abs(J - J.T).max() == 0.0 and np.abs(K - K.T).max() == 0.0
     Jm, Km = g.jk_build(pairs, Dt, "mixed")
+    Em = g.jk_energy(Dt, Jm, Km)
     Jm, Km = Jm.cpu().numpy(), Km.cpu().numpy()
-    shell = int(np.where(np.asarray(mol.shell_l) == 0)[0][5])
-    row = int(sum((int(l) + 1) * (int(l) + 2) // 2 for l in mol.shell_l[:shell]))
-    Jr, Kr = oracle.jk_rows(mol, D, [shell], thresh)
-    # quartets whose Schwarz product lies within the last bits of the threshold
-    # may be kept on one side and dropped on the other; each moves an element
-    # by at most thresh * max|D|
-    Q = oracle.schwarz(mol)
-    qa = Q[shell]
-    amb = np.abs(np.outer(qa, Q.ravel()) - thresh) <= 1e-8 * thresh
-    flips = 2 * thresh * np.abs(D).max() * int(amb.sum())
-    # FP64 tolerance 1e-10 relative to the largest element (as in the other FP64
-    # parity tests: an element here sums ~1e6 quartet contributions of size ~1)
-    tolJ = 1e-10 * max(1.0, np.abs(Jr).max()) + flips
-    tolK = 1e-10 * max(1.0, np.abs(Kr).max()) + flips
-    assert np.abs(J64[row] - Jr[0]).max() <= tolJ, np.abs(J64[row] - Jr[0]).max()
-    assert np.abs(K64[row] - Kr[0]).max() <= tolK, np.abs(K64[row] - Kr[0]).max()
-    assert np.abs(Jm[row] - Jr[0]).max() <= 1e-6
-    assert np.abs(Km[row] - Kr[0]).max() <= 1e-6
-    # and the whole matrices: symmetric, mixed within the target of FP64
-    assert np.abs(J64 - J64.T).max() == 0.0 and np.abs(K64 - K64.T).max() == 0.0
-    assert np.abs(Jm - J64).max() <= 1e-6 and np.abs(Km - K64).max() <= 1e-6
+    mJ, mK, mE = np.abs(Jm - Jo).max(), np.abs(Km - Ko).max(), abs(Em - Eo)
+    print(f"mixed: max|dJ| {mJ:.3e} max|dK| {mK:.3e} |dE| {mE:.3e}")
+    assert mJ <= 1e-6 and mK <= 1e-6 and mE <= 1e-6, (mJ, mK, mE)
     pairs.free()
