@@ -225,7 +225,7 @@ typedef enum {
                                   * an infinity */
     JK_OPT_GRAPH = 3,            /* nonzero: jk_build_batched captures and replays a CUDA graph */
     JK_OPT_PROFILE = 4,          /* nonzero: jk_build records CUDA events around every class launch */
-    JK_OPT_DENSITY_SCREEN = 5    /* mixed builds (single and batched): skip a shell quartet whose bound
+    JK_OPT_DENSITY_SCREEN = 5,   /* mixed builds (single and batched): skip a shell quartet whose bound
                                   * Q_ab Q_cd max|D| is below this value, with max|D| over the whole
                                   * matrix, and, for the quartets whose global bound reaches tau, over
                                   * the six D blocks the quartet reads (default 0: nothing is skipped).
@@ -233,6 +233,17 @@ typedef enum {
                                   * difference density makes the bounds small, so many quartets are
                                   * skipped.  Skipped quartets are counted in neither part of
                                   * jk_last_split. */
+    JK_OPT_RPATH = 6,            /* nonzero: the FP32 kernels of (dd|dd), (dd|dp) and (dp|dp) evaluate
+                                  * the Hermite R recursion in the order found by the greedy path
+                                  * search of Algorithm 1 (Sec. 5, Graph Compiler; per kernel the
+                                  * lambda of fewest operations) instead of the fixed t-u-v order
+                                  * (default 0).  Same integrals up to rounding. */
+    JK_OPT_FAIL_ALLOC_AFTER = 7  /* fault injection for callers' error handling: n >= 0 lets n more
+                                  * device allocations of the library succeed, then the next one
+                                  * fails with JK_ERR_NOMEM (as if the device were full) and the
+                                  * count stays at 0 (every later one fails) until the option is
+                                  * set to a negative value (default -1: off).  No device memory
+                                  * is touched by an injected failure. */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);

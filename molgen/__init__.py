@@ -33,7 +33,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "Molecule", "ncart", "lattice_sites", "random_molecule", "density",
+    "Molecule", "ncart", "lattice_sites", "random_molecule", "density", "density_n",
     "config", "config2_batch", "CONFIG_THRESH", "h2_sto3g",
 ]
 
@@ -173,6 +173,16 @@ def density(mol: Molecule, seed: int, decay: float | None = None) -> np.ndarray:
         D = D * np.exp(-decay * r)
     D = 0.5 * (D + D.T)
     return np.ascontiguousarray(D)
+
+
+def density_n(n: int, seed: int) -> np.ndarray:
+    """The same recipe for a basis of n functions given by its size alone
+    (e.g. the pure d/f basis of a molecule): D = C C^T, C ~ N(0, 0.1) of
+    shape n x max(1, n // 2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    C = rng.normal(0.0, 0.1, size=(n, max(1, n // 2)))
+    D = C @ C.T
+    return np.ascontiguousarray(0.5 * (D + D.T))
 
 
 #: Schwarz threshold per configuration (None = no screening).

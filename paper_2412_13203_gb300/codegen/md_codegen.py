@@ -334,7 +334,7 @@ def crange_groups(bra, ket):
 CRANGE_VALUES = 150
 
 
-def gen_quartet_body(bra, ket, real, mode_flat, cds=None):
+def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     """Device code computing acc[NAB*NCD] for one shell quartet (flat mode with
     `cds`: only those ket component pairs, acc[NAB*len(cds)]).
 
@@ -431,8 +431,9 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None):
     else:
         E(f"gb::boys_f64<{L}>(T, F, boys);")
     flops_setup = 16 + (kBoysCost(L))
-    if mode_flat and R_PATH_LAMBDA is not None:
-        R = gen_R_path(em, L, r_targets(bra, ket, cds), f32, R_PATH_LAMBDA)
+    lam = rpath if rpath is not None else R_PATH_LAMBDA
+    if mode_flat and lam is not None:
+        R = gen_R_path(em, L, r_targets(bra, ket, cds), f32, lam)
     elif f32:
         R = gen_R_scaled(em, L, "F", ("PQsx", "PQsy", "PQsz"), "r2k")
     else:
@@ -785,6 +786,15 @@ def gen_class_kernels(bra, ket):
                 body, st = gen_quartet_body(bra, ket, real, True, cds)
                 variants.append((f"_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, ib.x, "
                                                   f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * len(cds)))
+            if (bra, ket) in RPATH_CLASSES:
+                # the same ranges with the R recursion order of Algorithm 1
+                # (greedy path search, lambda of fewest operations per range)
+                for c0, c1 in crange_groups(bra, ket):
+                    cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
+                    body, _ = gen_quartet_body(bra, ket, real, True, cds, rpath=best_lambda(bra, ket, cds))
+                    variants.append((f"r_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, "
+                                                       f"ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);",
+                                     na * nb * len(cds)))
         else:
             body, st = gen_quartet_body(bra, ket, real, flat)
             variants.append(("", body, f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
@@ -861,15 +871,29 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   }}
 }}
 """)
-        if bra == ket and prec == "f64" and chunk:
+        if bra == ket and prec == "f64":
+            nab = na * nb
+            if chunk:
+                sbody = body  # the chunked FP64 body of this class (one ket component c = ci)
+                diag = (f"  for (int b = 0; b < {nb}; ++b)\n"
+                        f"    dg[ci * {nb} + b] = acc[(ci * {nb} + b) * {nd} + b];")
+            else:
+                sbody = body_f64_for_schwarz(bra, ket)
+                diag = f"  for (int d = 0; d < {nab}; ++d) dg[d] = acc[d * {nab} + d];"
             out.append(f"""
 __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArgs sa) {{
-  // one thread per (pair, component a = ci of shell a): the diagonal
-  // elements (ab|ab) with that a; Q is the max over the {nch} threads (sa.Q
-  // zeroed by the caller; non-negative doubles order like their bit patterns)
+  // one thread per (pair, component c = ci of shell a, part ipart of the bra
+  // primitive pairs): the partial diagonal elements (ab|ab)_ii of its bra
+  // primitive pairs go to its own slots of sa.diag (zeroed by the caller);
+  // gb::k_schwarz_finish adds the parts in a fixed order and takes
+  // Q = sqrt(max_i |(ab|ab)_ii|), so Q does not depend on scheduling
+  constexpr int S = gb::kSchwarzSplit;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)sa.count * {nch}) return;
-  const int i = (int)(tid / {nch}), ci = (int)(tid - (long long)i * {nch});
+  if (tid >= (long long)sa.count * {nch} * S) return;
+  const int ipart = (int)(tid % S);
+  const long long pc = tid / S;
+  const int i = (int)(pc / {nch}), ci = (int)(pc - (long long)i * {nch});
+  (void)ci;
   const int bra = sa.first + i, ket = bra;
   const gb::PairsView& pairs = sa.pairs;
   const double* __restrict__ boys = sa.boys;
@@ -877,30 +901,12 @@ __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArg
   const float tsmall = 0.f;
   (void)boysf; (void)tsmall;
   const int4 ib = pairs.info[bra], ik = ib;
-  const int ipart = 0, nsplit = 1;
+  const int nsplit = min(S, ib.z);
+  if (ipart >= nsplit) return;
   const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
-{indent(body)}
-  double m = 0.0;
-  for (int b = 0; b < {nb}; ++b) m = fmax(m, fabs(acc[(ci * {nb} + b) * {nd} + b]));
-  atomicMax(reinterpret_cast<unsigned long long*>(sa.Q + i), (unsigned long long)__double_as_longlong(sqrt(m)));
-}}
-""")
-        elif bra == ket and prec == "f64":
-            out.append(f"""
-__global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArgs sa) {{
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= sa.count) return;
-  const int bra = sa.first + i, ket = bra;
-  const gb::PairsView& pairs = sa.pairs;
-  const double* __restrict__ boys = sa.boys;
-  const float* __restrict__ boysf = nullptr;
-  const float tsmall = 0.f;
-  (void)boysf; (void)tsmall;
-  const int4 ib = pairs.info[bra], ik = ib;
-  const int ipart = 0, nsplit = 1;
-  const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
-{indent(body_f64_for_schwarz(bra, ket))}
-  sa.Q[i] = gb::schwarz_from_block<{na * nb}>(acc);
+{indent(sbody)}
+  double* dg = sa.diag + ((size_t)i * S + ipart) * {nab};
+{diag}
 }}
 """)
     return "".join(out), stats
@@ -1242,6 +1248,20 @@ def r_path(targets, lam=None, rng=None):
     return chosen
 
 
+# Classes whose FP32 range kernels are also emitted with Algorithm 1's
+# recursion order (launched when the library's R-path option is set): the
+# three with the largest FP32 share of the l <= 2 workloads.
+RPATH_CLASSES = [((2, 2), (2, 2)), ((2, 2), (2, 1)), ((2, 1), (2, 1))]
+RPATH_LAMBDAS = (0.0, 0.5, 1.0, 2.0)
+
+
+def best_lambda(bra, ket, cds):
+    """The lambda of Algorithm 1's cost whose path over the R values a
+    kernel reads has the fewest operations (ties: the smallest lambda)."""
+    t = r_targets(bra, ket, cds)
+    return min(RPATH_LAMBDAS, key=lambda lam: (r_path_flops(r_path(t, lam)), lam))
+
+
 # Recursion order of the R values in the straight-line kernels: None keeps the
 # fixed t-then-u-then-v order over full levels (the code the GPU runs has been
 # measured with); a number selects Algorithm 1's greedy search with that lambda
@@ -1363,11 +1383,15 @@ def generate(outdir, lmax=LMAX, nfiles=None):
                                           for c0, _ in crange_groups(bra, ket))
             else:
                 f32_launches = f"    eri_jk_{name}_f32<<<grid, block, 0, s>>>(a);"
+            rpath = ""
+            if (bra, ket) in RPATH_CLASSES and crange_groups(bra, ket):
+                rl = "\n".join(f"    eri_jk_{name}_f32r_c{c0}<<<grid, block, 0, s>>>(a);" for c0, _ in crange_groups(bra, ket))
+                rpath = f"  else if (prec == 2) {{  // FP32, Algorithm 1's recursion order\n{rl}\n  }}\n"
             src.append(f"""
 int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s) {{
   if (grid <= 0) return 0;
   if (prec == 0) eri_jk_{name}_f64<<<grid, block, 0, s>>>(a);
-  else {{
+{rpath}  else {{
 {f32_launches}
   }}
   return (int)cudaGetLastError();
@@ -1379,7 +1403,7 @@ int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStr
 int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
   if (a.count <= 0) return 0;
   const int bs = 128;
-  eri_schwarz_{bra[0]}{bra[1]}<<<(unsigned)(((long long)a.count * {nthr} + bs - 1) / bs), bs, 0, s>>>(a);
+  eri_schwarz_{bra[0]}{bra[1]}<<<(unsigned)(((long long)a.count * {nthr} * gb::kSchwarzSplit + bs - 1) / bs), bs, 0, s>>>(a);
   return (int)cudaGetLastError();
 }}
 """)

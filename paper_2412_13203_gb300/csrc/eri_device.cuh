@@ -93,12 +93,18 @@ struct GradArgs {
     double* grad;             // [natom * 3], accumulated
 };
 
+// Schwarz kernels spread the bra primitive pairs of a pair over up to this
+// many threads, each writing its partial diagonal (ab|ab)_ii.
+constexpr int kSchwarzSplit = 8;
+
 struct SchwarzArgs {
     PairsView pairs;
     int first, count;         // pair range (one angular class)
     const double* boys;
+    double* diag;             // [count][kSchwarzSplit][NAB] partial diagonals, zeroed by the caller
     double* Q;                // out: Q for pairs first..first+count-1
 };
+
 
 // ------------------------------------------------------------------ Boys
 template <int L>
@@ -494,14 +500,5 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
     }
 }
 
-
-// Schwarz factor from a (ab|ab) block: sqrt(max_i |(ab|ab)_ii|).
-template <int NAB>
-__device__ __forceinline__ double schwarz_from_block(const double* acc) {
-    double m = 0.0;
-#pragma unroll
-    for (int i = 0; i < NAB; ++i) m = fmax(m, fabs(acc[i * NAB + i]));
-    return sqrt(m);
-}
 
 }  // namespace gb

@@ -54,6 +54,11 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+// Fault injection (JK_OPT_FAIL_ALLOC_AFTER): the number of device
+// allocations that still succeed before one fails as if the device were out
+// of memory; negative: off.
+std::atomic<long long> g_fail_alloc{-1};
+
 #define CK(x)                                                                                     \
     do {                                                                                          \
         cudaError_t e_ = (x);                                                                     \
@@ -87,6 +92,10 @@ struct DevBuf {
         if (n <= bytes && p) return 0;
         release();
         if (n == 0) n = 16;
+        if (g_fail_alloc.load() >= 0 && g_fail_alloc.fetch_sub(1) <= 0) {
+            g_fail_alloc.store(0);
+            return fail(JK_ERR_NOMEM, "injected allocation failure (" + std::to_string(n) + " bytes)");
+        }
         if (cudaMalloc(&p, n) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -141,6 +150,7 @@ struct Options {
     int check_sym = 0;
     int graph = 1;
     int profile = 0;
+    int rpath = 0;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
 } g_opt;
 
 struct ProfRec {
@@ -479,6 +489,20 @@ __global__ void k_class_bounds(const unsigned long long* key, long long n, int s
     if (c != cp) start[c] = (int)k;
 }
 
+// Q_i = sqrt(max_d |sum_p diag[i][p][d]|) from the Schwarz kernels' partial
+// diagonals, the parts added in a fixed order (Q does not depend on scheduling).
+__global__ void k_schwarz_finish(const double* diag, int nab, int count, double* Q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double m = 0.0;
+    for (int d = 0; d < nab; ++d) {
+        double v = 0.0;
+        for (int p = 0; p < gb::kSchwarzSplit; ++p) v += diag[((size_t)i * gb::kSchwarzSplit + p) * nab + d];
+        m = fmax(m, fabs(v));
+    }
+    Q[i] = sqrt(m);
+}
+
 // Q_ab into A.w; maximum Q via integer atomics on the (non-negative) bit pattern.
 __global__ void k_store_q(const double* Q, int first, int count, double4* A, unsigned long long* qmax) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -560,15 +584,28 @@ __global__ void k_rows_count(const double4* A, int x0, int nX, const int* bseg /
     rket0[r] = s;
 }
 
+// Primitive quartets and (quartet x bra primitive pair) units of a class's
+// rows, summed per warp before one atomic per warp into acc[0], acc[1].
 __global__ void k_rows_primq(const long long* cnt, const int* rbra, const int* rket0, int nrows, const int4* info,
                              const long long* npre, unsigned long long* acc) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const long long c = cnt[r];
-    if (c == 0) return;
-    const long long kp = npre[rket0[r] + c] - npre[rket0[r]];
-    atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
-    atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
+    unsigned long long pq = 0, bp = 0;
+    if (r < nrows) {
+        const long long c = cnt[r];
+        if (c > 0) {
+            const long long kab = info[rbra[r]].z;
+            pq = (unsigned long long)((npre[rket0[r] + c] - npre[rket0[r]]) * kab);
+            bp = (unsigned long long)(c * kab);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pq += __shfl_xor_sync(0xffffffffu, pq, o);
+        bp += __shfl_xor_sync(0xffffffffu, bp, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (pq | bp)) {
+        atomicAdd(acc, pq);
+        atomicAdd(acc + 1, bp);
+    }
 }
 
 // Algorithmic cost of every row: the generator's operation count of its
@@ -814,7 +851,13 @@ int noalloc_scratch(double2** out) {
     return 0;
 }
 
-int pair_class_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+// Cartesian components n_a n_b of a pair class (classes ss ps pp ds dp dd fs fp fd ff).
+int pair_ncart(int cls) {
+    int la = 0;
+    while ((la + 1) * (la + 2) / 2 <= cls) ++la;
+    const int lb = cls - la * (la + 1) / 2;
+    return (la + 1) * (la + 2) / 2 * ((lb + 1) * (lb + 2) / 2);
+}
 
 gb::PairsView view_of(const jk_pairs_s* h) {
     gb::PairsView v;
@@ -969,7 +1012,6 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = d_q.alloc(sizeof(double) * np))) return rc;
     if ((rc = d_qmax.alloc(sizeof(unsigned long long)))) return rc;
     CK(cudaMemsetAsync(d_qmax.p, 0, sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(d_q.p, 0, sizeof(double) * np, st));  // chunked Schwarz kernels take a max into Q
     gb::PairsView pv;
     std::memset(&pv, 0, sizeof(pv));
     pv.npair = (int)np;
@@ -979,11 +1021,19 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     pv.pp = h->pp.as<double4>();
     pv.pp2 = h->pp2.as<double2>();
     const double* boys = g_boys[h->device].tab.as<double>();
+    DevBuf d_diag;
+    size_t diag_len = 1;
+    for (int c = 0; c < ncls; ++c) diag_len = std::max(diag_len, (size_t)(cend[c] - cst[c]) * pair_ncart(c));
+    if ((rc = d_diag.alloc(sizeof(double) * diag_len * gb::kSchwarzSplit))) return rc;
     for (int c = 0; c < ncls; ++c) {
         const int cnt = cend[c] - cst[c];
         if (cnt <= 0) continue;
-        gb::SchwarzArgs sa{pv, cst[c], cnt, boys, d_q.as<double>() + cst[c]};
+        const int nab = pair_ncart(c);
+        CK(cudaMemsetAsync(d_diag.p, 0, sizeof(double) * (size_t)cnt * nab * gb::kSchwarzSplit, st));
+        gb::SchwarzArgs sa{pv, cst[c], cnt, boys, d_diag.as<double>(), d_q.as<double>() + cst[c]};
         if (gb_launch_schwarz(c, sa, st)) return fail(JK_ERR_CUDA, "Schwarz kernel launch failed");
+        k_schwarz_finish<<<nblk(cnt, 256), 256, 0, st>>>(d_diag.as<double>(), nab, cnt, d_q.as<double>() + cst[c]);
+        CKL();
         k_store_q<<<nblk(cnt, 256), 256, 0, st>>>(d_q.as<double>() + cst[c], cst[c], cnt, s_A.as<double4>(),
                                                   d_qmax.as<unsigned long long>());
         CKL();
@@ -1059,67 +1109,81 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     }
     if ((rc = scan_exclusive(d_npk.as<long long>(), d_npre.as<long long>(), kept + 1, d_tot.as<long long>() + 1, st)))
         return rc;
-    DevBuf d_primq;
-    if ((rc = d_primq.alloc(2 * sizeof(unsigned long long)))) return rc;
+    // Every class pair's rows are enumerated, scanned and counted in stream
+    // order with shared scratch; the per-class totals land in one device array
+    // that is read back with a single synchronisation at the end.
     h->rows.clear();
     h->rows.reserve(ncls * (ncls + 1) / 2);
     h->nquartets = 0;
     h->nprimq = 0;
+    std::vector<int> seg_all, seg_off(ncls + 1, 0);
+    for (int Y = 0; Y < ncls; ++Y) {
+        for (int b = 0; b < kNB; ++b)
+            if (be[Y * kNB + b] > bs[Y * kNB + b]) { seg_all.push_back(bs[Y * kNB + b]); seg_all.push_back(be[Y * kNB + b]); }
+        seg_off[Y + 1] = (int)seg_all.size() / 2;
+    }
+    long long max_rows = 0;
     for (int X = 0; X < ncls; ++X) {
-        const int x0 = bs[X * kNB], x1 = be[X * kNB + kNB - 1];
-        const int nX = x1 - x0;
+        const int nX = be[X * kNB + kNB - 1] - bs[X * kNB];
         for (int Y = 0; Y <= X; ++Y) {
-            std::vector<int> seg;
-            for (int b = 0; b < kNB; ++b)
-                if (be[Y * kNB + b] > bs[Y * kNB + b]) { seg.push_back(bs[Y * kNB + b]); seg.push_back(be[Y * kNB + b]); }
-            const int nb = (int)seg.size() / 2;
+            const int nb = seg_off[Y + 1] - seg_off[Y];
             if (nX == 0 || nb == 0) continue;
             h->rows.emplace_back();
             ClassRows& cr = h->rows.back();
             cr.bra_cls = X;
             cr.ket_cls = Y;
+            if ((long long)nX * nb > INT32_MAX) return fail(JK_ERR_UNSUPPORTED, "more than 2^31 quartet rows in a class");
             cr.nrows = nX * nb;
-            DevBuf d_seg, d_cnt;
-            if ((rc = upload(d_seg, seg.data(), seg.size(), st))) return rc;
-            if ((rc = d_cnt.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = cr.start.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            if ((rc = cr.bra.alloc(sizeof(int) * cr.nrows))) return rc;
-            if ((rc = cr.ket0.alloc(sizeof(int) * cr.nrows))) return rc;
-            k_rows_count<<<nblk(cr.nrows, 256), 256, 0, st>>>(h->A.as<double4>(), x0, nX, d_seg.as<int>(), nb, X == Y,
-                                                              thresh, d_cnt.as<long long>(), cr.bra.as<int>(),
-                                                              cr.ket0.as<int>());
-            CKL();
-            CK(cudaMemsetAsync(d_cnt.as<long long>() + cr.nrows, 0, sizeof(long long), st));
-            CK(cudaMemsetAsync(d_primq.p, 0, 2 * sizeof(unsigned long long), st));
-            if ((rc = scan_exclusive(d_cnt.as<long long>(), cr.start.as<long long>(), cr.nrows + 1,
-                                     d_tot.as<long long>() + 2, st)))
-                return rc;
-            k_rows_primq<<<nblk(cr.nrows, 256), 256, 0, st>>>(d_cnt.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
-                                                              cr.nrows, h->info.as<int4>(), d_npre.as<long long>(),
-                                                              d_primq.as<unsigned long long>());
-            CKL();
-            // work items of the FP64 launch (the counts buffer is reused once primq has read it)
-            if ((rc = cr.istart.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
-            k_row_items<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.nrows,
-                                                             h->info.as<int4>(), nullptr, nullptr,
-                                                             gb_class_split(X, Y), d_cnt.as<long long>());
-            CKL();
-            if ((rc = scan_exclusive(d_cnt.as<long long>(), cr.istart.as<long long>(), cr.nrows + 1,
-                                     d_tot.as<long long>() + 3, st)))
-                return rc;
-            long long tot = 0, itot = 0;
-            unsigned long long pq2[2] = {0, 0};
-            CK(cudaMemcpyAsync(&tot, d_tot.as<long long>() + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(&itot, d_tot.as<long long>() + 3, sizeof(long long), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(pq2, d_primq.p, sizeof(pq2), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            cr.total = tot;
-            cr.itotal = itot;
-            cr.nprimq = (long long)pq2[0];
-            cr.nbrap = (long long)pq2[1];
-            h->nquartets += tot;
-            h->nprimq += cr.nprimq;
+            max_rows = std::max<long long>(max_rows, cr.nrows);
         }
+    }
+    const int ncr = (int)h->rows.size();
+    DevBuf d_seg, d_cnt, d_scr, d_ctot;
+    if ((rc = upload(d_seg, seg_all.data(), std::max<size_t>(1, seg_all.size()), st))) return rc;
+    if ((rc = d_cnt.alloc(sizeof(long long) * (max_rows + 1)))) return rc;
+    if ((rc = d_scr.alloc(sizeof(long long) * (scan_scratch_len(max_rows + 1) + 1)))) return rc;
+    if ((rc = d_ctot.alloc(sizeof(long long) * 4 * std::max(1, ncr)))) return rc;
+    CK(cudaMemsetAsync(d_ctot.p, 0, sizeof(long long) * 4 * std::max(1, ncr), st));
+    for (int k = 0; k < ncr; ++k) {
+        ClassRows& cr = h->rows[k];
+        const int X = cr.bra_cls, Y = cr.ket_cls;
+        const int x0 = bs[X * kNB], nX = be[X * kNB + kNB - 1] - x0, nb = seg_off[Y + 1] - seg_off[Y];
+        long long* ctot = d_ctot.as<long long>() + 4 * k;  // quartets, work items, primitive quartets, bra prim units
+        if ((rc = cr.start.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+        if ((rc = cr.bra.alloc(sizeof(int) * cr.nrows))) return rc;
+        if ((rc = cr.ket0.alloc(sizeof(int) * cr.nrows))) return rc;
+        if ((rc = cr.istart.alloc(sizeof(long long) * (cr.nrows + 1)))) return rc;
+        k_rows_count<<<nblk(cr.nrows, 256), 256, 0, st>>>(h->A.as<double4>(), x0, nX, d_seg.as<int>() + 2 * seg_off[Y],
+                                                          nb, X == Y, thresh, d_cnt.as<long long>(), cr.bra.as<int>(),
+                                                          cr.ket0.as<int>());
+        CKL();
+        CK(cudaMemsetAsync(d_cnt.as<long long>() + cr.nrows, 0, sizeof(long long), st));
+        if ((rc = scan_into(d_cnt.as<long long>(), cr.start.as<long long>(), cr.nrows + 1, ctot, d_scr.as<long long>(), st)))
+            return rc;
+        k_rows_primq<<<nblk(cr.nrows, 256), 256, 0, st>>>(d_cnt.as<long long>(), cr.bra.as<int>(), cr.ket0.as<int>(),
+                                                          cr.nrows, h->info.as<int4>(), d_npre.as<long long>(),
+                                                          reinterpret_cast<unsigned long long*>(ctot + 2));
+        CKL();
+        // work items of the FP64 launch (the counts buffer is reused once primq has read it)
+        k_row_items<<<nblk(cr.nrows, 256), 256, 0, st>>>(cr.start.as<long long>(), cr.bra.as<int>(), cr.nrows,
+                                                         h->info.as<int4>(), nullptr, nullptr, gb_class_split(X, Y),
+                                                         d_cnt.as<long long>());
+        CKL();
+        if ((rc = scan_into(d_cnt.as<long long>(), cr.istart.as<long long>(), cr.nrows + 1, ctot + 1,
+                            d_scr.as<long long>(), st)))
+            return rc;
+    }
+    std::vector<long long> ctot(4 * std::max(1, ncr));
+    CK(cudaMemcpyAsync(ctot.data(), d_ctot.p, sizeof(long long) * ctot.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < ncr; ++k) {
+        ClassRows& cr = h->rows[k];
+        cr.total = ctot[4 * k];
+        cr.itotal = ctot[4 * k + 1];
+        cr.nprimq = ctot[4 * k + 2];
+        cr.nbrap = ctot[4 * k + 3];
+        h->nquartets += cr.total;
+        h->nprimq += cr.nprimq;
     }
     return 0;
 }
@@ -1178,7 +1242,7 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
         pr->total = total_hint;
         CK(cudaEventRecord(pr->e0, st));
     }
-    const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec, a, grid, tc.block, st);
+    const int e = gb_launch_jk(cr.bra_cls, cr.ket_cls, prec == 1 && g_opt.rpath ? 2 : prec, a, grid, tc.block, st);
     if (e) return fail(JK_ERR_CUDA, std::string("ERI kernel launch: ") + cudaGetErrorString((cudaError_t)e));
     h->launches += 1;
     if (pr) CK(cudaEventRecord(pr->e1, st));
@@ -1461,7 +1525,7 @@ struct BatchPlan {
     std::vector<unsigned long long> serial;  // of every handle: a freed handle's address can come back
     std::vector<const double*> D;
     std::vector<double*> J, K;
-    int prec = 0, device = 0, max_n = 0, graph = 0;
+    int prec = 0, device = 0, max_n = 0, graph = 0, rpath = 0;
     double tau = 0.0, eps = 0.0, tsmall = 0.0;
     long long nquartets = 0;
     DevBuf bm, dmax, split_tot;
@@ -1485,6 +1549,14 @@ struct BatchPlan {
 std::mutex g_batch_mu;
 std::atomic<unsigned long long> g_serial{0};
 std::unique_ptr<BatchPlan> g_plan;
+
+// A cached batch plan copies its molecules' per-class launch configuration
+// when it is built: a new tuning of any of its handles (or freeing one)
+// retires it.
+void drop_plan_of(const jk_pairs_s* h) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (g_plan && std::find(g_plan->mols.begin(), g_plan->mols.end(), h) != g_plan->mols.end()) g_plan.reset();
+}
 
 __global__ void k_offset_copy(const long long* src, int n, long long off, long long* dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1685,7 +1757,8 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     const TuneCfg& tc = bc.tune[prec];
     int nsm = P.mols[0]->nsm;
     const long long items = bc.total * gb_class_split(bc.X, bc.Y) * gb_class_threads(bc.X, bc.Y, prec);  // upper bound
-    const int e = gb_launch_jk(bc.X, bc.Y, prec, a, grid_for(items, tc.block, tc.qpt, nsm), tc.block, s);
+    const int e = gb_launch_jk(bc.X, bc.Y, prec == 1 && P.rpath ? 2 : prec, a, grid_for(items, tc.block, tc.qpt, nsm),
+                               tc.block, s);
     if (e) return fail(JK_ERR_CUDA, std::string("batched ERI launch: ") + cudaGetErrorString((cudaError_t)e));
     P.launches += 1;
     return 0;
@@ -1822,7 +1895,8 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
     int dev = -1;
     CK(cudaGetDevice(&dev));
     bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
-                g_plan->tau == g_opt.tau && g_plan->eps == g_opt.eps && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph;
+                g_plan->tau == g_opt.tau && g_plan->eps == g_opt.eps && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph &&
+                g_plan->rpath == g_opt.rpath;
     for (int m = 0; same && m < nmol; ++m)
         same = g_plan->mols[m] == pairs[m] && g_plan->serial[m] == pairs[m]->serial && g_plan->D[m] == D[m] &&
                g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
@@ -1841,6 +1915,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
         P.eps = g_opt.eps;
         P.tsmall = g_opt.tsmall;
         P.graph = g_opt.graph;
+        P.rpath = g_opt.rpath;
         if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
     }
     BatchPlan& P = *g_plan;
@@ -1927,6 +2002,7 @@ int autotune_impl(jk_pairs_s* h, const double* D, double* J, double* K, int prec
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->tuned[prec] = 1;
+    drop_plan_of(h);
     return 0;
 }
 
@@ -2237,6 +2313,11 @@ int jk_set_option(jk_option opt, double v) {
             if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "density screening threshold");
             g_opt.eps = v;
             return JK_OK;
+        case JK_OPT_RPATH: g_opt.rpath = v != 0.0; return JK_OK;
+        case JK_OPT_FAIL_ALLOC_AFTER:
+            if (!std::isfinite(v)) return fail(JK_ERR_INVALID, "allocation fault count");
+            g_fail_alloc.store(v < 0 ? -1 : (long long)v);
+            return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2250,6 +2331,8 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_GRAPH: *v = g_opt.graph; return JK_OK;
         case JK_OPT_PROFILE: *v = g_opt.profile; return JK_OK;
         case JK_OPT_DENSITY_SCREEN: *v = g_opt.eps; return JK_OK;
+        case JK_OPT_RPATH: *v = g_opt.rpath; return JK_OK;
+        case JK_OPT_FAIL_ALLOC_AFTER: *v = (double)g_fail_alloc.load(); return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2298,17 +2381,25 @@ int jk_tuning(jk_pairs h, int max_rows, int* rows, int* nrows) {
 
 int jk_set_tuning(jk_pairs h, int nrows, const int* rows) {
     if (!h || nrows < 0 || (nrows > 0 && !rows)) return fail(JK_ERR_INVALID, "bad argument");
+    // every entry is checked before any is applied: a corrupted configuration changes nothing
+    const int ncls = gb_num_pair_classes();
     for (int k = 0; k < nrows; ++k) {
         const int* r = rows + 6 * k;
+        if (r[0] < 0 || r[0] >= ncls || r[1] < 0 || r[1] > r[0])
+            return fail(JK_ERR_INVALID, "tuning entry " + std::to_string(k) + ": class out of range");
         if (r[2] < 32 || r[2] > 128 || r[2] % 32 || r[4] < 32 || r[4] > 128 || r[4] % 32 || r[3] < 1 || r[5] < 1 ||
             r[3] > (1 << 20) || r[5] > (1 << 20))
-            return fail(JK_ERR_INVALID, "tuning entry out of range");
+            return fail(JK_ERR_INVALID, "tuning entry " + std::to_string(k) + " out of range");
+    }
+    for (int k = 0; k < nrows; ++k) {
+        const int* r = rows + 6 * k;
         for (ClassRows& cr : h->rows)
             if (cr.bra_cls == r[0] && cr.ket_cls == r[1]) {
                 cr.tune[0].block = r[2]; cr.tune[0].qpt = r[3];
                 cr.tune[1].block = r[4]; cr.tune[1].qpt = r[5];
             }
     }
+    drop_plan_of(h);
     return JK_OK;
 }
 
@@ -2518,10 +2609,7 @@ int jk_sph_transform(jk_pairs h, jk_sph_dir dir, const double* in, double* out, 
 
 void shellpairs_free(jk_pairs h) {
     if (!h) return;
-    {   // a cached batch plan that reads this handle's device arrays goes with it
-        std::lock_guard<std::mutex> lk(g_batch_mu);
-        if (g_plan && std::find(g_plan->mols.begin(), g_plan->mols.end(), h) != g_plan->mols.end()) g_plan.reset();
-    }
+    drop_plan_of(h);  // a cached batch plan that reads this handle's device arrays goes with it
     delete h;
 }
 

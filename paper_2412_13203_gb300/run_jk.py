@@ -1,5 +1,7 @@
-"""Command-line driver: one seeded workload, J/K (or gradient) builds on the
-GPU, timings printed.  Used for profiling captures.
+"""Command-line driver: one seeded workload (a reduced atom count of any of
+the synthetic recipes), J/K, gradient, pure-shell or one-electron builds on
+the GPU with their wall times -- a quick check of an installation, and the
+small cases the kernel profiles are captured on.
 
     python -m paper_2412_13203_gb300.run_jk --config 1 --prec fp64 [--natom 8] [--repeat 2]
         [--grad | --pure | --one-electron] [--screen EPS]

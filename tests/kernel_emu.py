@@ -60,11 +60,20 @@ def _sources(lmax, only=None, ntu=8):
             f32 = " ".join(f"eri_jk_{name}_f32_c{c0}(a);" for c0, _ in mg.crange_groups(bra, ket))
         else:
             f32 = f"eri_jk_{name}_f32(a);"
-        jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else {{ {f32} }} return 0;")
+        if (bra, ket) in mg.RPATH_CLASSES and mg.crange_groups(bra, ket):
+            # prec 2: the FP32 range kernels emitted with Algorithm 1's recursion order
+            f32r = " ".join(f"eri_jk_{name}_f32r_c{c0}(a);" for c0, _ in mg.crange_groups(bra, ket))
+            jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else if (prec == 2) {{ {f32r} }} "
+                            f"else {{ {f32} }} return 0;")
+        else:
+            jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else {{ {f32} }} return 0;")
         if bra == ket:
             nthr = mg.ncart(bra[0]) if mg.use_chunk(bra, ket) else 1
-            sw_cases.append(f"    case {pcs.index(bra)}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(count * {nthr}); "
-                            f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); return 0;")
+            nab = mg.ncart(bra[0]) * mg.ncart(bra[1])
+            sw_cases.append(f"    case {pcs.index(bra)}: nab = {nab}; diag.assign((size_t)count * gb::kSchwarzSplit * nab, 0.0); "
+                            f"sa.diag = diag.data(); for (blockIdx.x = 0; "
+                            f"blockIdx.x < (unsigned)(count * {nthr} * gb::kSchwarzSplit); "
+                            f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); break;")
         if (bra, ket) in gqs:
             gthr = mg.grad_threads(bra, ket)  # threads per work item (chunked f classes: ket components)
             grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(total * {gthr}); "
@@ -129,10 +138,23 @@ extern "C" int emu_schwarz(int X, int npair, const int4* info, const double4* A,
     sa.pairs = pv(npair, info, A, B, pp, pp2, nullptr, nullptr, nullptr);
     sa.first = first; sa.count = count; sa.boys = boys; sa.Q = Q;
     threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    std::vector<double> diag;
+    int nab = 0;
     switch (X) {
 """ + "\n".join(sw_cases) + """
+    default: return -1;
     }
-    return -1;
+    // the runtime's k_schwarz_finish: parts added in order, sqrt of the largest |diagonal|
+    for (int i = 0; i < count; ++i) {
+        double m = 0.0;
+        for (int d = 0; d < nab; ++d) {
+            double v = 0.0;
+            for (int p = 0; p < gb::kSchwarzSplit; ++p) v += diag[((size_t)i * gb::kSchwarzSplit + p) * nab + d];
+            m = std::fmax(m, std::fabs(v));
+        }
+        Q[i] = std::sqrt(m);
+    }
+    return 0;
 }
 extern "C" int emu_grad(int X, int Y, int npair, const int4* info, const double4* A, const double4* B,
                         const double4* pp, const double2* pp2, const double* alpha, int nrows,
