@@ -120,8 +120,10 @@ int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartet
  * (jk_set_option) run in FP32 -- primitive arithmetic, contracted block and
  * the digestion dot products, from centre differences formed in FP64 --
  * and each digested sum is added to J and K in FP64 (split accumulation);
- * the other quartets, the Boys function at small T, the Schwarz factors and
- * the final J/K symmetrisation stay FP64.  JK_FP64 accumulates J' and K'
+ * the other quartets, the Schwarz factors and the final J/K symmetrisation
+ * stay FP64, and the Boys function of FP32 quartets can be evaluated in FP64
+ * below T = tsmall (JK_OPT_MIXED_TSMALL; default 0: the FP32 evaluation,
+ * table and downward recursion, is as accurate there).  JK_FP64 accumulates J' and K'
  * with compensation (each update split into a multiple of 2^-32, summed
  * exactly while partial sums stay below 2^21, and a remainder summed
  * separately; handle-owned nbf x nbf scratch), so the result does not depend
@@ -219,7 +221,9 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 /* Tunables (process-wide). */
 typedef enum {
     JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
-    JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys in FP64 for T < tsmall (default 1.0) */
+    JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys of FP32 quartets in FP64 for T < tsmall (default 0:
+                                  * measured to change no J/K/E error on the benchmark workloads, while
+                                  * the FP64 branch kept the FP32 kernels' FP64 pipe busy) */
     JK_OPT_CHECK_SYMMETRY = 2,   /* nonzero: jk_build checks D == D^T first (synchronous):
                                   * JK_ERR_NOT_SYMMETRIC if not, JK_ERR_INVALID if D holds a NaN or
                                   * an infinity */

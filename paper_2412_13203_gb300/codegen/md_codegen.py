@@ -774,6 +774,12 @@ def gen_class_kernels(bra, ket):
     for prec, real in (("f64", "double"), ("f32", "float")):
         flat = use_flat(bra, ket, prec)
         name = class_name(bra, ket)
+        # warp-run pre-reduction of the digestion (FP32 flat and range kernels):
+        # J'_ab over the lanes of a row, the other targets over the lanes of a
+        # quartet split over bra primitive pairs (classes with P > 1)
+        warp = WARP_DIGEST.get(prec, False) and not chunk
+        wtpl = f", {real}, true, {'true' if P > 1 else 'false'}" if warp else ""
+        wargs = ", ws" if warp else ""
         # kernel variants of this precision: (name suffix, body, digest call, block size)
         variants = []
         if chunk:
@@ -784,31 +790,57 @@ def gen_class_kernels(bra, ket):
             for c0, c1 in crange_groups(bra, ket):
                 cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
                 body, st = gen_quartet_body(bra, ket, real, True, cds)
-                variants.append((f"_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, ib.x, "
-                                                  f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * len(cds)))
+                variants.append((f"_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}{wtpl}>(acc, ib.x, "
+                                                  f"ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf{wargs});",
+                                 na * nb * len(cds)))
             if (bra, ket) in RPATH_CLASSES:
                 # the same ranges with the R recursion order of Algorithm 1
                 # (greedy path search, lambda of fewest operations per range)
                 for c0, c1 in crange_groups(bra, ket):
                     cds = [c * nd + d for c in range(c0, c1) for d in range(nd)]
                     body, _ = gen_quartet_body(bra, ket, real, True, cds, rpath=best_lambda(bra, ket, cds))
-                    variants.append((f"r_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}>(acc, "
-                                                       f"ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);",
+                    variants.append((f"r_c{c0}", body, f"gb::digest_crange<{na}, {nb}, {nc}, {nd}, {c0}, {c1}{wtpl}>(acc, "
+                                                       f"ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf{wargs});",
                                      na * nb * len(cds)))
         else:
             body, st = gen_quartet_body(bra, ket, real, flat)
-            variants.append(("", body, f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}>"
-                                       f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf);", na * nb * nc * nd))
+            wt, wa = (wtpl, wargs) if flat else ("", "")
+            variants.append(("", body, f"gb::{'digest' if flat else 'digest_loop'}<{na}, {nb}, {nc}, {nd}{wt}>"
+                                       f"(acc, ib.x, ib.y, ik.x, ik.y, {{dm}}, Jm, Km, Jlm, Klm, nbf{wa});", na * nb * nc * nd))
         if prec == "f64":
             stats = st
         if real == "float":
-            centres = ("  const double4 Ad = pairs.A[bra], Cd = pairs.A[ket];\n"
-                       "  const float ACx = (float)(Ad.x - Cd.x), ACy = (float)(Ad.y - Cd.y), ACz = (float)(Ad.z - Cd.z);")
+            centres = ("  const float4 ah = pairs.Ahl[2 * bra], al = pairs.Ahl[2 * bra + 1];\n"
+                       "  const float4 ch = pairs.Ahl[2 * ket], cl = pairs.Ahl[2 * ket + 1];\n"
+                       "  // A - C from the split centres: no FP64 operation in an FP32 kernel\n"
+                       "  const float ACx = (ah.x - ch.x) + (al.x - cl.x), ACy = (ah.y - ch.y) + (al.y - cl.y),\n"
+                       "              ACz = (ah.z - ch.z) + (al.z - cl.z);")
             dmat = "Dfm"
         else:
             centres = "  const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];"
             dmat = "Dm"
         for suffix, body, digest, nacc in variants:
+            warpk = warp and ", ws);" in digest
+            loop_head = (
+                "  const long long stride = (long long)gridDim.x * blockDim.x;\n"
+                "  for (long long t0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~(GB_WARP_SIZE - 1)); "
+                "t0 < total; t0 += stride) {\n"
+                "  // warp-uniform loop: every lane takes part in the digestion's shuffles\n"
+                "  const long long tid = t0 + (threadIdx.x & (GB_WARP_SIZE - 1));\n"
+                "  const bool act = tid < total;\n"
+                "  const long long rt = act ? total - 1 - tid : 0;"
+                if warpk else
+                "  for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;\n"
+                "       tid += (long long)gridDim.x * blockDim.x) {\n"
+                "  const long long rt = total - 1 - tid;")
+            warp_tail = (
+                "  if (!act) {\n"
+                "#pragma unroll\n"
+                f"    for (int i = 0; i < {nacc}; ++i) acc[i] = 0;\n"
+                "  }\n"
+                "  const gb::WarpSeg ws = gb::warp_seg(act ? (unsigned)row : 0x80000000u | (threadIdx.x & 31),\n"
+                "                                      act ? (unsigned)((qt - ipart) & 0x7fffffff) : 0x80000000u | (threadIdx.x & 31), act);"
+                if warpk else "")
             out.append(f"""
 __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JKArgs args) {{
   // persistent grid-stride loop over the quartets of this launch; the total is
@@ -827,9 +859,7 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   const float* __restrict__ boysf = args.boysf;
   const float tsmall = args.tsmall;
   (void)boysf; (void)tsmall;
-  for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < total;
-       tid += (long long)gridDim.x * blockDim.x) {{
-  const long long rt = total - 1 - tid;
+{loop_head}
   const long long qq = rt / {nch};
   const int ci = (int)(rt - qq * {nch});
   const long long qt = base + qq;
@@ -867,6 +897,7 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   if (bra == ket) s *= 0.5f;
 #pragma unroll
   for (int i = 0; i < {nacc}; ++i) acc[i] *= s;
+{warp_tail}
   {digest.format(dm=dmat)}
   }}
 }}
@@ -1247,6 +1278,10 @@ def r_path(targets, lam=None, rng=None):
             todo.update(c for c in _r_children(node, best) if c not in chosen)
     return chosen
 
+
+# Warp-run pre-reduction of the digestion per precision (flat and range
+# digestion forms; see gb::WarpSeg).
+WARP_DIGEST = {"f32": True, "f64": False}
 
 # Classes whose FP32 range kernels are also emitted with Algorithm 1's
 # recursion order (launched when the library's R-path option is set): the

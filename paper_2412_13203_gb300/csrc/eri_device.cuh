@@ -37,6 +37,10 @@ struct PairsView {
     const float4* ppf;     // per primitive pair: P - A (xyz), p
     const float4* ppf2;    // per primitive pair: P - B (xyz), kappa
     const double* alpha;   // per primitive pair: exponent of the shell-a primitive (gradients)
+    // per pair: centre of a split into two floats per coordinate, [2i] = hi =
+    // (float)A, [2i + 1] = lo = (float)(A - hi): FP32 kernels form A - C as
+    // (hi_A - hi_C) + (lo_A - lo_C) without an FP64 operation
+    const float4* Ahl;
 };
 
 struct RowsView {
@@ -217,6 +221,67 @@ __device__ __forceinline__ void jk_add(double* X, double* lo, size_t i, double v
     atomicAdd(X + i, v);
 }
 
+// Warp-level pre-reduction of the digestion (FP32 kernels).  The lanes of a
+// warp hold consecutive work items: the items of one row share the bra pair
+// (its J'_ab targets), and the items of one shell quartet split over bra
+// primitive pairs share all of its targets.  Both form contiguous runs of
+// lanes; a run's sum is formed with shuffles and added to J or K by its first
+// lane -- one atomic (and one FP32 -> FP64 conversion) per run instead of one
+// per lane.  Lanes past the end of the work (the last iteration) take part
+// with zero values and keys of their own, and add nothing.
+#ifndef GB_WARP_SIZE
+#define GB_WARP_SIZE 32
+#endif
+struct WarpSeg {
+    unsigned rmask, qmask;  // bit o set: lane + o is in this lane's row / quartet run
+    bool rhead, qhead;      // this lane is the first of its run
+    bool act;               // this lane holds a real work item
+};
+
+__device__ __forceinline__ WarpSeg warp_seg(unsigned rkey, unsigned qkey, bool act) {
+    WarpSeg w;
+    const unsigned lane = threadIdx.x & (GB_WARP_SIZE - 1);
+    w.rmask = 0;
+    w.qmask = 0;
+    w.act = act;
+#pragma unroll
+    for (int o = 1; o < GB_WARP_SIZE; o <<= 1) {
+        const unsigned r2 = __shfl_down_sync(0xffffffffu, rkey, o);
+        const unsigned q2 = __shfl_down_sync(0xffffffffu, qkey, o);
+        if (lane + o < GB_WARP_SIZE) {
+            if (r2 == rkey) w.rmask |= o;
+            if (q2 == qkey) w.qmask |= o;
+        }
+    }
+    const unsigned rp = __shfl_up_sync(0xffffffffu, rkey, 1), qp = __shfl_up_sync(0xffffffffu, qkey, 1);
+    w.rhead = lane == 0 || rp != rkey;
+    w.qhead = lane == 0 || qp != qkey;
+    return w;
+}
+
+// Sum of v over this lane's run (complete at the run's first lane): tree
+// steps 1, 2, 4, ... add the partial of lane + o while it is in the same run.
+template <class T>
+__device__ __forceinline__ T run_sum(T v, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < GB_WARP_SIZE; o <<= 1) {
+        const T u = __shfl_down_sync(0xffffffffu, v, o);
+        if (mask & o) v += u;
+    }
+    return v;
+}
+
+// One digestion target: reduced over the row run (row) or the quartet run
+// when W is set, then added by the run's first lane.
+template <class R, bool W>
+__device__ __forceinline__ void jk_put(double* X, double* lo, size_t i, R v, const WarpSeg& ws, bool row) {
+    if constexpr (W) {
+        v = run_sum(v, row ? ws.rmask : ws.qmask);
+        if (!ws.act || !(row ? ws.rhead : ws.qhead)) return;
+    }
+    jk_add<R>(X, lo, i, (double)v);
+}
+
 // Fused J/K update of one unique shell quartet (ab|cd), acc[((a*NB+b)*NC+c)*ND+d],
 // already scaled by the degeneracy factor s.  With the eight permutational
 // images and a symmetric D,
@@ -227,10 +292,11 @@ __device__ __forceinline__ void jk_add(double* X, double* lo, size_t i, double v
 // R is the arithmetic type of the block and of the density copy (double for
 // FP64 quartets; float for FP32 quartets, whose sums are added to J and K
 // in FP64 by the atomics).
-template <int NA, int NB, int NC, int ND, class R>
+template <int NA, int NB, int NC, int ND, class R, bool WR = false, bool WQ = false>
 __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int fd,
                                        const R* __restrict__ D, double* J, double* K, double* Jlo,
-                                       double* Klo, int n) {
+                                       double* Klo, int n,
+                                       const WarpSeg& ws = WarpSeg()) {
     // J'_ab
 #pragma unroll
     for (int a = 0; a < NA; ++a)
@@ -242,7 +308,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fc + c) * n + fd + d), v);
-            jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
+            jk_put<R, WR>(J, Jlo, (size_t)(fa + a) * n + fb + b, v + v, ws, true);
         }
     // J'_cd
 #pragma unroll
@@ -255,7 +321,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fb + b), v);
-            jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
+            jk_put<R, WQ>(J, Jlo, (size_t)(fc + c) * n + fd + d, v + v, ws, false);
         }
     // K'_ac and K'_ad
 #pragma unroll
@@ -268,7 +334,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), v);
-            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fc + c, v, ws, false);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
@@ -278,7 +344,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fd + d, v, ws, false);
         }
     }
     // K'_bc and K'_bd
@@ -292,7 +358,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fc + c, v, ws, false);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
@@ -302,7 +368,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
                     v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fd + d, v, ws, false);
         }
     }
 }
@@ -311,10 +377,11 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
 // quartet: acc[(ab * NCR + (c - C0)) * ND + d], NCR = C1 - C0 (the FP32
 // kernels of the large classes compute a quartet's block one c range per
 // launch; the ranges' updates add up to the full one).
-template <int NA, int NB, int NC, int ND, int C0, int C1, class R>
+template <int NA, int NB, int NC, int ND, int C0, int C1, class R, bool WR = false, bool WQ = false>
 __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int fc, int fd,
                                               const R* __restrict__ D, double* J, double* K, double* Jlo,
-                                       double* Klo, int n) {
+                                       double* Klo, int n,
+                                       const WarpSeg& ws = WarpSeg()) {
     constexpr int NCR = C1 - C0;
 #define GB_ACC(a, b, c, d) acc[(((a) * NB + (b)) * NCR + ((c) - C0)) * ND + (d)]
 #pragma unroll
@@ -326,7 +393,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int c = C0; c < C1; ++c)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fc + c) * n + fd + d), v);
-            jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
+            jk_put<R, WR>(J, Jlo, (size_t)(fa + a) * n + fb + b, v + v, ws, true);
         }
 #pragma unroll
     for (int c = C0; c < C1; ++c)
@@ -337,7 +404,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int b = 0; b < NB; ++b) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fb + b), v);
-            jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
+            jk_put<R, WQ>(J, Jlo, (size_t)(fc + c) * n + fd + d, v + v, ws, false);
         }
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
@@ -348,7 +415,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fd + d), v);
-            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fc + c, v, ws, false);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {  // K'_ad
@@ -357,7 +424,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fc + c), v);
-            jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fd + d, v, ws, false);
         }
     }
 #pragma unroll
@@ -369,7 +436,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fd + d), v);
-            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fc + c, v, ws, false);
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {  // K'_bd
@@ -378,7 +445,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fc + c), v);
-            jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
+            jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fd + d, v, ws, false);
         }
     }
 #undef GB_ACC

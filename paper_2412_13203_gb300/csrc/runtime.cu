@@ -146,7 +146,7 @@ BoysTables g_boys[64];
 struct Options {
     double tau = 1e-2;
     double eps = 0.0;  // density screening of mixed builds (0: off)
-    double tsmall = 1.0;
+    double tsmall = 0.0;  // FP32 Boys everywhere in FP32 quartets (the FP64 branch buys no accuracy)
     int check_sym = 0;
     int graph = 1;
     int profile = 0;
@@ -168,6 +168,7 @@ struct jk_pairs_s {
     long long npair_all = 0, npair = 0, nprimpair = 0;
     double thresh = 0.0, Qmax = 0.0;
     DevBuf info, A, B, pp, pp2, ppf, ppf2;          // sorted, kept pairs
+    DevBuf Ahl;                                     // float4 x 2 per pair: centre of a as hi + lo floats
     DevBuf Df;                                      // FP32 copy of the last mixed build's D
     DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
     DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
@@ -533,6 +534,16 @@ __global__ void k_final_key(const double4* A, const int4* info, const int2* lab,
     val[k] = (int)k;
 }
 
+// Centre of a of every pair as two floats per coordinate (hi, lo = A - hi).
+__global__ void k_centres_hl(const double4* A, long long n, float4* hl) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double4 a = A[k];
+    const float hx = (float)a.x, hy = (float)a.y, hz = (float)a.z;
+    hl[2 * k] = make_float4(hx, hy, hz, 0.f);
+    hl[2 * k + 1] = make_float4((float)(a.x - hx), (float)(a.y - hy), (float)(a.z - hz), 0.f);
+}
+
 __global__ void k_quantise_q(double4* A, long long n) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -870,6 +881,7 @@ gb::PairsView view_of(const jk_pairs_s* h) {
     v.ppf = h->ppf.as<float4>();
     v.ppf2 = h->ppf2.as<float4>();
     v.alpha = h->alpha.as<double>();
+    v.Ahl = h->Ahl.as<float4>();
     return v;
 }
 
@@ -1074,6 +1086,11 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
         k_quantise_q<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), kept);
         CKL();
     }
+    if ((rc = h->Ahl.alloc(sizeof(float4) * 2 * nk))) return rc;
+    if (kept > 0) {
+        k_centres_hl<<<nblk(kept, 256), 256, 0, st>>>(h->A.as<double4>(), kept, h->Ahl.as<float4>());
+        CKL();
+    }
     // ---- class / bucket segments
     const int nseg = kMaxClasses * kNB;
     DevBuf d_bs;
@@ -1122,6 +1139,7 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
             if (be[Y * kNB + b] > bs[Y * kNB + b]) { seg_all.push_back(bs[Y * kNB + b]); seg_all.push_back(be[Y * kNB + b]); }
         seg_off[Y + 1] = (int)seg_all.size() / 2;
     }
+    if (seg_all.empty()) seg_all.assign(2, 0);  // nothing kept: a placeholder keeps the upload non-empty
     long long max_rows = 0;
     for (int X = 0; X < ncls; ++X) {
         const int nX = be[X * kNB + kNB - 1] - bs[X * kNB];

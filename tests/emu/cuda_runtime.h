@@ -53,4 +53,9 @@ inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &
 inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
 inline unsigned int __float_as_uint(float x) { unsigned int r; std::memcpy(&r, &x, 4); return r; }
 inline double __dadd_rn(double a, double b) { return a + b; }
+// one thread at a time: a warp of one lane, whose shuffles return its own value
+#define GB_WARP_SIZE 1
+template <class T> inline T __shfl_down_sync(unsigned, T v, int) { return v; }
+template <class T> inline T __shfl_up_sync(unsigned, T v, int) { return v; }
+template <class T> inline T __shfl_xor_sync(unsigned, T v, int) { return v; }
 inline double __dsub_rn(double a, double b) { return a - b; }

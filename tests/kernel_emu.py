@@ -78,14 +78,23 @@ def _sources(lmax, only=None, ntu=8):
             gthr = mg.grad_threads(bra, ket)  # threads per work item (chunked f classes: ket components)
             grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(total * {gthr}); "
                               f"++blockIdx.x) eri_grad_{name}_f64(g); return 0;")
-    src = ['#include "eri_device.cuh"', "#include <vector>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
+    src = ['#include "eri_device.cuh"', "#include <vector>", "#include <deque>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
+static std::deque<std::vector<float4>> g_ahl;  // split centres of every view built (kept alive)
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
     gb::PairsView v;
     std::memset(&v, 0, sizeof(v));
     v.npair = npair; v.info = info; v.A = A; v.B = B; v.pp = pp; v.pp2 = pp2; v.ppf = ppf; v.ppf2 = ppf2;
     v.alpha = alpha;
+    // the runtime's k_centres_hl: centre of a as hi = (float)A and lo = (float)(A - hi)
+    g_ahl.emplace_back(2 * (size_t)npair);
+    for (int i = 0; i < npair; ++i) {
+        const float hx = (float)A[i].x, hy = (float)A[i].y, hz = (float)A[i].z;
+        g_ahl.back()[2 * i] = float4{hx, hy, hz, 0.f};
+        g_ahl.back()[2 * i + 1] = float4{(float)(A[i].x - hx), (float)(A[i].y - hy), (float)(A[i].z - hz), 0.f};
+    }
+    v.Ahl = g_ahl.back().data();
     return v;
 }
 extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
