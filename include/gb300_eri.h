@@ -138,10 +138,14 @@ int jk_build(jk_pairs pairs, const double* D, double* J, double* K, jk_precision
 /* Nuclear gradient of E = tr(DJ)/2 - tr(DK)/4 at fixed D (device pointers):
  * dEdR[natom*3] (float64, device) is overwritten.  Derivative integrals by the
  * shift rule d phi_a/dA_i = 2 alpha phi_{a+1_i} - a_i phi_{a-1_i} on centres
- * A, B and C; the D centre by translational invariance.  Both precisions run
- * the FP64 derivative kernels, compiled for every class up to (ff|ff); a
- * library built for a lower angular momentum returns JK_ERR_UNSUPPORTED for
- * classes above it. */
+ * A, B and C; the D centre by translational invariance.  Compiled for every
+ * class up to (ff|ff) (a library built for a lower angular momentum returns
+ * JK_ERR_UNSUPPORTED for classes above it).  JK_FP64: every derivative
+ * integral in FP64.  JK_MIXED: the quartets whose density-weighted bound (as
+ * in jk_build) is below JK_OPT_GRAD_TAU take FP32 derivative kernels (centre
+ * differences formed in FP64, per-quartet sums added to dEdR in FP64), the
+ * others FP64; this synchronises the stream once (list sizes) and leaves its
+ * split in jk_last_split / jk_split_stats. */
 int jk_grad(jk_pairs pairs, const double* D, double* dEdR, jk_precision prec, void* cuda_stream);
 
 /* Multi-GPU split of one molecule (Sec. 4, stage 2: quartet blocks are
@@ -242,12 +246,16 @@ typedef enum {
                                   * search of Algorithm 1 (Sec. 5, Graph Compiler; per kernel the
                                   * lambda of fewest operations) instead of the fixed t-u-v order
                                   * (default 0).  Same integrals up to rounding. */
-    JK_OPT_FAIL_ALLOC_AFTER = 7  /* fault injection for callers' error handling: n >= 0 lets n more
+    JK_OPT_FAIL_ALLOC_AFTER = 7, /* fault injection for callers' error handling: n >= 0 lets n more
                                   * device allocations of the library succeed, then the next one
                                   * fails with JK_ERR_NOMEM (as if the device were full) and the
                                   * count stays at 0 (every later one fails) until the option is
                                   * set to a negative value (default -1: off).  No device memory
                                   * is touched by an injected failure. */
+    JK_OPT_GRAD_TAU = 8          /* mixed gradient (jk_grad with JK_MIXED): derivative integrals in FP32
+                                  * for the quartets whose density-weighted bound (as for JK_OPT_MIXED_TAU)
+                                  * is below this value, FP64 otherwise; every per-quartet gradient sum
+                                  * is added to dE/dR in FP64 (default 1e-3) */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);

@@ -961,10 +961,10 @@ def comp_table(l):
     return f"static __device__ __constant__ int c_comp_{l}[{len(rows)}] = {{{', '.join(map(str, rows))}}};"
 
 
-def _store_axis_array(E, em, name, li, lj, E_axis):
+def _store_axis_array(E, em, name, li, lj, E_axis, real="double"):
     """Write per-axis E[(i,j,t)] (i <= li, j <= lj) into a flat local array."""
     T = li + lj + 1
-    E(f"double {name}[{(li + 1) * (lj + 1) * T}];")
+    E(f"{real} {name}[{(li + 1) * (lj + 1) * T}];")
     for i in range(li + 1):
         for j in range(lj + 1):
             for t in range(T):
@@ -986,8 +986,9 @@ def grad_threads(bra, ket):
     return ncart(ket[0]) if use_grad_chunk(bra, ket) else 1
 
 
-def gen_grad_kernel(bra, ket):
-    """FP64 nuclear-gradient kernel of one class.
+def gen_grad_kernel(bra, ket, prec="f64"):
+    """Nuclear-gradient kernel of one class, FP64 or FP32 (the mixed gradient's
+    small-bound quartets), plus its launcher for both.
 
     Per unique shell quartet: Gamma_abcd = s (4 D_ab D_cd - D_ac D_bd - D_ad D_bc)
     (the weight of (ab|cd) in E = tr(DJ)/2 - tr(DK)/4 summed over its eight
@@ -997,7 +998,13 @@ def gen_grad_kernel(bra, ket):
       E'^{ab}_t = 2 alpha E^{a_x+1, b_x}_t - a_x E^{a_x-1, b_x}_t  (centre A),
       E'^{ab}_t = 2 beta  E^{a_x, b_x+1}_t - b_x E^{a_x, b_x-1}_t  (centre B),
     the same on the ket for centre C, and dI/dD = -(dI/dA + dI/dB + dI/dC)
-    (translational invariance)."""
+    (translational invariance).  The FP32 form works from the centre
+    differences formed in FP64 and rounded once (as the FP32 J/K kernels), with
+    the scaled R recursion (prefactor folded into the ket and bra weights), Gamma
+    formed in FP64 from D and rounded, and the per-item gradient sums added to
+    dE/dR in FP64.  Both forms walk the work items of a launch (rows.start[0]
+    .. rows.start[nrows] - 1, read on the device) with a grid-stride loop,
+    heaviest first, and read explicit ket lists where the rows carry them."""
     la, lb = bra
     lc, ld = ket
     L = la + lb + lc + ld
@@ -1008,46 +1015,61 @@ def gen_grad_kernel(bra, ket):
     h1 = herm(la + lb + 1)
     h0 = herm(la + lb)
     H1, H0 = len(h1), len(h0)
-    em = Emitter("double")
+    f32 = prec == "f32"
+    real = "float" if f32 else "double"
+    fma = "fmaf" if f32 else "fma"
+    zero = "0.0f" if f32 else "0.0"
+    em = Emitter(real)
     E = em.emit
     name = class_name(bra, ket)
     TB = la + lb + 3      # t range of the bra arrays (i <= la+1, j <= lb+1)
     TK = lc + ld + 2      # t range of the ket arrays (i <= lc+1, j <= ld)
     chunk = use_grad_chunk(bra, ket)
+    nthr = nc if chunk else 1
     NCDx = nd if chunk else NCD  # ket component pairs per thread
-    E(f"__global__ void __launch_bounds__(128) eri_grad_{name}_f64(const gb::GradArgs args) {{")
-    if chunk:
-        E("const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
-        E(f"if (gtid >= args.total * {nc}) return;")
-        E(f"const long long tid = gtid / {nc};")
-        E(f"const int cthr = (int)(gtid - tid * {nc});")
-    else:
-        E("const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;")
-        E("if (tid >= args.total) return;")
+    P = split_of(bra, ket)
+    E(f"__global__ void __launch_bounds__(128) eri_grad_{name}_{prec}(const gb::GradArgs args) {{")
+    E("const long long base = args.rows.start[0];")
+    E(f"const long long total = (args.rows.start[args.rows.nrows] - base) * {nthr};")
+    E("for (long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x; gt < total;")
+    E("     gt += (long long)gridDim.x * blockDim.x) {")
     # work items as in the J/K kernels: a quartet split into min(P, K_ab) items
     # over its bra primitive pairs, heaviest rows (largest ket primitive count,
     # at the end of the range) first so that the launch tail is light
-    P = split_of(bra, ket)
+    E("const long long rt = total - 1 - gt;")
+    E(f"const long long it = rt / {nthr};")
+    E(f"const int cthr = (int)(rt - it * {nthr});")
+    E("(void)cthr;")
     E("int row;")
     E("long long li;")
-    E("gb::locate_row(args.rows, args.base + args.total - 1 - tid, row, li);")
+    E("gb::locate_row(args.rows, base + it, row, li);")
     E("const int bra = __ldg(args.rows.bra + row);")
     E("const gb::PairsView& pairs = args.pairs;")
     E("const double* __restrict__ boys = args.boys;")
+    E("const float* __restrict__ boysf = args.boysf;")
+    E("const float tsmall = args.tsmall;")
+    E("(void)boysf; (void)tsmall;")
     E("const double* __restrict__ Dm = args.D;")
     E("const int n = args.nbf;")
     E("const int4 ib = pairs.info[bra];")
     E(f"const int nsplit = min({P}, ib.z);")
     E("const long long qo = li / nsplit;")
     E("const int ipart = (int)(li - qo * nsplit);")
-    E("const int ket = __ldg(args.rows.ket0 + row) + (int)qo;")
+    E("const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)")
+    E("                                : __ldg(args.rows.ket0 + row) + (int)qo;")
     E("const int4 ik = pairs.info[ket];")
-    E("const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];")
+    if f32:
+        E("const float4 ah = pairs.Ahl[2 * bra], al = pairs.Ahl[2 * bra + 1];")
+        E("const float4 ch = pairs.Ahl[2 * ket], cl = pairs.Ahl[2 * ket + 1];")
+        E("const float ACx = (ah.x - ch.x) + (al.x - cl.x), ACy = (ah.y - ch.y) + (al.y - cl.y),")
+        E("            ACz = (ah.z - ch.z) + (al.z - cl.z);")
+    else:
+        E("const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];")
     E("double s = 1.0;")
     E("if (ib.x == ib.y) s *= 0.5;")
     E("if (ik.x == ik.y) s *= 0.5;")
     E("if (bra == ket) s *= 0.5;")
-    E(f"double G[{NAB * NCDx}];")
+    E(f"{real} G[{NAB * NCDx}];")
     E(f"for (int ab = 0; ab < {NAB}; ++ab) {{")
     E(f"  const int a = ib.x + ab / {nb}, b = ib.y + ab % {nb};")
     E(f"  for (int cd = 0; cd < {NCDx}; ++cd) {{")
@@ -1055,47 +1077,76 @@ def gen_grad_kernel(bra, ket):
         E("    const int c = ik.x + cthr, d = ik.y + cd;")
     else:
         E(f"    const int c = ik.x + cd / {nd}, d = ik.y + cd % {nd};")
-    E("    G[ab * %d + cd] = s * (4.0 * Dm[(size_t)a * n + b] * Dm[(size_t)c * n + d] - Dm[(size_t)a * n + c] * Dm[(size_t)b * n + d] - Dm[(size_t)a * n + d] * Dm[(size_t)b * n + c]);" % NCDx)
+    E(f"    G[ab * {NCDx} + cd] = ({real})(s * (4.0 * Dm[(size_t)a * n + b] * Dm[(size_t)c * n + d] - Dm[(size_t)a * n + c] * Dm[(size_t)b * n + d] - Dm[(size_t)a * n + d] * Dm[(size_t)b * n + c]));")
     E("  }")
     E("}")
-    E("double gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0}, gC[3] = {0, 0, 0};")
-    E(f"double X[{H1 * NCDx}];")
-    E(f"double XC[{3 * H0 * NCDx}];")
-    E(f"double Rc[{S * S * S}];")
+    E(f"{real} gA[3] = {{0, 0, 0}}, gB[3] = {{0, 0, 0}}, gC[3] = {{0, 0, 0}};")
+    E(f"{real} X[{H1 * NCDx}];")
+    E(f"{real} XC[{3 * H0 * NCDx}];")
+    E(f"{real} Rc[{S * S * S}];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
-    E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
-    E("const double p = pa.w, kp = pb.x, inv2p = pb.y, alpha = pairs.alpha[ib.w + ip], beta = p - alpha;")
-    E("const double PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
-    E("const double PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
+    if f32:
+        E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
+        E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
+        E("const float alpha = (float)pairs.alpha[ib.w + ip], beta = p - alpha;")
+        E("const float PAx = pa.x, PAy = pa.y, PAz = pa.z;")
+        E("const float PBx = pb.x, PBy = pb.y, PBz = pb.z;")
+        E("const float PCx = PAx + ACx, PCy = PAy + ACy, PCz = PAz + ACz;  // P - C")
+    else:
+        E("const double4 pa = pairs.pp[ib.w + ip]; const double2 pb = pairs.pp2[ib.w + ip];")
+        E("const double p = pa.w, kp = pb.x, inv2p = pb.y, alpha = pairs.alpha[ib.w + ip], beta = p - alpha;")
+        E("const double PAx = pa.x - A.x, PAy = pa.y - A.y, PAz = pa.z - A.z;")
+        E("const double PBx = pa.x - B.x, PBy = pa.y - B.y, PBz = pa.z - B.z;")
     inv2p = Sym(name="inv2p")
     for ax in "xyz":
         Eb = gen_E_axis(em, f"gb{ax}", la + 1, lb + 1, Sym(name=f"PA{ax}"), Sym(name=f"PB{ax}"), inv2p)
-        _store_axis_array(E, em, f"eb{ax}", la + 1, lb + 1, Eb)
-    E(f"for (int i = 0; i < {H1 * NCDx}; ++i) X[i] = 0.0;")
-    E(f"for (int i = 0; i < {3 * H0 * NCDx}; ++i) XC[i] = 0.0;")
+        _store_axis_array(E, em, f"eb{ax}", la + 1, lb + 1, Eb, real)
+    E(f"for (int i = 0; i < {H1 * NCDx}; ++i) X[i] = 0;")
+    E(f"for (int i = 0; i < {3 * H0 * NCDx}; ++i) XC[i] = 0;")
     E("for (int jq = 0; jq < ik.z; ++jq) {")
-    E("const double4 qa = pairs.pp[ik.w + jq]; const double2 qb = pairs.pp2[ik.w + jq];")
-    E("const double q = qa.w, kq = qb.x, inv2q = qb.y, gam2 = 2.0 * pairs.alpha[ik.w + jq];")
-    E("const double QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
-    E("const double QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
+    if f32:
+        E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
+        E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q), gam2 = 2.0f * (float)pairs.alpha[ik.w + jq];")
+        E("const float QCx = qa.x, QCy = qa.y, QCz = qa.z;")
+        E("const float QDx = qb.x, QDy = qb.y, QDz = qb.z;")
+    else:
+        E("const double4 qa = pairs.pp[ik.w + jq]; const double2 qb = pairs.pp2[ik.w + jq];")
+        E("const double q = qa.w, kq = qb.x, inv2q = qb.y, gam2 = 2.0 * pairs.alpha[ik.w + jq];")
+        E("const double QCx = qa.x - C.x, QCy = qa.y - C.y, QCz = qa.z - C.z;")
+        E("const double QDx = qa.x - Dd.x, QDy = qa.y - Dd.y, QDz = qa.z - Dd.z;")
     inv2q = Sym(name="inv2q")
     for ax in "xyz":
         Ek = gen_E_axis(em, f"gk{ax}", lc + 1, ld, Sym(name=f"QC{ax}"), Sym(name=f"QD{ax}"), inv2q, sign=True)
-        _store_axis_array(E, em, f"ek{ax}", lc + 1, ld, Ek)
-    E("const double PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
-    E("const double rs = rsqrt(p + q);")
-    E("const double rho = p * q * rs * rs;")
-    E("const double T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
-    E("const double pref = kp * kq * rs;")
-    E("const double m2r = -2 * rho;")
-    E(f"double F[{L1 + 1}];")
-    E(f"gb::boys_f64<{L1}>(T, F, boys);")
-    if chunk:
-        gen_R_rolled(em, L1, False)
+        _store_axis_array(E, em, f"ek{ax}", lc + 1, ld, Ek, real)
+    if f32:
+        E("const float PQx = PCx - QCx, PQy = PCy - QCy, PQz = PCz - QCz;")
+        E("const float rs = rsqrtf(p + q);")
+        E("const float kqrs = kq * rs;  // ket weight of the scaled R (the bra weight kp follows below)")
+        E("const float rho = p * q * rs * rs;")
+        E("const float T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
+        E("const float r2 = 2.0f * rho;")
+        E("const float PQsx = r2 * PQx, PQsy = r2 * PQy, PQsz = r2 * PQz;")
+        for a in range(1, L1):
+            E(f"const float r2k{a} = {float(a)!r}f * r2;")
+        E(f"float F[{L1 + 1}];")
+        E(f"gb::boys_mixed<{L1}>(T, F, boys, boysf, tsmall);")
     else:
-        R = gen_R(em, L1, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
+        E("const double PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
+        E("const double rs = rsqrt(p + q);")
+        E("const double rho = p * q * rs * rs;")
+        E("const double T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
+        E("const double pref = kp * kq * rs;")
+        E("const double m2r = -2 * rho;")
+        E(f"double F[{L1 + 1}];")
+        E(f"gb::boys_f64<{L1}>(T, F, boys);")
+    if chunk:
+        gen_R_rolled(em, L1, f32)
+    else:
+        R = gen_R_scaled(em, L1, "F", ("PQsx", "PQsy", "PQsz"), "r2k") if f32 else \
+            gen_R(em, L1, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
         for (t, u, v), sv in R.items():
             E(f"Rc[{(t * S + u) * S + v}] = {em.val(sv)};")
+    kw = " * kqrs" if f32 else ""
     E(f"for (int cd = 0; cd < {NCDx}; ++cd) {{")
     if chunk:
         E("  const int c = cthr, d = cd;")
@@ -1105,16 +1156,16 @@ def gen_grad_kernel(bra, ket):
     E(f"  const int dx = c_comp_{ld}[3 * d], dy = c_comp_{ld}[3 * d + 1], dz = c_comp_{ld}[3 * d + 2];")
     # X over H1
     for k in range(H1):
-        E(f"  double xh{k} = X[{k * NCDx} + cd];")
+        E(f"  {real} xh{k} = X[{k * NCDx} + cd];")
     E("  for (int tau = 0; tau <= cx + dx; ++tau) {")
-    E(f"    const double ex = ekx[(cx * {ld + 1} + dx) * {TK} + tau];")
+    E(f"    const {real} ex = ekx[(cx * {ld + 1} + dx) * {TK} + tau]{kw};")
     E("    for (int nu = 0; nu <= cy + dy; ++nu) {")
-    E(f"      const double exy = ex * eky[(cy * {ld + 1} + dy) * {TK} + nu];")
+    E(f"      const {real} exy = ex * eky[(cy * {ld + 1} + dy) * {TK} + nu];")
     E("      for (int phi = 0; phi <= cz + dz; ++phi) {")
-    E(f"        const double e = exy * ekz[(cz * {ld + 1} + dz) * {TK} + phi];")
-    E(f"        const double* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
+    E(f"        const {real} e = exy * ekz[(cz * {ld + 1} + dz) * {TK} + phi];")
+    E(f"        const {real}* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
     for k, (t, u, v) in enumerate(h1):
-        E(f"        xh{k} = fma(e, Rb[{(t * S + u) * S + v}], xh{k});")
+        E(f"        xh{k} = {fma}(e, Rb[{(t * S + u) * S + v}], xh{k});")
     E("  }}}")
     for k in range(H1):
         E(f"  X[{k * NCDx} + cd] = xh{k};")
@@ -1123,7 +1174,7 @@ def gen_grad_kernel(bra, ket):
         cc = {"x": ("cx", "dx"), "y": ("cy", "dy"), "z": ("cz", "dz")}
         E("  {")
         for k in range(H0):
-            E(f"  double xc{k} = XC[{(di * H0 + k) * NCDx} + cd];")
+            E(f"  {real} xc{k} = XC[{(di * H0 + k) * NCDx} + cd];")
         rng = {a: (f"{cc[a][0]} + {cc[a][1]}" + (" + 1" if a == ax else "")) for a in "xyz"}
         idx = {"x": "tau", "y": "nu", "z": "phi"}
 
@@ -1133,16 +1184,16 @@ def gen_grad_kernel(bra, ket):
             if a != ax:
                 return f"ek{a}[({c} * {ld + 1} + {d}) * {TK} + {v}]"
             return (f"(gam2 * ek{a}[(({c} + 1) * {ld + 1} + {d}) * {TK} + {v}]"
-                    f" - ({c} > 0 ? {c} * ek{a}[(({c} - 1) * {ld + 1} + {d}) * {TK} + {v}] : 0.0))")
+                    f" - ({c} > 0 ? {c} * ek{a}[(({c} - 1) * {ld + 1} + {d}) * {TK} + {v}] : {zero}))")
         E(f"  for (int tau = 0; tau <= {rng['x']}; ++tau) {{")
-        E(f"    const double ex = {coef('x')};")
+        E(f"    const {real} ex = {coef('x')}{kw};")
         E(f"    for (int nu = 0; nu <= {rng['y']}; ++nu) {{")
-        E(f"      const double exy = ex * {coef('y')};")
+        E(f"      const {real} exy = ex * {coef('y')};")
         E(f"      for (int phi = 0; phi <= {rng['z']}; ++phi) {{")
-        E(f"        const double e = exy * {coef('z')};")
-        E(f"        const double* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
+        E(f"        const {real} e = exy * {coef('z')};")
+        E(f"        const {real}* Rb = Rc + (tau * {S} + nu) * {S} + phi;")
         for k, (t, u, v) in enumerate(h0):
-            E(f"        xc{k} = fma(e, Rb[{(t * S + u) * S + v}], xc{k});")
+            E(f"        xc{k} = {fma}(e, Rb[{(t * S + u) * S + v}], xc{k});")
         E("  }}}")
         for k in range(H0):
             E(f"  XC[{(di * H0 + k) * NCDx} + cd] = xc{k};")
@@ -1151,63 +1202,67 @@ def gen_grad_kernel(bra, ket):
     E("}  // ket primitives")
     # contraction with Gamma
     TBs = TB
+    two = "2.0f" if f32 else "2.0"
+    one = "1.0f" if f32 else "1.0"
     E(f"for (int ab = 0; ab < {NAB}; ++ab) {{")
     E(f"  const int a = ab / {nb}, b = ab % {nb};")
     E(f"  const int ax_ = c_comp_{la}[3 * a], ay_ = c_comp_{la}[3 * a + 1], az_ = c_comp_{la}[3 * a + 2];")
     E(f"  const int bx_ = c_comp_{lb}[3 * b], by_ = c_comp_{lb}[3 * b + 1], bz_ = c_comp_{lb}[3 * b + 2];")
     E("  const int ai[3] = {ax_, ay_, az_}, bi[3] = {bx_, by_, bz_};")
-    E("  const double* ebv[3] = {ebx, eby, ebz};")
+    E(f"  const {real}* ebv[3] = {{ebx, eby, ebz}};")
     E(f"  for (int cd = 0; cd < {NCDx}; ++cd) {{")
-    E(f"    const double g = G[ab * {NCDx} + cd];")
-    E("    if (g == 0.0) continue;")
+    E(f"    const {real} g = G[ab * {NCDx} + cd]{' * kp' if f32 else ''};")
+    E("    if (g == 0) continue;")
     # plain bra E over H0 for the C derivative; derivative bra E over H1 for A and B
     E("    for (int dir = 0; dir < 3; ++dir) {")
-    E("      double vA = 0.0, vB = 0.0, vC = 0.0;")
+    E(f"      {real} vA = 0, vB = 0, vC = 0;")
     E("      const int rx = ai[0] + bi[0] + (dir == 0), ry = ai[1] + bi[1] + (dir == 1), rz = ai[2] + bi[2] + (dir == 2);")
     E("      for (int t = 0; t <= rx; ++t) for (int u = 0; u <= ry; ++u) for (int v = 0; v <= rz; ++v) {")
     E("        const int tt[3] = {t, u, v};")
-    E("        double fA = 1.0, fB = 1.0, f0 = 1.0;")
+    E(f"        {real} fA = {one}, fB = {one}, f0 = {one};")
     E("        for (int k = 0; k < 3; ++k) {")
-    E(f"          const double* e = ebv[k];")
-    E(f"          const double base = e[(ai[k] * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
+    E(f"          const {real}* e = ebv[k];")
+    E(f"          const {real} base = e[(ai[k] * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
     E("          if (k == dir) {")
-    E(f"            const double up_a = e[((ai[k] + 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
-    E(f"            const double dn_a = ai[k] > 0 ? e[((ai[k] - 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]] : 0.0;")
-    E(f"            const double up_b = e[(ai[k] * {lb + 2} + bi[k] + 1) * {TBs} + tt[k]];")
-    E(f"            const double dn_b = bi[k] > 0 ? e[(ai[k] * {lb + 2} + bi[k] - 1) * {TBs} + tt[k]] : 0.0;")
-    E("            fA *= 2.0 * alpha * up_a - ai[k] * dn_a;")
-    E("            fB *= 2.0 * beta * up_b - bi[k] * dn_b;")
+    E(f"            const {real} up_a = e[((ai[k] + 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]];")
+    E(f"            const {real} dn_a = ai[k] > 0 ? e[((ai[k] - 1) * {lb + 2} + bi[k]) * {TBs} + tt[k]] : {zero};")
+    E(f"            const {real} up_b = e[(ai[k] * {lb + 2} + bi[k] + 1) * {TBs} + tt[k]];")
+    E(f"            const {real} dn_b = bi[k] > 0 ? e[(ai[k] * {lb + 2} + bi[k] - 1) * {TBs} + tt[k]] : {zero};")
+    E(f"            fA *= {two} * alpha * up_a - ai[k] * dn_a;")
+    E(f"            fB *= {two} * beta * up_b - bi[k] * dn_b;")
     E("            f0 *= base;")
     E("          } else { fA *= base; fB *= base; f0 *= base; }")
     E("        }")
     E("        const int tot = t + u + v;")
     E("        const int h = tot * (tot + 1) * (tot + 2) / 6 + (tot - t) * (tot - t + 1) / 2 + (tot - t - u);")
-    E(f"        const double xv = X[h * {NCDx} + cd];")
-    E("        vA = fma(fA, xv, vA);")
-    E("        vB = fma(fB, xv, vB);")
+    E(f"        const {real} xv = X[h * {NCDx} + cd];")
+    E(f"        vA = {fma}(fA, xv, vA);")
+    E(f"        vB = {fma}(fB, xv, vB);")
     E(f"        if (tot <= {la + lb} && t <= ai[0] + bi[0] && u <= ai[1] + bi[1] && v <= ai[2] + bi[2])")
-    E(f"          vC = fma(f0, XC[(dir * {H0} + h) * {NCDx} + cd], vC);")
+    E(f"          vC = {fma}(f0, XC[(dir * {H0} + h) * {NCDx} + cd], vC);")
     E("      }")
-    E("      gA[dir] = fma(g, vA, gA[dir]);")
-    E("      gB[dir] = fma(g, vB, gB[dir]);")
-    E("      gC[dir] = fma(g, vC, gC[dir]);")
+    E(f"      gA[dir] = {fma}(g, vA, gA[dir]);")
+    E(f"      gB[dir] = {fma}(g, vB, gB[dir]);")
+    E(f"      gC[dir] = {fma}(g, vC, gC[dir]);")
     E("    }")
     E("  }")
     E("}")
     E("}  // bra primitives")
     E("const int2 atb = args.atoms[bra], atk = args.atoms[ket];")
-    E("for (int k = 0; k < 3; ++k) {")
-    E("  atomicAdd(args.grad + 3 * atb.x + k, gA[k]);")
-    E("  atomicAdd(args.grad + 3 * atb.y + k, gB[k]);")
-    E("  atomicAdd(args.grad + 3 * atk.x + k, gC[k]);")
-    E("  atomicAdd(args.grad + 3 * atk.y + k, -(gA[k] + gB[k] + gC[k]));")
+    E("for (int k = 0; k < 3; ++k) {  // the item's sums, added in FP64")
+    E("  atomicAdd(args.grad + 3 * atb.x + k, (double)gA[k]);")
+    E("  atomicAdd(args.grad + 3 * atb.y + k, (double)gB[k]);")
+    E("  atomicAdd(args.grad + 3 * atk.x + k, (double)gC[k]);")
+    E("  atomicAdd(args.grad + 3 * atk.y + k, -((double)gA[k] + (double)gB[k] + (double)gC[k]));")
     E("}")
+    E("}")  # grid-stride loop
     E("}")
-    E(f"""
-int launch_grad_{name}(const gb::GradArgs& a, cudaStream_t s) {{
-  if (a.total <= 0) return 0;
-  const int bs = 128;
-  eri_grad_{name}_f64<<<(unsigned)((a.total{f" * {nc}" if chunk else ""} + bs - 1) / bs), bs, 0, s>>>(a);
+    if f32:
+        E(f"""
+int launch_grad_{name}(int prec, const gb::GradArgs& a, int grid, cudaStream_t s) {{
+  if (grid <= 0) return 0;
+  if (prec == 0) eri_grad_{name}_f64<<<grid, 128, 0, s>>>(a);
+  else eri_grad_{name}_f32<<<grid, 128, 0, s>>>(a);
   return (int)cudaGetLastError();
 }}""")
     return "\n".join(em.lines) + "\n"
@@ -1449,16 +1504,17 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
     ngf = max(4, len(gqs) // 5)
     gbins = [[] for _ in range(ngf)]
     gload = [0] * ngf
-    for bra, ket in sorted(gqs, key=lambda x: -len(gen_grad_kernel(*x))):
+    gcode = {q: gen_grad_kernel(*q, "f64") + gen_grad_kernel(*q, "f32") for q in gqs}
+    for bra, ket in sorted(gqs, key=lambda x: -len(gcode[x])):
         k = gload.index(min(gload))
         gbins[k].append((bra, ket))
-        gload[k] += len(gen_grad_kernel(bra, ket))
+        gload[k] += len(gcode[(bra, ket)])
     for k, items in enumerate(gbins):
         if not items:
             continue
         src = [header] + [comp_table(l) for l in range(min(lmax, GRAD_LMAX) + 1)]
         for bra, ket in items:
-            src.append(gen_grad_kernel(bra, ket))
+            src.append(gcode[(bra, ket)])
         fn = os.path.join(outdir, f"md_grad_{k}.cu")
         _write_if_changed(fn, "".join(src))
         files.append(fn)
@@ -1471,7 +1527,7 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
     for pc in pcs:
         d.append(f"int launch_schwarz_{pc[0]}{pc[1]}(const gb::SchwarzArgs& a, cudaStream_t s);")
     for bra, ket in gqs:
-        d.append(f"int launch_grad_{class_name(bra, ket)}(const gb::GradArgs& a, cudaStream_t s);")
+        d.append(f"int launch_grad_{class_name(bra, ket)}(int prec, const gb::GradArgs& a, int grid, cudaStream_t s);")
     n = len(pcs)
     d.append("typedef int (*jk_launch_fn)(int, const gb::JKArgs&, int, int, cudaStream_t);")
     d.append("typedef int (*schwarz_launch_fn)(const gb::SchwarzArgs&, cudaStream_t);")
@@ -1482,7 +1538,7 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
             row.append(f"launch_jk_{class_name(pcs[i], pcs[j])}" if j <= i else "nullptr")
         tab.append("{" + ", ".join(row) + "}")
     d.append(f"extern \"C\" int gb_num_pair_classes() {{ return {n}; }}")
-    d.append("typedef int (*grad_launch_fn)(const gb::GradArgs&, cudaStream_t);")
+    d.append("typedef int (*grad_launch_fn)(int, const gb::GradArgs&, int, cudaStream_t);")
     gtab = []
     for i in range(n):
         row = [f"launch_grad_{class_name(pcs[i], pcs[j])}" if j <= i and (pcs[i], pcs[j]) in gqs else "nullptr"
@@ -1490,8 +1546,15 @@ int launch_schwarz_{bra[0]}{bra[1]}(const gb::SchwarzArgs& a, cudaStream_t s) {{
         gtab.append("{" + ", ".join(row) + "}")
     d.append(f"static const grad_launch_fn k_grad_tab[{n}][{n}] = {{{', '.join(gtab)}}};")
     d.append("// -1: no derivative kernel for this class (shells above the gradient lmax)")
-    d.append("int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s) {\n"
-             "  return k_grad_tab[bra_cls][ket_cls] ? k_grad_tab[bra_cls][ket_cls](a, s) : -1;\n}")
+    d.append("// prec 0: FP64 derivative kernel, 1: FP32 (mixed gradient); grid-stride over the launch's items\n"
+             "int gb_launch_grad(int bra_cls, int ket_cls, int prec, const gb::GradArgs& a, int grid, cudaStream_t s) {\n"
+             "  return k_grad_tab[bra_cls][ket_cls] ? k_grad_tab[bra_cls][ket_cls](prec, a, grid, s) : -1;\n}")
+    gthr = []
+    for i in range(n):
+        gthr.append("{" + ", ".join(str(grad_threads(pcs[i], pcs[j]) if j <= i else 1) for j in range(n)) + "}")
+    d.append(f"static const int k_grad_threads_tab[{n}][{n}] = {{{', '.join(gthr)}}};")
+    d.append("// threads per work item of a derivative kernel (f classes: one per ket component c)")
+    d.append("int gb_grad_threads(int bra_cls, int ket_cls) { return k_grad_threads_tab[bra_cls][ket_cls]; }")
     d.append(f"int gb_grad_lmax() {{ return {min(lmax, GRAD_LMAX)}; }}")
     thr = []
     for prec in ("f64", "f32"):

@@ -87,10 +87,10 @@ struct JKArgs {
 
 struct GradArgs {
     PairsView pairs;
-    RowsView rows;
-    long long base;           // first work item of the launch (rows.start[0]; 0 for a whole class)
-    long long total;          // work items of the launch
+    RowsView rows;            // work items of the launch: rows.start[0] .. rows.start[nrows] - 1 (device)
     const double* boys;
+    const float* boysf;       // FP32 Boys table (FP32 derivative kernels)
+    float tsmall;             // FP32 kernels: FP64 Boys below this T
     const double* D;
     int nbf;
     const int2* atoms;        // per pair: atoms of shells a and b

@@ -38,7 +38,8 @@
 int gb_launch_jk(int bra_cls, int ket_cls, int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s);
 int gb_launch_schwarz(int cls, const gb::SchwarzArgs& a, cudaStream_t s);
 int gb_class_flops(int bra_cls, int ket_cls, int* per_primq, int* per_brap);
-int gb_launch_grad(int bra_cls, int ket_cls, const gb::GradArgs& a, cudaStream_t s);
+int gb_launch_grad(int bra_cls, int ket_cls, int prec, const gb::GradArgs& a, int grid, cudaStream_t s);
+int gb_grad_threads(int bra_cls, int ket_cls);
 int gb_grad_lmax();
 int gb_class_threads(int bra_cls, int ket_cls, int prec);
 int gb_class_split(int bra_cls, int ket_cls);
@@ -151,6 +152,7 @@ struct Options {
     int graph = 1;
     int profile = 0;
     int rpath = 0;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
+    double grad_tau = 1e-3;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
 } g_opt;
 
 struct ProfRec {
@@ -1273,7 +1275,7 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
 // demoted, FP64).  The per-row arrays are sized for the whole class and
 // written at the rows' own indices (with a zero after row r1 - 1).
 int split_count(jk_pairs_s* h, ClassRows& cr, int r0, int r1, const double* dmax, long long* split_tot,
-                cudaStream_t st) {
+                cudaStream_t st, double tau, double eps) {
     int rc;
     const long long n1 = cr.nrows + 1;
     for (DevBuf* b : {&cr.c64, &cr.c32, &cr.cdem, &cr.w64, &cr.w32, &cr.wdem, &cr.s64, &cr.s32, &cr.sdem, &cr.l64,
@@ -1284,7 +1286,7 @@ int split_count(jk_pairs_s* h, ClassRows& cr, int r0, int r1, const double* dmax
     const int nr = r1 - r0;
     k_rows_split<<<nblk(nr, 256), 256, 0, st>>>(
         cr.start.as<long long>() + r0, cr.bra.as<int>() + r0, cr.ket0.as<int>() + r0, nr, h->A.as<double4>(), dmax,
-        g_opt.tau, g_opt.eps, h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell,
+        tau, eps, h->info.as<int4>(), h->pair_sh.as<int2>(), h->Dsh.as<float>(), h->nshell,
         gb_class_split(cr.bra_cls, cr.ket_cls), cr.c64.as<long long>() + r0, cr.cdem.as<long long>() + r0,
         cr.c32.as<long long>() + r0, cr.k32.as<int>() + r0, cr.w64.as<long long>() + r0,
         cr.wdem.as<long long>() + r0, cr.w32.as<long long>() + r0, reinterpret_cast<unsigned long long*>(split_tot));
@@ -1299,7 +1301,7 @@ int split_count(jk_pairs_s* h, ClassRows& cr, int r0, int r1, const double* dmax
 // split_tot[2..4]), list offsets (l64, ldem; totals into split_tot[5..6]) and
 // the list fill.  The prefixes start at 0 at row r0.
 int split_fill(jk_pairs_s* h, ClassRows& cr, int r0, int r1, long long* split_tot, int* list64, int* listdem,
-               cudaStream_t st) {
+               cudaStream_t st, double tau, double eps) {
     int rc;
     const long long n1 = r1 - r0 + 1;
     long long* scr = cr.scr.as<long long>();
@@ -1312,7 +1314,7 @@ int split_fill(jk_pairs_s* h, ClassRows& cr, int r0, int r1, long long* split_to
         return rc;
     const int nr = r1 - r0;
     k_rows_fill<<<nblk(nr, 256), 256, 0, st>>>(cr.bra.as<int>() + r0, cr.ket0.as<int>() + r0, cr.k32.as<int>() + r0, nr,
-                                               h->A.as<double4>(), g_opt.tau, g_opt.eps, h->pair_sh.as<int2>(),
+                                               h->A.as<double4>(), tau, eps, h->pair_sh.as<int2>(),
                                                h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>() + r0,
                                                cr.ldem.as<long long>() + r0, list64, listdem);
     CKL();
@@ -1468,7 +1470,8 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         for (int k = 0; k < ncr; ++k) {
             range(k, R0[k], R1[k]);
             if (h->rows[k].total > 0 && R1[k] > R0[k] &&
-                (rc = split_count(h, h->rows[k], R0[k], R1[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st)))
+                (rc = split_count(h, h->rows[k], R0[k], R1[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st,
+                                  g_opt.tau, g_opt.eps)))
                 return rc;
         }
         // list sizes: one host synchronisation per mixed build
@@ -1488,7 +1491,9 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
             if (cr.total <= 0 || r1 <= r0) continue;
             int* l64 = h->list64.as<int>() + off64[k];
             int* ldm = h->listdem.as<int>() + offd[k];
-            if ((rc = split_fill(h, cr, r0, r1, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st))) return rc;
+            if ((rc = split_fill(h, cr, r0, r1, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st, g_opt.tau,
+                                 g_opt.eps)))
+                return rc;
             if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
                                    cr.l64.as<long long>(), l64, r0)))
                 return rc;
@@ -2202,35 +2207,101 @@ int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR
     }
     int rc;
     if (nparts > 1 && (rc = ensure_partition(h, nparts, st))) return rc;
-    // both precisions run the FP64 derivative kernels
+    const int ncr = (int)h->rows.size();
+    std::vector<int> R0(ncr), R1(ncr);
+    std::vector<long long> items(ncr);
+    for (int k = 0; k < ncr; ++k) {
+        R0[k] = nparts > 1 ? h->part_rows[k][part] : 0;
+        R1[k] = nparts > 1 ? h->part_rows[k][part + 1] : h->rows[k].nrows;
+        items[k] = nparts > 1 ? h->part_items[k][part + 1] - h->part_items[k][part] : h->rows[k].itotal;
+    }
     CK(cudaMemsetAsync(dEdR, 0, sizeof(double) * 3 * h->natom, st));
     h->launches = 0;
-    for (size_t k = 0; k < h->rows.size(); ++k) {
+    // one launch over rows [r0, r1) of a class: per-row item prefix `start`,
+    // contiguous kets from ket0 or explicit ones (kofs/klist)
+    auto launch = [&](int k, int kp, const long long* start, const int* ket0, const long long* kofs, const int* klist) {
         const ClassRows& cr = h->rows[k];
-        if (cr.total <= 0) continue;
-        const int r0 = nparts > 1 ? h->part_rows[k][part] : 0;
-        const int r1 = nparts > 1 ? h->part_rows[k][part + 1] : cr.nrows;
-        const long long i0 = nparts > 1 ? h->part_items[k][part] : 0;
-        const long long i1 = nparts > 1 ? h->part_items[k][part + 1] : cr.itotal;
-        if (r1 <= r0 || i1 <= i0) continue;
+        const int r0 = R0[k], nr = R1[k] - R0[k];
         gb::GradArgs a;
         std::memset(&a, 0, sizeof(a));
         a.pairs = view_of(h);
-        a.rows.nrows = r1 - r0;
-        a.rows.start = cr.istart.as<long long>() + r0;  // work items, as the J/K kernels
+        a.rows.nrows = nr;
+        a.rows.start = start + r0;
         a.rows.bra = cr.bra.as<int>() + r0;
-        a.rows.ket0 = cr.ket0.as<int>() + r0;
-        a.base = i0;
-        a.total = i1 - i0;
+        a.rows.ket0 = ket0 ? ket0 + r0 : nullptr;
+        a.rows.kofs = kofs ? kofs + r0 : nullptr;
+        a.rows.klist = klist;
         a.boys = g_boys[h->device].tab.as<double>();
+        a.boysf = g_boys[h->device].tabf.as<float>();
+        a.tsmall = (float)g_opt.tsmall;
         a.D = D;
         a.nbf = h->nbf;
         a.atoms = h->pair_atoms.as<int2>();
         a.grad = dEdR;
-        const int e = gb_launch_grad(cr.bra_cls, cr.ket_cls, a, st);
+        const int grid = grid_for(items[k] * gb_grad_threads(cr.bra_cls, cr.ket_cls), 128, 1, h->nsm);
+        const int e = gb_launch_grad(cr.bra_cls, cr.ket_cls, kp, a, grid, st);
         if (e) return fail(JK_ERR_CUDA, std::string("gradient kernel launch: ") + cudaGetErrorString((cudaError_t)e));
         h->launches += 1;
+        return 0;
+    };
+    if (prec == JK_FP64) {
+        for (int k = 0; k < ncr; ++k) {
+            const ClassRows& cr = h->rows[k];
+            if (cr.total <= 0 || R1[k] <= R0[k] || items[k] <= 0) continue;
+            if ((rc = launch(k, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), nullptr, nullptr))) return rc;
+        }
+        return JK_OK;
     }
+    // mixed: the J/K kernels' split with the gradient's cutoff -- derivative
+    // integrals of the quartets whose density-weighted bound is below grad_tau
+    // in FP32 (accumulated per item, added to dE/dR in FP64), the others FP64
+    const int n = h->nbf;
+    const size_t nst = (size_t)kSplitSlots * std::max(1, ncr);
+    if ((rc = h->scratch.alloc(64))) return rc;
+    if ((rc = h->split_tot.alloc(sizeof(long long) * nst))) return rc;
+    CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * nst, st));
+    CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
+    k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n * n, h->scratch.as<unsigned long long>(), nullptr);
+    CKL();
+    const size_t ns2 = (size_t)h->nshell * h->nshell;
+    if ((rc = h->Dsh.alloc(sizeof(float) * ns2))) return rc;
+    CK(cudaMemsetAsync(h->Dsh.p, 0, sizeof(float) * ns2, st));
+    k_dsh<<<152 * 4, 256, 0, st>>>(D, n, h->bf_shell.as<int>(), h->nshell, h->Dsh.as<unsigned int>());
+    CKL();
+    const double* dmax = reinterpret_cast<const double*>(h->scratch.p);
+    for (int k = 0; k < ncr; ++k)
+        if (h->rows[k].total > 0 && R1[k] > R0[k] &&
+            (rc = split_count(h, h->rows[k], R0[k], R1[k], dmax, h->split_tot.as<long long>() + kSplitSlots * k, st,
+                              g_opt.grad_tau, 0.0)))
+            return rc;
+    std::vector<long long> cnt(nst);
+    CK(cudaMemcpyAsync(cnt.data(), h->split_tot.p, sizeof(long long) * nst, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<long long> off64(ncr + 1, 0), offd(ncr + 1, 0);
+    for (int k = 0; k < ncr; ++k) {
+        off64[k + 1] = off64[k] + cnt[kSplitSlots * k + 1];
+        offd[k + 1] = offd[k] + cnt[kSplitSlots * k + 7];
+    }
+    if ((rc = h->list64.alloc(sizeof(int) * std::max(1LL, off64[ncr])))) return rc;
+    if ((rc = h->listdem.alloc(sizeof(int) * std::max(1LL, offd[ncr])))) return rc;
+    for (int k = 0; k < ncr; ++k) {
+        ClassRows& cr = h->rows[k];
+        if (cr.total <= 0 || R1[k] <= R0[k]) continue;
+        int* l64 = h->list64.as<int>() + off64[k];
+        int* ldm = h->listdem.as<int>() + offd[k];
+        if ((rc = split_fill(h, cr, R0[k], R1[k], h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st,
+                             g_opt.grad_tau, 0.0)))
+            return rc;
+        if ((rc = launch(k, 0, cr.s64.as<long long>(), nullptr, cr.l64.as<long long>(), l64))) return rc;
+        if ((rc = launch(k, 1, cr.s32.as<long long>(), cr.k32.as<int>(), nullptr, nullptr))) return rc;
+        if ((rc = launch(k, 1, cr.sdem.as<long long>(), nullptr, cr.ldem.as<long long>(), ldm))) return rc;
+    }
+    // the split diagnostics (jk_last_split, jk_split_stats) now describe this gradient
+    h->list_off64 = off64;
+    h->list_offd = offd;
+    h->last_r0 = R0;
+    h->last_r1 = R1;
+    h->last_prec = JK_MIXED;
     return JK_OK;
 }
 
@@ -2336,6 +2407,10 @@ int jk_set_option(jk_option opt, double v) {
             if (!std::isfinite(v)) return fail(JK_ERR_INVALID, "allocation fault count");
             g_fail_alloc.store(v < 0 ? -1 : (long long)v);
             return JK_OK;
+        case JK_OPT_GRAD_TAU:
+            if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "gradient tau");
+            g_opt.grad_tau = v;
+            return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2351,6 +2426,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_DENSITY_SCREEN: *v = g_opt.eps; return JK_OK;
         case JK_OPT_RPATH: *v = g_opt.rpath; return JK_OK;
         case JK_OPT_FAIL_ALLOC_AFTER: *v = (double)g_fail_alloc.load(); return JK_OK;
+        case JK_OPT_GRAD_TAU: *v = g_opt.grad_tau; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }

@@ -48,7 +48,7 @@ def _sources(lmax, only=None, ntu=8):
     for bra, ket in qs:
         code = mg.gen_class_kernels(bra, ket)[0]
         if (bra, ket) in gqs:
-            g = mg.gen_grad_kernel(bra, ket)
+            g = mg.gen_grad_kernel(bra, ket, "f64") + mg.gen_grad_kernel(bra, ket, "f32")
             code += g[:g.index("\nint launch_grad_")]
         k = load_.index(min(load_))
         tus[k].append(code)
@@ -76,8 +76,8 @@ def _sources(lmax, only=None, ntu=8):
                             f"++blockIdx.x) eri_schwarz_{bra[0]}{bra[1]}(sa); break;")
         if (bra, ket) in gqs:
             gthr = mg.grad_threads(bra, ket)  # threads per work item (chunked f classes: ket components)
-            grad_cases.append(f"    case {key}: for (blockIdx.x = 0; blockIdx.x < (unsigned)(total * {gthr}); "
-                              f"++blockIdx.x) eri_grad_{name}_f64(g); return 0;")
+            # grid-stride kernels: one call (one block of one thread) visits every item
+            grad_cases.append(f"    case {key}: if (prec == 0) eri_grad_{name}_f64(g); else eri_grad_{name}_f32(g); return 0;")
     src = ['#include "eri_device.cuh"', "#include <vector>", "#include <deque>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
 static std::deque<std::vector<float4>> g_ahl;  // split centres of every view built (kept alive)
@@ -165,16 +165,17 @@ extern "C" int emu_schwarz(int X, int npair, const int4* info, const double4* A,
     }
     return 0;
 }
-extern "C" int emu_grad(int X, int Y, int npair, const int4* info, const double4* A, const double4* B,
-                        const double4* pp, const double2* pp2, const double* alpha, int nrows,
-                        const long long* start, const int* bra, const int* ket0, long long total,
-                        const double* boys, const double* D, int nbf, const int2* atoms, double* grad) {
+extern "C" int emu_grad(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
+                        const double4* pp, const double2* pp2, const float4* ppf, const float4* ppf2,
+                        const double* alpha, int nrows, const long long* start, const int* bra, const int* ket0,
+                        const double* boys, const float* boysf, float tsmall, const double* D, int nbf,
+                        const int2* atoms, double* grad) {
     gb::GradArgs g;
     std::memset(&g, 0, sizeof(g));
-    g.pairs = pv(npair, info, A, B, pp, pp2, nullptr, nullptr, alpha);
+    g.pairs = pv(npair, info, A, B, pp, pp2, ppf, ppf2, alpha);
     g.rows.nrows = nrows; g.rows.start = start; g.rows.bra = bra; g.rows.ket0 = ket0;
-    g.total = total; g.boys = boys; g.D = D; g.nbf = nbf; g.atoms = atoms; g.grad = grad;
-    threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
+    g.boys = boys; g.boysf = boysf; g.tsmall = tsmall; g.D = D; g.nbf = nbf; g.atoms = atoms; g.grad = grad;
+    blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
 """ + "\n".join(grad_cases) + """
     }
@@ -359,7 +360,8 @@ class Problem:
             assert rc == 0
         return Q
 
-    def grad(self):
+    def grad(self, prec=0, tsmall=0.0):
+        """dE/dR from the derivative kernels of one precision (0 FP64, 1 FP32)."""
         lib = load(self.lmax, self.only)
         g = np.zeros((self.mol.xyz.shape[0], 3))
         for X in range(len(self.pcs)):
@@ -368,10 +370,11 @@ class Problem:
                 if r is None:
                     continue
                 bra, ket0, start = r
-                rc = lib.emu_grad(X, Y, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
-                                  self._p(self.pp), self._p(self.pp2), self._p(self.alpha), len(bra),
-                                  self._p(start), self._p(bra), self._p(ket0), C.c_longlong(int(start[-1])),
-                                  self._p(self.boys), self._p(self.D), self.nbf, self._p(self.atoms), self._p(g))
+                rc = lib.emu_grad(X, Y, prec, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
+                                  self._p(self.pp), self._p(self.pp2), self._p(self.ppf), self._p(self.ppf2),
+                                  self._p(self.alpha), len(bra), self._p(start), self._p(bra), self._p(ket0),
+                                  self._p(self.boys), self._p(self.boysf), C.c_float(tsmall), self._p(self.D),
+                                  self.nbf, self._p(self.atoms), self._p(g))
                 assert rc == 0
         return g
 

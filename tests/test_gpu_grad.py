@@ -72,3 +72,51 @@ def test_autograd_function(g):
     e = float(E.detach())
     assert abs(e - oracle.energy(D, Jo, Ko)) <= 1e-10 * max(1.0, abs(e))
     assert np.abs(Dt.grad.cpu().numpy() - (Jo - 0.5 * Ko)).max() <= 1e-10 * max(1.0, np.abs(Jo).max())
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(4, [0, 1, 2], 3, 2), (5, [0, 0, 1, 2], 4, 4)])
+def test_mixed_gradient_matches_oracle(g, seed, shells, natom, kmax):
+    """Mixed-precision gradient: the derivative integrals of the quartets
+    whose density-weighted bound is below grad_tau in FP32 (added to dE/dR in
+    FP64), the others FP64 -- within 1e-6 of the oracle's analytic gradient.
+    With grad_tau above every bound (all FP32) the FP32 kernels alone are
+    held to the same relative accuracy as the FP32 J/K kernels."""
+    mol = molgen.random_molecule(300 + seed, natom, shells, 1, kmax, 0.1, 50.0, layout="lattice", spacing=1.8)
+    D = molgen.density(mol, 400 + seed)
+    pairs = g.ShellPairs(mol)
+    Dt = torch.from_numpy(D).cuda()
+    go = oracle.grad(mol, D, mode="unique")
+    scale = max(1.0, np.abs(go).max())
+    tau = g.get_option("grad_tau")
+    both = False
+    try:
+        for t in (tau, 1e-2):
+            g.set_option("grad_tau", t)
+            gm = g.jk_grad(pairs, Dt, "mixed").cpu().numpy()
+            n32, n64 = g.last_split(pairs)
+            assert n32 + n64 == pairs.nquartets
+            both = both or (n32 > 0 and n64 > 0)
+            assert np.abs(gm - go).max() <= 1e-6, (t, np.abs(gm - go).max())
+            assert np.abs(gm.sum(axis=0)).max() <= 1e-8 * scale
+        assert both  # some setting ran both precisions
+        g.set_option("grad_tau", 1e30)
+        ga = g.jk_grad(pairs, Dt, "mixed").cpu().numpy()
+        assert g.last_split(pairs)[1] == 0
+        assert np.abs(ga - go).max() <= 2e-6 * scale
+    finally:
+        g.set_option("grad_tau", tau)
+    pairs.free()
+
+
+def test_mixed_gradient_24_atoms(g):
+    """The 24-atom workload: mixed gradient within 1e-6 of the FP64 one (itself
+    pinned to the oracle above), and its parts sum to it."""
+    mol, D = molgen.config(3)
+    pairs = g.ShellPairs(mol, molgen.CONFIG_THRESH[3])
+    Dt = torch.from_numpy(D).cuda()
+    g64 = g.jk_grad(pairs, Dt, "fp64")
+    gm = g.jk_grad(pairs, Dt, "mixed")
+    assert float((gm - g64).abs().max()) <= 1e-6, float((gm - g64).abs().max())
+    gs = sum(g.jk_grad_part(pairs, Dt, p, 2, "mixed") for p in range(2))
+    assert float((gs - gm).abs().max()) <= 1e-9 * float(gm.abs().max())
+    pairs.free()

@@ -43,6 +43,20 @@ def test_emulated_gradient():
     assert np.abs(g - go).max() <= 1e-10 * max(1.0, np.abs(go).max())
 
 
+@pytest.mark.parametrize("seed,shells,lmax", [(64, [0, 1, 2], 2), (74, [1, 3], 3)])
+def test_emulated_gradient_fp32(seed, shells, lmax):
+    """The FP32 derivative kernels (every quartet in FP32, real FP32 arithmetic;
+    the mixed gradient runs them for its small-bound quartets) against the
+    oracle's analytic gradient, and translational invariance."""
+    mol, D = _mol(seed, shells, 2, 2)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=lmax)
+    g = pr.grad(prec=1)
+    go = oracle.grad(mol, D, mode="unique")
+    scale = max(1.0, np.abs(go).max())
+    assert np.abs(g - go).max() <= 2e-6 * scale, np.abs(g - go).max() / scale
+    assert np.abs(g.sum(axis=0)).max() <= 2e-6 * scale
+
+
 @pytest.mark.parametrize("seed,shells", [(69, [0, 3]), (70, [3, 1]), (71, [2, 3])])
 def test_emulated_gradient_f_classes(seed, shells):
     """Derivative kernels of classes with an f shell (one thread per work item
