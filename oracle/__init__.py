@@ -69,6 +69,8 @@ def _load():
             lib.orc_jk.restype = C.c_longlong
             lib.orc_jk_rows.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, ip, dp, dp]
             lib.orc_jk_rows.restype = C.c_int
+            lib.orc_jk_rows_ld.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, ip, dp, dp]
+            lib.orc_jk_rows_ld.restype = C.c_int
             lib.orc_jk_quartets.argtypes = [C.POINTER(_Mol), dp, C.c_longlong, ip, dp, dp]
             lib.orc_jk_quartets.restype = C.c_longlong
             lib.orc_energy.argtypes = [C.c_int, dp, dp, dp]
@@ -213,15 +215,18 @@ def sample_unique_quartets(mol, n, seed, thresh=None, Q=None):
     return np.concatenate(out)[:n].astype(np.int32)
 
 
-def jk_rows(mol, D, shells, thresh: float | None = None):
-    """Rows of J and K for every basis function of the listed shells."""
+def jk_rows(mol, D, shells, thresh: float | None = None, extended: bool = False):
+    """Rows of J and K for every basis function of the listed shells.
+    ``extended``: every integral and sum in long double (an extended-precision
+    reference on x86, where long double has a 64-bit significand)."""
     v = _MolView(mol)
     D = np.ascontiguousarray(D, dtype=np.float64)
     shells = np.ascontiguousarray(shells, dtype=np.int32)
     nrow = int(sum((int(mol.shell_l[s]) + 1) * (int(mol.shell_l[s]) + 2) // 2 for s in shells))
     Jr = np.zeros((nrow, v.nbf))
     Kr = np.zeros((nrow, v.nbf))
-    rc = _load().orc_jk_rows(v.ref(), _dp(D), float(thresh or 0.0), int(shells.shape[0]), _ip(shells), _dp(Jr), _dp(Kr))
+    fn = _load().orc_jk_rows_ld if extended else _load().orc_jk_rows
+    rc = fn(v.ref(), _dp(D), float(thresh or 0.0), int(shells.shape[0]), _ip(shells), _dp(Jr), _dp(Kr))
     if rc != 0:
         raise ValueError("bad row shell")
     return Jr, Kr

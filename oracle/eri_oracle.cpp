@@ -46,6 +46,7 @@ typedef struct {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr long double kPiL = 3.14159265358979323846264338327950288L;
 constexpr int kLmax = 8;  // per shell, gradients included (l <= 3 shells + 1, with margin)
 
 inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
@@ -76,22 +77,28 @@ inline int gidx(const int* x) { return cumoff(x[0] + x[1] + x[2]) + cidx(x[0], x
 // evaluated separately for every m (all terms positive, no cancellation).
 // T >= 30: F_0 = sqrt(pi/T) erf(sqrt(T)) / 2 and the upward recursion
 // F_{m+1} = ((2m+1) F_m - exp(-T)) / (2T), stable for large T.
-void boys(int mmax, double T, double* F) {
-    if (T < 30.0) {
-        const double eT = std::exp(-T);
+template <class R>
+void boys(int mmax, R T, R* F) {
+    if (T < R(30)) {
+        const R eT = std::exp(-T);
         for (int m = 0; m <= mmax; ++m) {
-            double term = 1.0 / (2 * m + 1), sum = term;
+            // the terms are positive; their sum is compensated (Kahan) so that
+            // the ~100 terms needed near T = 30 do not add up ~100 roundings
+            R term = R(1) / (2 * m + 1), sum = term, comp = R(0);
             for (int k = 1; k < 400; ++k) {
-                term *= 2.0 * T / (2 * m + 2 * k + 1);
-                sum += term;
-                if (term < sum * 1e-18) break;
+                term *= R(2) * T / (2 * m + 2 * k + 1);
+                const R y = term - comp;
+                const R t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+                if (term < sum * R(sizeof(R) > sizeof(double) ? 1e-22 : 1e-18)) break;
             }
             F[m] = eT * sum;
         }
     } else {
-        const double eT = std::exp(-T);
-        F[0] = 0.5 * std::sqrt(kPi / T) * std::erf(std::sqrt(T));
-        for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - eT) / (2.0 * T);
+        const R eT = std::exp(-T);
+        F[0] = R(0.5) * std::sqrt(R(kPiL) / T) * std::erf(std::sqrt(T));
+        for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - eT) / (R(2) * T);
     }
 }
 
@@ -107,21 +114,22 @@ struct Shell {
 //   (a, b + 1_i | = (a + 1_i, b | + (A - B)_i (a, b |
 // in: G[iE][x] for e-shells of total angular momentum la..la+lb (global index
 // minus cumoff(la)); out: H[ia][ib][x].
-void hrr(int la, int lb, const double* AB, const double* G, int X, double* H) {
+template <class R>
+void hrr(int la, int lb, const R* AB, const R* G, int X, R* H) {
     const auto& C = comps();
     const int base = cumoff(la);
     const int nE = cumoff(la + lb + 1) - base;
     if (lb == 0) {
-        std::memcpy(H, G, sizeof(double) * ncart(la) * X);
+        std::memcpy(H, G, sizeof(R) * ncart(la) * X);
         return;
     }
     // level tables: T_j[(a global - base) * ncart(j) + ib][x], a over l in [la, la+lb-j]
-    std::vector<double> prev(G, G + (size_t)nE * X), cur;
+    std::vector<R> prev(G, G + (size_t)nE * X), cur;
     for (int j = 1; j <= lb; ++j) {
         const int nbj = ncart(j), nbm = ncart(j - 1);
         const int amax = la + lb - j;
         const int na_all = cumoff(amax + 1) - base;
-        cur.assign((size_t)na_all * nbj * X, 0.0);
+        cur.assign((size_t)na_all * nbj * X, R(0));
         for (int ib = 0; ib < nbj; ++ib) {
             const Comp& b = C[j][ib];
             int d = b.x[0] > 0 ? 0 : (b.x[1] > 0 ? 1 : 2);
@@ -133,9 +141,9 @@ void hrr(int la, int lb, const double* AB, const double* G, int X, double* H) {
                     int ap[3] = {a.x[0], a.x[1], a.x[2]};
                     ap[d] += 1;
                     const int ia = gidx(a.x) - base, iap = gidx(ap) - base;
-                    double* dst = &cur[((size_t)ia * nbj + ib) * X];
-                    const double* s1 = &prev[((size_t)iap * nbm + ibm) * X];
-                    const double* s2 = &prev[((size_t)ia * nbm + ibm) * X];
+                    R* dst = &cur[((size_t)ia * nbj + ib) * X];
+                    const R* s1 = &prev[((size_t)iap * nbm + ibm) * X];
+                    const R* s2 = &prev[((size_t)ia * nbm + ibm) * X];
                     for (int x = 0; x < X; ++x) dst[x] = s1[x] + AB[d] * s2[x];
                 }
             }
@@ -143,51 +151,56 @@ void hrr(int la, int lb, const double* AB, const double* G, int X, double* H) {
         prev.swap(cur);
     }
     // rows with l == la are the first ncart(la) a-entries
-    std::memcpy(H, prev.data(), sizeof(double) * ncart(la) * ncart(lb) * X);
+    std::memcpy(H, prev.data(), sizeof(R) * ncart(la) * ncart(lb) * X);
 }
 
-struct Work {
-    std::vector<double> V, G, H, T;
+template <class R>
+struct WorkT {
+    std::vector<R> V, G, H, T, K;
 };
+using Work = WorkT<double>;
 
 // Contracted shell quartet (ab|cd), out[ia][ib][ic][id].
-void eri_quartet(const Shell& a, const Shell& b, const Shell& c, const Shell& d, double* out, Work& w) {
+// R is the arithmetic type (double, or long double for the extended-precision
+// reference); the shell data are read as given and converted once.
+template <class R>
+void eri_quartet(const Shell& a, const Shell& b, const Shell& c, const Shell& d, R* out, WorkT<R>& w) {
     const auto& C = comps();
     const int Emax = a.l + b.l, Fmax = c.l + d.l, L = Emax + Fmax;
     const int NI = cumoff(Emax + 1), NJ = cumoff(Fmax + 1);
     const int e0 = cumoff(a.l), ne = NI - e0;
     const int f0 = cumoff(c.l), nf = NJ - f0;
     w.V.resize((size_t)(L + 1) * NI * NJ);
-    w.G.assign((size_t)ne * nf, 0.0);
-    double* V = w.V.data();
-    auto at = [&](int m, int i, int j) -> double& { return V[((size_t)m * NI + i) * NJ + j]; };
-    double AB[3], CD[3];
-    for (int i = 0; i < 3; ++i) { AB[i] = a.R[i] - b.R[i]; CD[i] = c.R[i] - d.R[i]; }
-    const double AB2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
-    const double CD2 = CD[0] * CD[0] + CD[1] * CD[1] + CD[2] * CD[2];
-    double F[2 * (2 * kLmax) + 2];
+    w.G.assign((size_t)ne * nf, R(0));
+    R* V = w.V.data();
+    auto at = [&](int m, int i, int j) -> R& { return V[((size_t)m * NI + i) * NJ + j]; };
+    R AB[3], CD[3];
+    for (int i = 0; i < 3; ++i) { AB[i] = R(a.R[i]) - R(b.R[i]); CD[i] = R(c.R[i]) - R(d.R[i]); }
+    const R AB2 = AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2];
+    const R CD2 = CD[0] * CD[0] + CD[1] * CD[1] + CD[2] * CD[2];
+    R F[2 * (2 * kLmax) + 2];
     for (int ka = 0; ka < a.k; ++ka)
     for (int kb = 0; kb < b.k; ++kb) {
-        const double al = a.e[ka], be = b.e[kb], p = al + be;
-        const double Kab = std::exp(-al * be / p * AB2);
-        double P[3], PA[3];
-        for (int i = 0; i < 3; ++i) { P[i] = (al * a.R[i] + be * b.R[i]) / p; PA[i] = P[i] - a.R[i]; }
+        const R al = a.e[ka], be = b.e[kb], p = al + be;
+        const R Kab = std::exp(-al * be / p * AB2);
+        R P[3], PA[3];
+        for (int i = 0; i < 3; ++i) { P[i] = (al * R(a.R[i]) + be * R(b.R[i])) / p; PA[i] = P[i] - R(a.R[i]); }
         for (int kc = 0; kc < c.k; ++kc)
         for (int kd = 0; kd < d.k; ++kd) {
-            const double ga = c.e[kc], de = d.e[kd], q = ga + de;
-            const double Kcd = std::exp(-ga * de / q * CD2);
-            double Q[3], QC[3], W[3], WP[3], WQ[3], PQ2 = 0.0;
+            const R ga = c.e[kc], de = d.e[kd], q = ga + de;
+            const R Kcd = std::exp(-ga * de / q * CD2);
+            R Q[3], QC[3], W[3], WP[3], WQ[3], PQ2 = 0;
             for (int i = 0; i < 3; ++i) {
-                Q[i] = (ga * c.R[i] + de * d.R[i]) / q;
-                QC[i] = Q[i] - c.R[i];
+                Q[i] = (ga * R(c.R[i]) + de * R(d.R[i])) / q;
+                QC[i] = Q[i] - R(c.R[i]);
                 W[i] = (p * P[i] + q * Q[i]) / (p + q);
                 WP[i] = W[i] - P[i];
                 WQ[i] = W[i] - Q[i];
                 PQ2 += (P[i] - Q[i]) * (P[i] - Q[i]);
             }
-            const double rho = p * q / (p + q);
-            boys(L, rho * PQ2, F);
-            const double pref = 2.0 * std::pow(kPi, 2.5) / (p * q * std::sqrt(p + q)) * Kab * Kcd;
+            const R rho = p * q / (p + q);
+            boys<R>(L, rho * PQ2, F);
+            const R pref = R(2) * std::pow(R(kPiL), R(2.5)) / (p * q * std::sqrt(p + q)) * Kab * Kcd;
             for (int m = 0; m <= L; ++m) at(m, 0, 0) = pref * F[m];
             // electron 1: [e 0|0 0]^(m)
             for (int le = 1; le <= Emax; ++le)
@@ -199,8 +212,8 @@ void eri_quartet(const Shell& a, const Shell& b, const Shell& c, const Shell& d,
                     int ie2 = -1;
                     if (n1 > 0) { int e2[3] = {e1[0], e1[1], e1[2]}; e2[dd] -= 1; ie2 = gidx(e2); }
                     for (int m = 0; m <= L - le; ++m) {
-                        double v = PA[dd] * at(m, ie1, 0) + WP[dd] * at(m + 1, ie1, 0);
-                        if (n1 > 0) v += n1 / (2.0 * p) * (at(m, ie2, 0) - rho / p * at(m + 1, ie2, 0));
+                        R v = PA[dd] * at(m, ie1, 0) + WP[dd] * at(m + 1, ie1, 0);
+                        if (n1 > 0) v += R(n1) / (R(2) * p) * (at(m, ie2, 0) - rho / p * at(m + 1, ie2, 0));
                         at(m, ie, 0) = v;
                     }
                 }
@@ -220,14 +233,14 @@ void eri_quartet(const Shell& a, const Shell& b, const Shell& c, const Shell& d,
                             int ie1 = -1;
                             if (ne1 > 0) { int e1[3] = {e.x[0], e.x[1], e.x[2]}; e1[dd] -= 1; ie1 = gidx(e1); }
                             for (int m = 0; m <= L - le - lf; ++m) {
-                                double v = QC[dd] * at(m, ie, jf1) + WQ[dd] * at(m + 1, ie, jf1);
-                                if (n1 > 0) v += n1 / (2.0 * q) * (at(m, ie, jf2) - rho / q * at(m + 1, ie, jf2));
-                                if (ne1 > 0) v += ne1 / (2.0 * (p + q)) * at(m + 1, ie1, jf1);
+                                R v = QC[dd] * at(m, ie, jf1) + WQ[dd] * at(m + 1, ie, jf1);
+                                if (n1 > 0) v += R(n1) / (R(2) * q) * (at(m, ie, jf2) - rho / q * at(m + 1, ie, jf2));
+                                if (ne1 > 0) v += R(ne1) / (R(2) * (p + q)) * at(m + 1, ie1, jf1);
                                 at(m, ie, jf) = v;
                             }
                         }
                 }
-            const double cc = a.c[ka] * b.c[kb] * c.c[kc] * d.c[kd];
+            const R cc = R(a.c[ka]) * R(b.c[kb]) * R(c.c[kc]) * R(d.c[kd]);
             for (int i = 0; i < ne; ++i)
                 for (int j = 0; j < nf; ++j) w.G[(size_t)i * nf + j] += cc * at(0, e0 + i, f0 + j);
         }
@@ -240,7 +253,8 @@ void eri_quartet(const Shell& a, const Shell& b, const Shell& c, const Shell& d,
     w.T.resize((size_t)nf * na * nb);
     for (int i = 0; i < na * nb; ++i)
         for (int j = 0; j < nf; ++j) w.T[(size_t)j * na * nb + i] = w.H[(size_t)i * nf + j];
-    std::vector<double> ket((size_t)nc * nd * na * nb);
+    std::vector<R>& ket = w.K;
+    ket.resize((size_t)nc * nd * na * nb);
     hrr(c.l, d.l, CD, w.T.data(), na * nb, ket.data());
     for (int i = 0; i < na * nb; ++i)
         for (int j = 0; j < nc * nd; ++j) out[(size_t)i * nc * nd + j] = ket[(size_t)j * na * nb + i];
@@ -257,17 +271,19 @@ std::vector<int> bf_offsets(const orc_mol& m) {
 }
 
 // Neumaier-compensated accumulator array.
-struct CompArr {
-    std::vector<double> s, c;
-    explicit CompArr(size_t n = 0) : s(n, 0.0), c(n, 0.0) {}
-    inline void add(size_t i, double v) {
-        double t = s[i] + v;
+template <class R>
+struct CompArrT {
+    std::vector<R> s, c;
+    explicit CompArrT(size_t n = 0) : s(n, R(0)), c(n, R(0)) {}
+    inline void add(size_t i, R v) {
+        R t = s[i] + v;
         if (std::fabs(s[i]) >= std::fabs(v)) c[i] += (s[i] - t) + v;
         else c[i] += (v - t) + s[i];
         s[i] = t;
     }
-    double get(size_t i) const { return s[i] + c[i]; }
+    R get(size_t i) const { return s[i] + c[i]; }
 };
+using CompArr = CompArrT<double>;
 
 void schwarz_table(const orc_mol& m, std::vector<double>& Q) {
     const int S = m.nshell;
@@ -288,6 +304,56 @@ void schwarz_table(const orc_mol& m, std::vector<double>& Q) {
                 Q[(size_t)a * S + b] = Q[(size_t)b * S + a] = std::sqrt(mx);
             }
     }
+}
+
+template <class R>
+int jk_rows_impl(const orc_mol* m, const double* D, double thresh, int nrows, const int* rows,
+                 double* Jr, double* Kr) {
+    const auto o = bf_offsets(*m);
+    const int S = m->nshell, N = o[S];
+    std::vector<double> Q;
+    if (thresh > 0) schwarz_table(*m, Q);
+    int r0 = 0;
+    for (int r = 0; r < nrows; ++r) {
+        const int a = rows[r];
+        if (a < 0 || a >= S) return -1;
+        const int na = ncart(m->l[a]);
+        CompArrT<R> Jt((size_t)na * N), Kt((size_t)na * N);
+#pragma omp parallel
+        {
+            WorkT<R> w;
+            std::vector<R> blk;
+            CompArrT<R> Jl((size_t)na * N), Kl((size_t)na * N);
+#pragma omp for schedule(dynamic)
+            for (int b = 0; b < S; ++b)
+                for (int c = 0; c < S; ++c)
+                    for (int d = 0; d < S; ++d) {
+                        if (thresh > 0 && Q[(size_t)a * S + b] * Q[(size_t)c * S + d] < thresh) continue;
+                        Shell A = shell_of(*m, a), B = shell_of(*m, b), C = shell_of(*m, c), Dd = shell_of(*m, d);
+                        const int nb = ncart(B.l), nc = ncart(C.l), nd = ncart(Dd.l);
+                        blk.resize((size_t)na * nb * nc * nd);
+                        eri_quartet(A, B, C, Dd, blk.data(), w);
+                        for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
+                        for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
+                            const R v = blk[((i * nb + j) * nc + k) * nd + l];
+                            Jl.add((size_t)i * N + o[b] + j, v * R(D[(size_t)(o[c] + k) * N + o[d] + l]));
+                            Kl.add((size_t)i * N + o[c] + k, v * R(D[(size_t)(o[b] + j) * N + o[d] + l]));
+                        }
+                    }
+#pragma omp critical
+            for (size_t i = 0; i < (size_t)na * N; ++i) {
+                Jt.add(i, Jl.s[i]); Jt.add(i, Jl.c[i]);
+                Kt.add(i, Kl.s[i]); Kt.add(i, Kl.c[i]);
+            }
+        }
+        for (int i = 0; i < na; ++i)
+            for (int j = 0; j < N; ++j) {
+                Jr[(size_t)(r0 + i) * N + j] = (double)Jt.get((size_t)i * N + j);
+                Kr[(size_t)(r0 + i) * N + j] = (double)Kt.get((size_t)i * N + j);
+            }
+        r0 += na;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -495,51 +561,15 @@ long long orc_jk_quartets(const orc_mol* m, const double* D, long long nq, const
 // [sum ncart(rows) x nbf].
 int orc_jk_rows(const orc_mol* m, const double* D, double thresh, int nrows, const int* rows,
                 double* Jr, double* Kr) {
-    const auto o = bf_offsets(*m);
-    const int S = m->nshell, N = o[S];
-    std::vector<double> Q;
-    if (thresh > 0) schwarz_table(*m, Q);
-    int r0 = 0;
-    for (int r = 0; r < nrows; ++r) {
-        const int a = rows[r];
-        if (a < 0 || a >= S) return -1;
-        const int na = ncart(m->l[a]);
-        CompArr Jt((size_t)na * N), Kt((size_t)na * N);
-#pragma omp parallel
-        {
-            Work w;
-            std::vector<double> blk;
-            CompArr Jl((size_t)na * N), Kl((size_t)na * N);
-#pragma omp for schedule(dynamic)
-            for (int b = 0; b < S; ++b)
-                for (int c = 0; c < S; ++c)
-                    for (int d = 0; d < S; ++d) {
-                        if (thresh > 0 && Q[(size_t)a * S + b] * Q[(size_t)c * S + d] < thresh) continue;
-                        Shell A = shell_of(*m, a), B = shell_of(*m, b), C = shell_of(*m, c), Dd = shell_of(*m, d);
-                        const int nb = ncart(B.l), nc = ncart(C.l), nd = ncart(Dd.l);
-                        blk.resize((size_t)na * nb * nc * nd);
-                        eri_quartet(A, B, C, Dd, blk.data(), w);
-                        for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
-                        for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
-                            const double v = blk[((i * nb + j) * nc + k) * nd + l];
-                            Jl.add((size_t)i * N + o[b] + j, v * D[(size_t)(o[c] + k) * N + o[d] + l]);
-                            Kl.add((size_t)i * N + o[c] + k, v * D[(size_t)(o[b] + j) * N + o[d] + l]);
-                        }
-                    }
-#pragma omp critical
-            for (size_t i = 0; i < (size_t)na * N; ++i) {
-                Jt.add(i, Jl.s[i]); Jt.add(i, Jl.c[i]);
-                Kt.add(i, Kl.s[i]); Kt.add(i, Kl.c[i]);
-            }
-        }
-        for (int i = 0; i < na; ++i)
-            for (int j = 0; j < N; ++j) {
-                Jr[(size_t)(r0 + i) * N + j] = Jt.get((size_t)i * N + j);
-                Kr[(size_t)(r0 + i) * N + j] = Kt.get((size_t)i * N + j);
-            }
-        r0 += na;
-    }
-    return 0;
+    return jk_rows_impl<double>(m, D, thresh, nrows, rows, Jr, Kr);
+}
+
+// The same rows with every integral and sum in long double (x86: 64-bit
+// significand): an extended-precision reference for the FP64 rows (the
+// Schwarz screening, from the FP64 Q, is the same).
+int orc_jk_rows_ld(const orc_mol* m, const double* D, double thresh, int nrows, const int* rows,
+                   double* Jr, double* Kr) {
+    return jk_rows_impl<long double>(m, D, thresh, nrows, rows, Jr, Kr);
 }
 
 // E = tr(D J)/2 - tr(D K)/4 with a compensated sum.

@@ -17,9 +17,15 @@ def test_zero_argument():
 
 @pytest.mark.parametrize("T", [1e-8, 1e-3, 0.5, 3.0, 12.5, 29.99, 30.0, 45.0, 120.0])
 def test_f0_closed_form(T):
-    # F_0(T) = sqrt(pi/T) erf(sqrt(T)) / 2
-    ref = 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
-    assert abs(oracle.boys(0, T)[0] - ref) <= 2e-16 * max(1.0, ref) + 1e-16
+    # F_0(T) = sqrt(pi/T) erf(sqrt(T)) / 2, evaluated to 40 digits (the same
+    # closed form in double carries ~2 ulp of its own rounding)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    ref = float(0.5 * mpmath.sqrt(mpmath.pi / T) * mpmath.erf(mpmath.sqrt(T)))
+    assert abs(oracle.boys(0, T)[0] - ref) <= 2e-16 * max(1.0, ref) + 1e-17
+    # and the double closed form within its own rounding
+    ref64 = 0.5 * math.sqrt(math.pi / T) * math.erf(math.sqrt(T))
+    assert abs(oracle.boys(0, T)[0] - ref64) <= 4e-16 * max(1.0, ref64) + 1e-16
 
 
 @pytest.mark.parametrize("T", [1e-6, 0.1, 1.0, 5.0, 17.0, 29.5, 31.0, 60.0])

@@ -101,3 +101,20 @@ def test_h2_sto3g_textbook():
     J, K, _ = oracle.jk(mol, P, mode="all")
     H = S * 0 + T + V
     assert abs(oracle.energy(P, J, K) + float(np.sum(P * H)) - Eel) < 1e-12
+
+
+def test_extended_precision_rows():
+    """The long-double J/K rows (the extended-precision reference the full-size
+    FP64 parity was checked against) agree with the FP64 rows and with the
+    FP64 all-quartet build to FP64 rounding on a small molecule, for s, p and
+    d rows; a wrong conversion or truncated type in the templated path would
+    show here."""
+    mol = _mol(25, [0, 1, 2], natom=3, kmax=3)
+    D = molgen.density(mol, 9)
+    J, K, _ = oracle.jk(mol, D, mode="all")
+    for shells in ([0], [1, 2]):
+        rows = oracle.bf_shell_rows(mol, shells)
+        Jd, Kd = oracle.jk_rows(mol, D, shells)
+        Jl, Kl = oracle.jk_rows(mol, D, shells, extended=True)
+        for X, Y in ((Jl, Jd), (Kl, Kd), (Jl, J[rows]), (Kl, K[rows])):
+            assert np.abs(X - Y).max() <= 1e-13 * np.abs(Y).max()
