@@ -224,7 +224,7 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 
 /* Tunables (process-wide). */
 typedef enum {
-    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
+    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 2e-2) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys of FP32 quartets in FP64 for T < tsmall (default 0:
                                   * measured to change no J/K/E error on the benchmark workloads, while
                                   * the FP64 branch kept the FP32 kernels' FP64 pipe busy) */
@@ -245,7 +245,7 @@ typedef enum {
                                   * the Hermite R recursion in the order found by the greedy path
                                   * search of Algorithm 1 (Sec. 5, Graph Compiler; per kernel the
                                   * lambda of fewest operations) instead of the fixed t-u-v order
-                                  * (default 0).  Same integrals up to rounding. */
+                                  * (default 1; 0: the fixed order).  Same integrals up to rounding. */
     JK_OPT_FAIL_ALLOC_AFTER = 7, /* fault injection for callers' error handling: n >= 0 lets n more
                                   * device allocations of the library succeed, then the next one
                                   * fails with JK_ERR_NOMEM (as if the device were full) and the
@@ -255,7 +255,7 @@ typedef enum {
     JK_OPT_GRAD_TAU = 8          /* mixed gradient (jk_grad with JK_MIXED): derivative integrals in FP32
                                   * for the quartets whose density-weighted bound (as for JK_OPT_MIXED_TAU)
                                   * is below this value, FP64 otherwise; every per-quartet gradient sum
-                                  * is added to dE/dR in FP64 (default 1e-3) */
+                                  * is added to dE/dR in FP64 (default 3e-4) */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);

@@ -145,14 +145,14 @@ std::mutex g_boys_mu;
 BoysTables g_boys[64];
 
 struct Options {
-    double tau = 1e-2;
+    double tau = 2e-2;  // the largest decade step meeting 1e-6 Eh on J, K and E of the 32-atom workload
     double eps = 0.0;  // density screening of mixed builds (0: off)
     double tsmall = 0.0;  // FP32 Boys everywhere in FP32 quartets (the FP64 branch buys no accuracy)
     int check_sym = 0;
     int graph = 1;
     int profile = 0;
-    int rpath = 0;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
-    double grad_tau = 1e-3;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
+    int rpath = 1;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
+    double grad_tau = 3e-4;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
 } g_opt;
 
 struct ProfRec {

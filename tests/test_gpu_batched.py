@@ -51,7 +51,9 @@ def test_batched_matches_oracle_and_single(g, graph):
 def test_batched_mixed(g, graph):
     """The batched mixed form (density-weighted FP64 selection, pre-pass outside
     the captured graph) against FP64 builds, and against the single-molecule
-    mixed path, which selects the same quartets; a second call replays."""
+    mixed path, which selects the same quartets (its FP32 sums are grouped
+    over other warp lanes, so the two agree to FP32 rounding of the small
+    contributions, not bit for bit); a second call replays."""
     g.set_option("graph", graph)
     mols = _mols()
     pairs = [g.ShellPairs(m, 1e-12) for m, _ in mols]
@@ -67,8 +69,8 @@ def test_batched_mixed(g, graph):
                 J1, K1 = g.jk_build(p, Dt, "fp64")
                 assert float((J1 - J).abs().max()) <= 1e-6 and float((K1 - K).abs().max()) <= 1e-6
                 Jm, Km = g.jk_build(p, Dt, "mixed")
-                assert float((Jm - J).abs().max()) <= 1e-10 * max(1.0, float(Jm.abs().max()))
-                assert float((Km - K).abs().max()) <= 1e-10 * max(1.0, float(Km.abs().max()))
+                assert float((Jm - J).abs().max()) <= 1e-8 * max(1.0, float(Jm.abs().max()))
+                assert float((Km - K).abs().max()) <= 1e-8 * max(1.0, float(Km.abs().max()))
     finally:
         g.set_option("graph", 1)
 
