@@ -224,7 +224,7 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 
 /* Tunables (process-wide). */
 typedef enum {
-    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 2e-2) */
+    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys of FP32 quartets in FP64 for T < tsmall (default 0:
                                   * measured to change no J/K/E error on the benchmark workloads, while
                                   * the FP64 branch kept the FP32 kernels' FP64 pipe busy) */
@@ -252,10 +252,15 @@ typedef enum {
                                   * count stays at 0 (every later one fails) until the option is
                                   * set to a negative value (default -1: off).  No device memory
                                   * is touched by an injected failure. */
-    JK_OPT_GRAD_TAU = 8          /* mixed gradient (jk_grad with JK_MIXED): derivative integrals in FP32
+    JK_OPT_GRAD_TAU = 8,         /* mixed gradient (jk_grad with JK_MIXED): derivative integrals in FP32
                                   * for the quartets whose density-weighted bound (as for JK_OPT_MIXED_TAU)
                                   * is below this value, FP64 otherwise; every per-quartet gradient sum
                                   * is added to dE/dR in FP64 (default 3e-4) */
+    JK_OPT_DF_TIER = 9           /* mixed builds (single and batched): nonzero runs the quartets the
+                                  * density-weighted bound keeps out of FP32 (l <= 2 classes) in
+                                  * double-float arithmetic -- every value an unevaluated sum of two
+                                  * floats, ~44 significant bits, all on the FP32 pipe -- instead of
+                                  * FP64 (default 1); the FP64 build is unaffected */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);
@@ -301,8 +306,8 @@ int jk_split_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
 
 /* Launch timings of the last jk_build with JK_OPT_PROFILE set (host,
  * synchronous): up to max_rows rows of 5 doubles: bra class, ket class,
- * precision (0 FP64, 1 FP32), shell quartets, milliseconds (CUDA events on
- * the build's stream).  *nrows receives the number of launches. */
+ * precision (0 FP64, 1 FP32, 3 double-float), shell quartets, milliseconds
+ * (CUDA events on the build's stream).  *nrows receives the number of launches. */
 int jk_profile(jk_pairs pairs, int max_rows, double* rows, int* nrows);
 
 /* Diagnostic microbenchmark: sustained FMA throughput of this GPU's SIMT

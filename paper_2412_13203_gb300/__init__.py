@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgb300eri.so")
 
 JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3, "profile": 4, "density_screen": 5,
-          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8}
+          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8, "df_tier": 9}
 _PREC = {"fp64": 0, "mixed": 1}
 
 _lib = None
@@ -230,6 +230,14 @@ def partition(cost, nparts: int) -> np.ndarray:
     _check(load().jk_partition(int(c.shape[0]), c.ctypes.data_as(C.POINTER(C.c_double)), int(nparts),
                                b.ctypes.data_as(C.POINTER(C.c_int64))))
     return b
+
+
+def prepare_partition(pairs: ShellPairs, nparts: int) -> int:
+    """Compute and cache the handle's row partition for nparts parts (one
+    synchronisation); returns the number of (class, part) entries."""
+    n = C.c_int()
+    _check(load().jk_part_rows(pairs.handle, int(nparts), 0, None, C.byref(n)))
+    return n.value
 
 
 def part_rows(pairs: ShellPairs, nparts: int):
@@ -471,7 +479,8 @@ def profile(pairs: ShellPairs):
     for k in range(min(n.value, 256)):
         r = buf[5 * k:5 * k + 5]
         out.append(dict(cls=PAIR_CLASS_NAMES[int(r[0])] + "|" + PAIR_CLASS_NAMES[int(r[1])], bra=int(r[0]),
-                        ket=int(r[1]), prec="fp64" if r[2] == 0 else "fp32", nquartets=int(r[3]), ms=r[4]))
+                        ket=int(r[1]), prec={0: "fp64", 3: "df"}.get(int(r[2]), "fp32"), nquartets=int(r[3]),
+                        ms=r[4]))
     return out
 
 

@@ -90,6 +90,18 @@ class Sym:
 ONE = Sym(1.0)
 ZERO = Sym(0.0)
 
+DFL = "gb::dfl"  # double-float value type of the device header (hi + lo floats)
+
+
+def df_literal(c):
+    """A constant as a double-float literal: hi the nearest float, lo the
+    nearest float to the remainder (split here, so no FP64 operation is emitted)."""
+    import struct
+    f32 = lambda x: struct.unpack("f", struct.pack("f", x))[0]
+    hi = f32(float(c))
+    lo = f32(float(c) - hi)
+    return f"{DFL}({hi!r}f, {lo!r}f)" if lo != 0.0 else f"{DFL}({hi!r}f)"
+
 
 class Emitter:
     def __init__(self, real):
@@ -100,6 +112,8 @@ class Emitter:
     def lit(self, c):
         if self.real == "float":
             return f"{c!r}f" if not float(c).is_integer() else f"{float(c):.1f}f"
+        if self.real == DFL:
+            return df_literal(c)
         return repr(float(c))
 
     def val(self, s: Sym):
@@ -350,6 +364,8 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     assert mode_flat or len(cds) == NCD
     NS = len(cds)  # ket component pairs computed here
     f32 = real == "float"
+    dfm = real == DFL        # double-float: FP32-pipe arithmetic, FP32-style scaled R and folded prefactors
+    sc = f32 or dfm
     em = Emitter(real)
     hb = herm(la + lb)
     hbi = hidx(hb)
@@ -367,7 +383,14 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
         E(f"{real} Xl[{HAB * NCD}];")
         E(f"{real} Rc[{L1 * L1 * L1}];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
-    if f32:
+    if dfm:
+        E("const float4* pd_ = pairs.ppd + 5 * (ib.w + ip);")
+        E("const float4 u0 = pd_[0], u1 = pd_[1], u2 = pd_[2], u3 = pd_[3], u4 = pd_[4];")
+        E("const gb::dfl PAx(u0.x, u0.y), PAy(u0.z, u0.w), PAz(u1.x, u1.y);")
+        E("const gb::dfl PBx(u1.z, u1.w), PBy(u2.x, u2.y), PBz(u2.z, u2.w);")
+        E("const gb::dfl p(u3.x, u3.y), kp(u3.z, u3.w), inv2p(u4.x, u4.y);")
+        E("const gb::dfl PCx = PAx + ACx, PCy = PAy + ACy, PCz = PAz + ACz;  // P - C")
+    elif f32:
         # P - A, P - B and A - C were formed in FP64 and rounded once
         E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
         E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
@@ -387,7 +410,13 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     else:
         E(f"for (int i = 0; i < {HAB * NCD}; ++i) Xl[i] = 0;")
     E("for (int jq = 0; jq < ik.z; ++jq) {")
-    if f32:
+    if dfm:
+        E("const float4* qd_ = pairs.ppd + 5 * (ik.w + jq);")
+        E("const float4 w0 = qd_[0], w1 = qd_[1], w2 = qd_[2], w3 = qd_[3], w4 = qd_[4];")
+        E("const gb::dfl QCx(w0.x, w0.y), QCy(w0.z, w0.w), QCz(w1.x, w1.y);")
+        E("const gb::dfl QDx(w1.z, w1.w), QDy(w2.x, w2.y), QDz(w2.z, w2.w);")
+        E("const gb::dfl q(w3.x, w3.y), kq(w3.z, w3.w), inv2q(w4.x, w4.y);")
+    elif f32:
         E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
         E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q);")
         E("const float QCx = qa.x, QCy = qa.y, QCz = qa.z;")
@@ -402,39 +431,44 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     Ekx = gen_E_axis(em, "ekx", lc, ld, Sym(name="QCx"), Sym(name="QDx"), inv2q, sign=True)
     Eky = gen_E_axis(em, "eky", lc, ld, Sym(name="QCy"), Sym(name="QDy"), inv2q, sign=True)
     Ekz = gen_E_axis(em, "ekz", lc, ld, Sym(name="QCz"), Sym(name="QDz"), inv2q, sign=True)
-    if f32:
-        E("const float PQx = PCx - QCx, PQy = PCy - QCy, PQz = PCz - QCz;")
+    if sc:
+        E(f"const {real} PQx = PCx - QCx, PQy = PCy - QCy, PQz = PCz - QCz;")
     else:
         E(f"const {real} PQx = pa.x - qa.x, PQy = pa.y - qa.y, PQz = pa.z - qa.z;")
-    if f32:
+    if dfm:
+        E("const gb::dfl rs = gb::df_rsqrt(p + q);")
+        E("const gb::dfl kqrs = kq * rs;")
+    elif f32:
         E("const float rs = rsqrtf(p + q);")
         E("const float kqrs = kq * rs;")
     else:
         E("const double rs = rsqrt(p + q);")
     if mode_flat:
-        kprod = gen_products(em, "ek", lc, ld, Ekx, Eky, Ekz, Sym(name="kqrs") if f32 else None)
+        kprod = gen_products(em, "ek", lc, ld, Ekx, Eky, Ekz, Sym(name="kqrs") if sc else None)
     flops_eket = em.flops
     em.flops = 0
     E(f"const {real} rho = p * q * rs * rs;")
     E(f"const {real} T = rho * (PQx * PQx + PQy * PQy + PQz * PQz);")
-    if f32:
-        E("const float r2 = 2.0f * rho;")
-        E("const float PQsx = r2 * PQx, PQsy = r2 * PQy, PQsz = r2 * PQz;")
+    if sc:
+        E(f"const {real} r2 = rho + rho;")
+        E(f"const {real} PQsx = r2 * PQx, PQsy = r2 * PQy, PQsz = r2 * PQz;")
         for a in range(1, L):
-            E(f"const float r2k{a} = {float(a)!r}f * r2;")
+            E(f"const {real} r2k{a} = {float(a)!r}f * r2;")
     else:
         E(f"const {real} pref = kp * kq * rs;")
         E(f"const {real} m2r = -2 * rho;")
     E(f"{real} F[{L + 1}];")
-    if f32:
+    if dfm:
+        E(f"gb::boys_df<{L}>(T, F, boysd);")
+    elif f32:
         E(f"gb::boys_mixed<{L}>(T, F, boys, boysf, tsmall);")
     else:
         E(f"gb::boys_f64<{L}>(T, F, boys);")
     flops_setup = 16 + (kBoysCost(L))
     lam = rpath if rpath is not None else R_PATH_LAMBDA
     if mode_flat and lam is not None:
-        R = gen_R_path(em, L, r_targets(bra, ket, cds), f32, lam)
-    elif f32:
+        R = gen_R_path(em, L, r_targets(bra, ket, cds), sc, lam)
+    elif sc:
         R = gen_R_scaled(em, L, "F", ("PQsx", "PQsy", "PQsz"), "r2k")
     else:
         R = gen_R(em, L, "pref", "m2r", "F", ("PQx", "PQy", "PQz"))
@@ -467,7 +501,7 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
         for h in range(HAB):
             E(f"{real} xh{h} = Xl[{h} * {NCD} + cd];")
         E("for (int tau = 0; tau <= cx + dx; ++tau) {")
-        E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {lc + ld + 1} + tau]{' * kqrs' if f32 else ''};")
+        E(f"const {real} ex = ekxa[(cx * {ld + 1} + dx) * {lc + ld + 1} + tau]{' * kqrs' if sc else ''};")
         E("for (int nu = 0; nu <= cy + dy; ++nu) {")
         E(f"const {real} exy = ex * ekya[(cy * {ld + 1} + dy) * {lc + ld + 1} + nu];")
         E("for (int phi = 0; phi <= cz + dz; ++phi) {")
@@ -489,7 +523,7 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     Ebx = gen_E_axis(em, "ebx", la, lb, Sym(name="PAx"), Sym(name="PBx"), inv2p)
     Eby = gen_E_axis(em, "eby", la, lb, Sym(name="PAy"), Sym(name="PBy"), inv2p)
     Ebz = gen_E_axis(em, "ebz", la, lb, Sym(name="PAz"), Sym(name="PBz"), inv2p)
-    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz, Sym(name="kp") if f32 else None)
+    bprod = gen_products(em, "eb", la, lb, Ebx, Eby, Ebz, Sym(name="kp") if sc else None)
     flops_ebra = em.flops
     # bra transform
     em.flops = 0
@@ -771,8 +805,9 @@ def gen_class_kernels(bra, ket):
     P = split_of(bra, ket)    # bra primitive pairs of a quartet spread over up to P threads
     out = []
     stats = None
-    for prec, real in (("f64", "double"), ("f32", "float")):
-        flat = use_flat(bra, ket, prec)
+    precs = [("f64", "double"), ("f32", "float")] + ([("df", DFL)] if has_df(bra, ket) else [])
+    for prec, real in precs:
+        flat = use_flat(bra, ket, "f64" if prec == "df" else prec)
         name = class_name(bra, ket)
         # warp-run pre-reduction of the digestion (FP32 flat and range kernels):
         # J'_ab over the lanes of a row, the other targets over the lanes of a
@@ -816,6 +851,14 @@ def gen_class_kernels(bra, ket):
                        "  const float ACx = (ah.x - ch.x) + (al.x - cl.x), ACy = (ah.y - ch.y) + (al.y - cl.y),\n"
                        "              ACz = (ah.z - ch.z) + (al.z - cl.z);")
             dmat = "Dfm"
+        elif real == DFL:
+            centres = ("  const float4 ah = pairs.Ahl[2 * bra], al = pairs.Ahl[2 * bra + 1];\n"
+                       "  const float4 ch = pairs.Ahl[2 * ket], cl = pairs.Ahl[2 * ket + 1];\n"
+                       "  // A - C in double-float from the split centres\n"
+                       "  const gb::dfl ACx = (gb::dfl(ah.x) - gb::dfl(ch.x)) + (gb::dfl(al.x) - gb::dfl(cl.x));\n"
+                       "  const gb::dfl ACy = (gb::dfl(ah.y) - gb::dfl(ch.y)) + (gb::dfl(al.y) - gb::dfl(cl.y));\n"
+                       "  const gb::dfl ACz = (gb::dfl(ah.z) - gb::dfl(ch.z)) + (gb::dfl(al.z) - gb::dfl(cl.z));")
+            dmat = "Ddm"
         else:
             centres = "  const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];"
             dmat = "Dm"
@@ -857,8 +900,9 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   const long long total = (args.rows.start[args.rows.nrows] - base) * {nch};
   const double* __restrict__ boys = args.boys;
   const float* __restrict__ boysf = args.boysf;
+  const float2* __restrict__ boysd = args.boysd;
   const float tsmall = args.tsmall;
-  (void)boysf; (void)tsmall;
+  (void)boys; (void)boysf; (void)boysd; (void)tsmall;
 {loop_head}
   const long long qq = rt / {nch};
   const int ci = (int)(rt - qq * {nch});
@@ -871,15 +915,16 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   gb::PairsView pairs = args.pairs;
   const double* Dm = args.D;
   const float* Dfm = args.Df;
+  const gb::dfl* Ddm = args.Ddf;
   double* Jm = args.J;
   double* Km = args.K;
   double* Jlm = args.Jlo;
   double* Klm = args.Klo;
   int nbf = args.nbf;
-  (void)Dm; (void)Dfm; (void)Jlm; (void)Klm;
+  (void)Dm; (void)Dfm; (void)Ddm; (void)Jlm; (void)Klm;
   if (args.mols) {{
     const gb::BatchMol& bm = args.mols[args.row_mol[row]];
-    pairs = bm.pairs; Dm = bm.D; Dfm = bm.Df; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
+    pairs = bm.pairs; Dm = bm.D; Dfm = bm.Df; Ddm = bm.Ddf; Jm = bm.J; Km = bm.K; nbf = bm.nbf;
     Jlm = bm.Jlo; Klm = bm.Klo;
   }}
   const int4 ib = pairs.info[bra];
@@ -1334,6 +1379,13 @@ def r_path(targets, lam=None, rng=None):
     return chosen
 
 
+def has_df(bra, ket):
+    """Classes that also carry a double-float kernel (the mixed build's
+    largest-bound quartets): every l <= 2 class (the f classes' chunked form
+    keeps FP64)."""
+    return max(bra + ket) <= 2
+
+
 # Warp-run pre-reduction of the digestion per precision (flat and range
 # digestion forms; see gb::WarpSeg).
 WARP_DIGEST = {"f32": True, "f64": False}
@@ -1477,11 +1529,14 @@ def generate(outdir, lmax=LMAX, nfiles=None):
             if (bra, ket) in RPATH_CLASSES and crange_groups(bra, ket):
                 rl = "\n".join(f"    eri_jk_{name}_f32r_c{c0}<<<grid, block, 0, s>>>(a);" for c0, _ in crange_groups(bra, ket))
                 rpath = f"  else if (prec == 2) {{  // FP32, Algorithm 1's recursion order\n{rl}\n  }}\n"
+            dfl_launch = (f"  else if (prec == 3) eri_jk_{name}_df<<<grid, block, 0, s>>>(a);  // double-float\n"
+                          if has_df(bra, ket) else
+                          f"  else if (prec == 3) eri_jk_{name}_f64<<<grid, block, 0, s>>>(a);  // no double-float form\n")
             src.append(f"""
 int launch_jk_{name}(int prec, const gb::JKArgs& a, int grid, int block, cudaStream_t s) {{
   if (grid <= 0) return 0;
   if (prec == 0) eri_jk_{name}_f64<<<grid, block, 0, s>>>(a);
-{rpath}  else {{
+{dfl_launch}{rpath}  else {{
 {f32_launches}
   }}
   return (int)cudaGetLastError();

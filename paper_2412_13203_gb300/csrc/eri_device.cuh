@@ -4,8 +4,71 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace gb {
+
+// ------------------------------------------------------------------ double-float
+// A value carried as an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// about 44 significant bits, with every operation on the FP32 pipe: the
+// mixed build's largest-bound quartets run in it instead of FP64 (the GB300's
+// FP64 rate is 1/64 of its FP32 rate).  Sums use Knuth's two-sum on the high
+// parts, products the FMA-exact product of the high parts (Dekker/Knuth
+// error-free transformations); the low parts are added without their own
+// error terms, which bounds every operation's error by ~2^-44 of its operands.
+struct dfl {
+    float hi, lo;
+    __host__ __device__ constexpr dfl(float h = 0.f, float l = 0.f) : hi(h), lo(l) {}
+    __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}
+    dfl(double) = delete;  // a double would lose its low bits silently: split it with df_const
+    explicit __host__ __device__ operator double() const { return (double)hi + (double)lo; }
+};
+
+// hi + lo split of a double (compile-time constants and host / setup code)
+__host__ __device__ constexpr dfl df_const(double x) { return dfl((float)x, (float)(x - (double)(float)x)); }
+
+// the global fma overloads stay visible next to the double-float one below
+using ::fma;
+using ::fmaf;
+
+__device__ __forceinline__ dfl df_norm(float s, float e) {  // fast two-sum, |s| >= |e|
+    const float h = s + e;
+    return dfl(h, e - (h - s));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    return df_norm(s, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dfl operator*(dfl a, float b) {
+    const float p = a.hi * b;
+    return df_norm(p, fmaf(a.lo, b, fmaf(a.hi, b, -p)));
+}
+__device__ __forceinline__ dfl operator*(float a, dfl b) { return b * a; }
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { a = a + b; return a; }
+__device__ __forceinline__ dfl& operator*=(dfl& a, dfl b) { a = a * b; return a; }
+__device__ __forceinline__ dfl& operator*=(dfl& a, float b) { a = a * b; return a; }
+__device__ __forceinline__ bool operator==(dfl a, float b) { return a.hi == b && a.lo == 0.f; }
+__device__ __forceinline__ dfl fma(dfl a, dfl b, dfl c) { return a * b + c; }
+__device__ __forceinline__ dfl df_rsqrt(dfl x) {
+    // rsqrtf of the high part, then one Newton step in double-float
+    const dfl r(rsqrtf(x.hi));
+    return r + r * (dfl(0.5f) - (x * (r * r)) * 0.5f);
+}
+template <class T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+__device__ __forceinline__ dfl ldg(const dfl* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return dfl(v.x, v.y);
+}
 
 constexpr int kLmaxShell = 3;
 constexpr int kLmaxBoys = 4 * kLmaxShell + 1;  // highest F_m needed (gradients of (ff|ff))
@@ -41,6 +104,9 @@ struct PairsView {
     // (float)A, [2i + 1] = lo = (float)(A - hi): FP32 kernels form A - C as
     // (hi_A - hi_C) + (lo_A - lo_C) without an FP64 operation
     const float4* Ahl;
+    // per primitive pair, double-float kernels: 5 float4 = (P-A)x,(P-A)y | (P-A)z,(P-B)x |
+    // (P-B)y,(P-B)z | p, kappa | 1/(2p), - (each value as hi, lo; differences formed in FP64)
+    const float4* ppd;
 };
 
 struct RowsView {
@@ -57,6 +123,7 @@ struct BatchMol {
     PairsView pairs;
     const double* D;
     float* Df;                // FP32 copy of D (mixed builds; written by the max|D| pass)
+    dfl* Ddf;                 // double-float copy of D (mixed builds)
     float* Dsh;               // mixed builds: max |D| per shell block [nshell^2]
     const int* bf_shell;      // shell of every basis function
     const int2* psh;          // shells a, b of every kept pair
@@ -76,6 +143,8 @@ struct JKArgs {
     float tsmall;             // mixed kernels: FP64 Boys below this T
     const double* D;
     const float* Df;          // FP32 copy of D (mixed builds: digestion of the FP32 quartets)
+    const dfl* Ddf;           // double-float copy of D (mixed builds: digestion of the double-float quartets)
+    const float2* boysd;      // double-float Boys table (hi, lo of the FP64 table)
     double* J;                // accumulates J' (J = J' + J'^T afterwards)
     double* K;                // accumulates K'
     double* Jlo;              // FP64 builds: remainders of the split accumulation (see jk_add);
@@ -168,6 +237,45 @@ __device__ __forceinline__ void boys_f32(float T, float* F, const float* __restr
     }
 }
 
+// Double-float evaluation (the double-float quartets of a mixed build): the
+// FP64 table's values split into hi + lo, the same Taylor series, downward
+// recursion and asymptotic form, every operation on the FP32 pipe.
+// 1/(2m+1) as double-float constants (the downward recursion of boys_df)
+static __constant__ dfl kInvOddDf[kLmaxBoys + 1] = {
+    df_const(1.0), df_const(1.0 / 3), df_const(1.0 / 5), df_const(1.0 / 7), df_const(1.0 / 9),
+    df_const(1.0 / 11), df_const(1.0 / 13), df_const(1.0 / 15), df_const(1.0 / 17), df_const(1.0 / 19),
+    df_const(1.0 / 21), df_const(1.0 / 23), df_const(1.0 / 25), df_const(1.0 / 27)};
+
+template <int L>
+__device__ __forceinline__ void boys_df(dfl T, dfl* F, const float2* __restrict__ tab) {
+    if (T.hi < (float)kBoysTmax) {
+        const int k = __float2int_rn(T.hi * kBoysPerUnit);
+        const dfl d = dfl(k * (1.0f / kBoysPerUnit)) - T;  // the grid point is exact in FP32
+        const float2* c = tab + ((size_t)k * kBoysRows + L) * kBoysTaylor;
+        float2 cv = __ldg(c + kBoysTaylor - 1);
+        dfl f(cv.x, cv.y);
+#pragma unroll
+        for (int j = kBoysTaylor - 2; j >= 0; --j) { cv = __ldg(c + j); f = fma(f, d, dfl(cv.x, cv.y)); }
+        F[L] = f;
+        if (L > 0) {
+            const float2* e = tab + ((size_t)k * kBoysRows + kLmaxBoys + 1) * kBoysTaylor;
+            cv = __ldg(e + kBoysTaylor - 1);
+            dfl eT(cv.x, cv.y);
+#pragma unroll
+            for (int j = kBoysTaylor - 2; j >= 0; --j) { cv = __ldg(e + j); eT = fma(eT, d, dfl(cv.x, cv.y)); }
+            const dfl t2 = T + T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], eT) * kInvOddDf[m];
+        }
+    } else {
+        const dfl r = df_rsqrt(T);
+        F[0] = r * dfl(0.886226952f, -2.66231996e-08f);  // sqrt(pi)/2 / sqrt(T), hi + lo
+        const dfl h = (r * r) * 0.5f;                 // 1 / (2T)
+#pragma unroll
+        for (int m = 0; m < L; ++m) F[m + 1] = F[m] * (h * (float)(2 * m + 1));
+    }
+}
+
 // Mixed precision: FP64 evaluation below tsmall, FP32 above.
 template <int L>
 __device__ __forceinline__ void boys_mixed(float T, float* F, const double* __restrict__ tab,
@@ -210,7 +318,7 @@ constexpr double kSplitC = 1572864.0;  // 1.5 * 2^20: ulp 2^-32
 
 template <class R>
 __device__ __forceinline__ void jk_add(double* X, double* lo, size_t i, double v) {
-    if constexpr (sizeof(R) == sizeof(double)) {
+    if constexpr (std::is_same<R, double>::value) {
         if (lo) {
             const double vh = __dsub_rn(__dadd_rn(v, kSplitC), kSplitC);
             atomicAdd(X + i, vh);
@@ -307,7 +415,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int c = 0; c < NC; ++c)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fc + c) * n + fd + d), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fc + c) * n + fd + d), v);
             jk_put<R, WR>(J, Jlo, (size_t)(fa + a) * n + fb + b, v + v, ws, true);
         }
     // J'_cd
@@ -320,7 +428,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fb + b), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fa + a) * n + fb + b), v);
             jk_put<R, WQ>(J, Jlo, (size_t)(fc + c) * n + fd + d, v + v, ws, false);
         }
     // K'_ac and K'_ad
@@ -333,7 +441,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fb + b) * n + fd + d), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fc + c, v, ws, false);
         }
 #pragma unroll
@@ -343,7 +451,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int b = 0; b < NB; ++b)
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fb + b) * n + fc + c), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fd + d, v, ws, false);
         }
     }
@@ -357,7 +465,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fa + a) * n + fd + d), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fc + c, v, ws, false);
         }
 #pragma unroll
@@ -367,7 +475,7 @@ __device__ __forceinline__ void digest(const R* acc, int fa, int fb, int fc, int
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int c = 0; c < NC; ++c)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fa + a) * n + fc + c), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fd + d, v, ws, false);
         }
     }
@@ -392,7 +500,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int c = C0; c < C1; ++c)
 #pragma unroll
-                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fc + c) * n + fd + d), v);
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fc + c) * n + fd + d), v);
             jk_put<R, WR>(J, Jlo, (size_t)(fa + a) * n + fb + b, v + v, ws, true);
         }
 #pragma unroll
@@ -403,7 +511,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
-                for (int b = 0; b < NB; ++b) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fb + b), v);
+                for (int b = 0; b < NB; ++b) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fa + a) * n + fb + b), v);
             jk_put<R, WQ>(J, Jlo, (size_t)(fc + c) * n + fd + d, v + v, ws, false);
         }
 #pragma unroll
@@ -414,7 +522,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
-                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fd + d), v);
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fb + b) * n + fd + d), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fc + c, v, ws, false);
         }
 #pragma unroll
@@ -423,7 +531,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
-                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fb + b) * n + fc + c), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fa + a) * n + fd + d, v, ws, false);
         }
     }
@@ -435,7 +543,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
-                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+                for (int d = 0; d < ND; ++d) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fa + a) * n + fd + d), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fc + c, v, ws, false);
         }
 #pragma unroll
@@ -444,7 +552,7 @@ __device__ __forceinline__ void digest_crange(const R* acc, int fa, int fb, int 
 #pragma unroll
             for (int a = 0; a < NA; ++a)
 #pragma unroll
-                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+                for (int c = C0; c < C1; ++c) v = fma(GB_ACC(a, b, c, d), ldg(D + (size_t)(fa + a) * n + fc + c), v);
             jk_put<R, WQ>(K, Klo, (size_t)(fb + b) * n + fd + d, v, ws, false);
         }
     }
@@ -463,7 +571,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
         const int a = ab / NB, b = ab % NB;
         R v = 0;
         for (int cd = 0; cd < NC * ND; ++cd)
-            v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fc + cd / ND) * n + fd + cd % ND), v);
+            v = fma(acc[ab * NC * ND + cd], ldg(D + (size_t)(fc + cd / ND) * n + fd + cd % ND), v);
         jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
     }
 #pragma unroll 1
@@ -471,7 +579,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
         const int c = cd / ND, d = cd % ND;
         R v = 0;
         for (int ab = 0; ab < NA * NB; ++ab)
-            v = fma(acc[ab * NC * ND + cd], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
+            v = fma(acc[ab * NC * ND + cd], ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
         jk_add<R>(J, Jlo, (size_t)(fc + c) * n + fd + d, (double)(v + v));
     }
 #pragma unroll 1
@@ -481,7 +589,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             R vac = 0;
             for (int b = 0; b < NB; ++b)
                 for (int d = 0; d < ND; ++d)
-                    vac = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
+                    vac = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fb + b) * n + fd + d), vac);
             jk_add<R>(K, Klo, (size_t)(fa + a) * n + fc + c, (double)vac);
         }
 #pragma unroll 1
@@ -491,7 +599,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             R v = 0;
             for (int b = 0; b < NB; ++b)
                 for (int c = 0; c < NC; ++c)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fb + b) * n + fc + c), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fb + b) * n + fc + c), v);
             jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
 #pragma unroll 1
@@ -501,7 +609,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             R v = 0;
             for (int a = 0; a < NA; ++a)
                 for (int d = 0; d < ND; ++d)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fa + a) * n + fd + d), v);
             jk_add<R>(K, Klo, (size_t)(fb + b) * n + fc + c, (double)v);
         }
 #pragma unroll 1
@@ -511,7 +619,7 @@ __device__ __forceinline__ void digest_loop(const R* acc, int fa, int fb, int fc
             R v = 0;
             for (int a = 0; a < NA; ++a)
                 for (int c = 0; c < NC; ++c)
-                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], __ldg(D + (size_t)(fa + a) * n + fc + c), v);
+                    v = fma(acc[((a * NB + b) * NC + c) * ND + d], ldg(D + (size_t)(fa + a) * n + fc + c), v);
             jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
 }
@@ -529,14 +637,14 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
     for (int ab = 0; ab < NA * NB; ++ab) {  // J'_ab
         const int a = ab / NB, b = ab % NB;
         R v = 0;
-        for (int d = 0; d < ND; ++d) v = fma(acc[ab * ND + d], __ldg(D + (size_t)c * n + fd + d), v);
+        for (int d = 0; d < ND; ++d) v = fma(acc[ab * ND + d], ldg(D + (size_t)c * n + fd + d), v);
         jk_add<R>(J, Jlo, (size_t)(fa + a) * n + fb + b, (double)(v + v));
     }
 #pragma unroll 1
     for (int d = 0; d < ND; ++d) {  // J'_cd
         R v = 0;
         for (int ab = 0; ab < NA * NB; ++ab)
-            v = fma(acc[ab * ND + d], __ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
+            v = fma(acc[ab * ND + d], ldg(D + (size_t)(fa + ab / NB) * n + fb + ab % NB), v);
         jk_add<R>(J, Jlo, (size_t)c * n + fd + d, (double)(v + v));
     }
 #pragma unroll 1
@@ -544,11 +652,11 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
         R vac = 0;  // K'_ac
         for (int b = 0; b < NB; ++b)
             for (int d = 0; d < ND; ++d)
-                vac = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + fd + d), vac);
+                vac = fma(acc[(a * NB + b) * ND + d], ldg(D + (size_t)(fb + b) * n + fd + d), vac);
         jk_add<R>(K, Klo, (size_t)(fa + a) * n + c, (double)vac);
         for (int d = 0; d < ND; ++d) {  // K'_ad
             R v = 0;
-            for (int b = 0; b < NB; ++b) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fb + b) * n + c), v);
+            for (int b = 0; b < NB; ++b) v = fma(acc[(a * NB + b) * ND + d], ldg(D + (size_t)(fb + b) * n + c), v);
             jk_add<R>(K, Klo, (size_t)(fa + a) * n + fd + d, (double)v);
         }
     }
@@ -557,11 +665,11 @@ __device__ __forceinline__ void digest_chunk(const R* acc, int ci, int fa, int f
         R vbc = 0;  // K'_bc
         for (int a = 0; a < NA; ++a)
             for (int d = 0; d < ND; ++d)
-                vbc = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + fd + d), vbc);
+                vbc = fma(acc[(a * NB + b) * ND + d], ldg(D + (size_t)(fa + a) * n + fd + d), vbc);
         jk_add<R>(K, Klo, (size_t)(fb + b) * n + c, (double)vbc);
         for (int d = 0; d < ND; ++d) {  // K'_bd
             R v = 0;
-            for (int a = 0; a < NA; ++a) v = fma(acc[(a * NB + b) * ND + d], __ldg(D + (size_t)(fa + a) * n + c), v);
+            for (int a = 0; a < NA; ++a) v = fma(acc[(a * NB + b) * ND + d], ldg(D + (size_t)(fa + a) * n + c), v);
             jk_add<R>(K, Klo, (size_t)(fb + b) * n + fd + d, (double)v);
         }
     }

@@ -138,20 +138,21 @@ struct ClassRows {
 
 // Boys tables (one set per device, built on first use).
 struct BoysTables {
-    DevBuf tab, tabf;
+    DevBuf tab, tabf, tabd;  // FP64, FP32, double-float (hi, lo of FP64)
     bool ready = false;
 };
 std::mutex g_boys_mu;
 BoysTables g_boys[64];
 
 struct Options {
-    double tau = 2e-2;  // the largest decade step meeting 1e-6 Eh on J, K and E of the 32-atom workload
+    double tau = 1e-2;  // meets 1e-6 Eh on J, K and E of the 32-atom workload and of the 64 batch molecules
     double eps = 0.0;  // density screening of mixed builds (0: off)
     double tsmall = 0.0;  // FP32 Boys everywhere in FP32 quartets (the FP64 branch buys no accuracy)
     int check_sym = 0;
     int graph = 1;
     int profile = 0;
     int rpath = 1;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
+    int df_tier = 1;   // mixed builds: the FP64-selected quartets in double-float arithmetic
     double grad_tau = 3e-4;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
 } g_opt;
 
@@ -171,6 +172,8 @@ struct jk_pairs_s {
     double thresh = 0.0, Qmax = 0.0;
     DevBuf info, A, B, pp, pp2, ppf, ppf2;          // sorted, kept pairs
     DevBuf Ahl;                                     // float4 x 2 per pair: centre of a as hi + lo floats
+    DevBuf ppd;                                     // float4 x 5 per primitive pair: double-float data
+    DevBuf Ddf;                                     // double-float copy of the last mixed build's D
     DevBuf Df;                                      // FP32 copy of the last mixed build's D
     DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
     DevBuf pair_atoms;                              // int2 per pair: atoms of shells a, b
@@ -238,7 +241,7 @@ __global__ void k_boys_raw(double* raw, int nm) {
     raw[idx] = exp(-T) * sum;
 }
 
-__global__ void k_boys_fill(const double* raw, int nm, double* tab, float* tabf) {
+__global__ void k_boys_fill(const double* raw, int nm, double* tab, float* tabf, float2* tabd) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int per = gb::kBoysRows * gb::kBoysTaylor;
     if (idx >= gb::kBoysNgrid * per) return;
@@ -253,6 +256,7 @@ __global__ void k_boys_fill(const double* raw, int nm, double* tab, float* tabf)
     }
     tab[idx] = v;
     tabf[idx] = (float)v;
+    tabd[idx] = make_float2((float)v, (float)(v - (double)(float)v));
 }
 
 int ensure_boys(int dev, cudaStream_t st) {
@@ -267,9 +271,11 @@ int ensure_boys(int dev, cudaStream_t st) {
     const size_t n = (size_t)gb::kBoysNgrid * gb::kBoysRows * gb::kBoysTaylor;
     if ((rc = b.tab.alloc(sizeof(double) * n))) return rc;
     if ((rc = b.tabf.alloc(sizeof(float) * n))) return rc;
+    if ((rc = b.tabd.alloc(sizeof(float2) * n))) return rc;
     k_boys_raw<<<(gb::kBoysNgrid * nm + 127) / 128, 128, 0, st>>>(raw.as<double>(), nm);
     CKL();
-    k_boys_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw.as<double>(), nm, b.tab.as<double>(), b.tabf.as<float>());
+    k_boys_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw.as<double>(), nm, b.tab.as<double>(), b.tabf.as<float>(),
+                                                            b.tabd.as<float2>());
     CKL();
     CK(cudaStreamSynchronize(st));
     b.ready = true;
@@ -440,7 +446,7 @@ __global__ void k_pair_count(ShellDev S, long long npair, long long* nprimpair, 
 }
 
 __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, int4* info, double4* A, double4* B,
-                            int2* atoms, int2* lab, double4* pp, double2* pp2, float4* ppf, float4* ppf2,
+                            int2* atoms, int2* lab, double4* pp, double2* pp2, float4* ppf, float4* ppf2, float4* ppd,
                             double* alpha, int2* sh) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair) return;
@@ -474,6 +480,14 @@ __global__ void k_pair_fill(ShellDev S, long long npair, const long long* poff, 
             const double fa = -be * ip, fb = al * ip;
             ppf[o + n] = make_float4((float)(fa * ABx), (float)(fa * ABy), (float)(fa * ABz), (float)p);
             ppf2[o + n] = make_float4((float)(fb * ABx), (float)(fb * ABy), (float)(fb * ABz), (float)kap);
+            // double-float data: every value as hi + lo floats (P - A, P - B, p, kappa, 1/2p)
+            const double dv[9] = {fa * ABx, fa * ABy, fa * ABz, fb * ABx, fb * ABy, fb * ABz, p, kap, 0.5 * ip};
+            float hl[20];
+            for (int t = 0; t < 9; ++t) { hl[2 * t] = (float)dv[t]; hl[2 * t + 1] = (float)(dv[t] - (double)hl[2 * t]); }
+            hl[18] = 0.f;
+            hl[19] = 0.f;
+            float4* dst = ppd + 5 * (o + n);
+            for (int t = 0; t < 5; ++t) dst[t] = make_float4(hl[4 * t], hl[4 * t + 1], hl[4 * t + 2], hl[4 * t + 3]);
             alpha[o + n] = al;
         }
 }
@@ -676,12 +690,13 @@ __global__ void k_row_items(const long long* start, const int* rbra, int nrows, 
 
 // max |x| (as the bit pattern of a non-negative double) and, if xf is not
 // null, the FP32 copy of x used by the digestion of FP32 quartets.
-__global__ void k_absmax(const double* x, long long n, unsigned long long* out, float* xf) {
+__global__ void k_absmax(const double* x, long long n, unsigned long long* out, float* xf, float2* xd = nullptr) {
     double m = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v = x[i];
         m = fmax(m, fabs(v));
         if (xf) xf[i] = (float)v;
+        if (xd) xd[i] = make_float2((float)v, (float)(v - (double)(float)v));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
@@ -884,6 +899,7 @@ gb::PairsView view_of(const jk_pairs_s* h) {
     v.ppf2 = h->ppf2.as<float4>();
     v.alpha = h->alpha.as<double>();
     v.Ahl = h->Ahl.as<float4>();
+    v.ppd = h->ppd.as<float4>();
     return v;
 }
 
@@ -984,11 +1000,13 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     if ((rc = h->pp2.alloc(sizeof(double2) * nprimpair))) return rc;
     if ((rc = h->ppf.alloc(sizeof(float4) * nprimpair))) return rc;
     if ((rc = h->ppf2.alloc(sizeof(float4) * nprimpair))) return rc;
+    if ((rc = h->ppd.alloc(sizeof(float4) * 5 * nprimpair))) return rc;
     if ((rc = h->alpha.alloc(sizeof(double) * nprimpair))) return rc;
     k_pair_fill<<<nblk(np, 128), 128, 0, st>>>(SD, np, d_poff.as<long long>(), u_info.as<int4>(), u_A.as<double4>(),
                                                 u_B.as<double4>(), u_atoms.as<int2>(), u_lab.as<int2>(),
                                                 h->pp.as<double4>(), h->pp2.as<double2>(), h->ppf.as<float4>(),
-                                                h->ppf2.as<float4>(), h->alpha.as<double>(), u_sh.as<int2>());
+                                                h->ppf2.as<float4>(), h->ppd.as<float4>(), h->alpha.as<double>(),
+                                                u_sh.as<int2>());
     CKL();
     // ---- sort 1: by class, then Schwarz per class
     if ((rc = sort_pairs(d_key.as<unsigned long long>(), d_val.as<int>(), npad, st))) return rc;
@@ -1245,11 +1263,14 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.tsmall = (float)g_opt.tsmall;
     a.D = D;
     a.Df = h->Df.as<float>();
+    a.Ddf = h->Ddf.as<gb::dfl>();
+    a.boysd = g_boys[h->device].tabd.as<float2>();
     a.J = J;
     a.K = K;
     a.nbf = h->nbf;
-    const TuneCfg& tc = cr.tune[prec];
-    const int grid = grid_for(total_hint * gb_class_threads(cr.bra_cls, cr.ket_cls, prec), tc.block, tc.qpt, h->nsm);
+    const TuneCfg& tc = cr.tune[prec == 3 ? 0 : prec];
+    const int grid = grid_for(total_hint * gb_class_threads(cr.bra_cls, cr.ket_cls, prec == 3 ? 0 : prec), tc.block, tc.qpt,
+                              h->nsm);
     ProfRec* pr = nullptr;
     if (g_opt.profile) {
         h->prof.emplace_back();
@@ -1455,8 +1476,10 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         if ((rc = h->split_tot.alloc(sizeof(long long) * nst))) return rc;
         CK(cudaMemsetAsync(h->split_tot.p, 0, sizeof(long long) * nst, st));
         if ((rc = h->Df.alloc(sizeof(float) * n2))) return rc;
+        if (g_opt.df_tier && (rc = h->Ddf.alloc(sizeof(float2) * n2))) return rc;
         CK(cudaMemsetAsync(h->scratch.p, 0, 8, st));
-        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n2, h->scratch.as<unsigned long long>(), h->Df.as<float>());
+        k_absmax<<<152 * 4, 256, 0, st>>>(D, (long long)n2, h->scratch.as<unsigned long long>(), h->Df.as<float>(),
+                                          g_opt.df_tier ? h->Ddf.as<float2>() : nullptr);
         CKL();
         // max |D| per shell block, for the density-weighted FP64 selection
         const size_t ns2 = (size_t)h->nshell * h->nshell;
@@ -1494,8 +1517,9 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
             if ((rc = split_fill(h, cr, r0, r1, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st, g_opt.tau,
                                  g_opt.eps)))
                 return rc;
-            if ((rc = launch_class(h, cr, 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
-                                   cr.l64.as<long long>(), l64, r0)))
+            // the largest-bound quartets: FP64, or double-float on the FP32 pipe (JK_OPT_DF_TIER)
+            if ((rc = launch_class(h, cr, g_opt.df_tier ? 3 : 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st,
+                                   r1 - r0, cr.l64.as<long long>(), l64, r0)))
                 return rc;
             if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st, r1 - r0,
                                    nullptr, nullptr, r0)))
@@ -1548,7 +1572,7 @@ struct BatchPlan {
     std::vector<unsigned long long> serial;  // of every handle: a freed handle's address can come back
     std::vector<const double*> D;
     std::vector<double*> J, K;
-    int prec = 0, device = 0, max_n = 0, graph = 0, rpath = 0;
+    int prec = 0, device = 0, max_n = 0, graph = 0, rpath = 0, df = 0;
     double tau = 0.0, eps = 0.0, tsmall = 0.0;
     long long nquartets = 0;
     DevBuf bm, dmax, split_tot;
@@ -1630,6 +1654,7 @@ __global__ void k_absmax_batched(const gb::BatchMol* bm, unsigned long long* out
         const double x = m.D[i];
         v = fmax(v, fabs(x));
         m.Df[i] = (float)x;  // FP32 copy for the digestion of FP32 quartets
+        if (m.Ddf) m.Ddf[i] = gb::dfl((float)x, (float)(x - (double)(float)x));
     }
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(v));
@@ -1660,7 +1685,9 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
         host[m].D = P.D[m];
         if (P.prec == JK_MIXED && (rc = h->Df.alloc(sizeof(float) * (size_t)h->nbf * h->nbf))) return rc;
         if (P.prec == JK_MIXED && (rc = h->Dsh.alloc(sizeof(float) * (size_t)h->nshell * h->nshell))) return rc;
+        if (P.prec == JK_MIXED && P.df && (rc = h->Ddf.alloc(sizeof(float2) * (size_t)h->nbf * h->nbf))) return rc;
         host[m].Df = h->Df.as<float>();
+        host[m].Ddf = P.df ? h->Ddf.as<gb::dfl>() : nullptr;
         host[m].Dsh = h->Dsh.as<float>();
         host[m].bf_shell = h->bf_shell.as<int>();
         host[m].psh = h->pair_sh.as<int2>();
@@ -1774,12 +1801,13 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     a.rows.klist = klist;
     a.boys = g_boys[P.device].tab.as<double>();
     a.boysf = g_boys[P.device].tabf.as<float>();
+    a.boysd = g_boys[P.device].tabd.as<float2>();
     a.tsmall = (float)P.tsmall;
     a.mols = P.bm.as<gb::BatchMol>();
     a.row_mol = bc.rowmol.as<int>();
-    const TuneCfg& tc = bc.tune[prec];
+    const TuneCfg& tc = bc.tune[prec == 3 ? 0 : prec];
     int nsm = P.mols[0]->nsm;
-    const long long items = bc.total * gb_class_split(bc.X, bc.Y) * gb_class_threads(bc.X, bc.Y, prec);  // upper bound
+    const long long items = bc.total * gb_class_split(bc.X, bc.Y) * gb_class_threads(bc.X, bc.Y, prec == 3 ? 0 : prec);
     const int e = gb_launch_jk(bc.X, bc.Y, prec == 1 && P.rpath ? 2 : prec, a, grid_for(items, tc.block, tc.qpt, nsm),
                                tc.block, s);
     if (e) return fail(JK_ERR_CUDA, std::string("batched ERI launch: ") + cudaGetErrorString((cudaError_t)e));
@@ -1822,7 +1850,8 @@ int enqueue_batch(BatchPlan& P) {
                                                                     l64, ldm);
             CKL();
             P.launches += 1 + 5 * scan_launches(n1);
-            if ((rc = launch_batch_class(P, bc, 0, bc.s64.as<long long>(), nullptr, s, bc.l64.as<long long>(), l64)))
+            if ((rc = launch_batch_class(P, bc, P.df ? 3 : 0, bc.s64.as<long long>(), nullptr, s, bc.l64.as<long long>(),
+                                         l64)))
                 return rc;
             if ((rc = launch_batch_class(P, bc, 1, bc.s32.as<long long>(), bc.k32.as<int>(), s))) return rc;
             if ((rc = launch_batch_class(P, bc, 1, bc.sdem.as<long long>(), nullptr, s, bc.ldem.as<long long>(), ldm)))
@@ -1919,7 +1948,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
     CK(cudaGetDevice(&dev));
     bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
                 g_plan->tau == g_opt.tau && g_plan->eps == g_opt.eps && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph &&
-                g_plan->rpath == g_opt.rpath;
+                g_plan->rpath == g_opt.rpath && g_plan->df == g_opt.df_tier;
     for (int m = 0; same && m < nmol; ++m)
         same = g_plan->mols[m] == pairs[m] && g_plan->serial[m] == pairs[m]->serial && g_plan->D[m] == D[m] &&
                g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
@@ -1939,6 +1968,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
         P.tsmall = g_opt.tsmall;
         P.graph = g_opt.graph;
         P.rpath = g_opt.rpath;
+        P.df = g_opt.df_tier;
         if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
     }
     BatchPlan& P = *g_plan;
@@ -2411,6 +2441,7 @@ int jk_set_option(jk_option opt, double v) {
             if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "gradient tau");
             g_opt.grad_tau = v;
             return JK_OK;
+        case JK_OPT_DF_TIER: g_opt.df_tier = v != 0.0; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2427,6 +2458,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_RPATH: *v = g_opt.rpath; return JK_OK;
         case JK_OPT_FAIL_ALLOC_AFTER: *v = (double)g_fail_alloc.load(); return JK_OK;
         case JK_OPT_GRAD_TAU: *v = g_opt.grad_tau; return JK_OK;
+        case JK_OPT_DF_TIER: *v = g_opt.df_tier; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }

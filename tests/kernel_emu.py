@@ -60,13 +60,14 @@ def _sources(lmax, only=None, ntu=8):
             f32 = " ".join(f"eri_jk_{name}_f32_c{c0}(a);" for c0, _ in mg.crange_groups(bra, ket))
         else:
             f32 = f"eri_jk_{name}_f32(a);"
+        dfc = f"else if (prec == 3) eri_jk_{name}_{'df' if mg.has_df(bra, ket) else 'f64'}(a); "
         if (bra, ket) in mg.RPATH_CLASSES and mg.crange_groups(bra, ket):
             # prec 2: the FP32 range kernels emitted with Algorithm 1's recursion order
             f32r = " ".join(f"eri_jk_{name}_f32r_c{c0}(a);" for c0, _ in mg.crange_groups(bra, ket))
             jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else if (prec == 2) {{ {f32r} }} "
-                            f"else {{ {f32} }} return 0;")
+                            f"{dfc}else {{ {f32} }} return 0;")
         else:
-            jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); else {{ {f32} }} return 0;")
+            jk_cases.append(f"    case {key}: if (prec == 0) eri_jk_{name}_f64(a); {dfc}else {{ {f32} }} return 0;")
         if bra == ket:
             nthr = mg.ncart(bra[0]) if mg.use_chunk(bra, ket) else 1
             nab = mg.ncart(bra[0]) * mg.ncart(bra[1])
@@ -81,6 +82,13 @@ def _sources(lmax, only=None, ntu=8):
     src = ['#include "eri_device.cuh"', "#include <vector>", "#include <deque>", "emu_dim3 blockIdx, threadIdx, blockDim, gridDim;"] + decls
     src.append("""
 static std::deque<std::vector<float4>> g_ahl;  // split centres of every view built (kept alive)
+// double-float data of the problem being emulated (emu_set_df), read by the next views and launches
+static const float4* g_ppd = nullptr;
+static const float2* g_boysd = nullptr;
+static const gb::dfl* g_ddf = nullptr;
+extern "C" void emu_set_df(const float4* ppd, const float2* boysd, const void* ddf) {
+    g_ppd = ppd; g_boysd = boysd; g_ddf = (const gb::dfl*)ddf;
+}
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
     gb::PairsView v;
@@ -95,6 +103,7 @@ static gb::PairsView pv(int npair, const int4* info, const double4* A, const dou
         g_ahl.back()[2 * i + 1] = float4{(float)(A[i].x - hx), (float)(A[i].y - hy), (float)(A[i].z - hz), 0.f};
     }
     v.Ahl = g_ahl.back().data();
+    v.ppd = g_ppd;
     return v;
 }
 extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
@@ -109,6 +118,7 @@ extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const
     a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
     a.rows.kofs = kofs; a.rows.klist = klist;
     a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.D = D; a.Df = Df; a.J = J; a.K = K; a.nbf = nbf;
+    a.boysd = g_boysd; a.Ddf = g_ddf;
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
 """ + "\n".join(jk_cases) + """
@@ -261,7 +271,7 @@ class Problem:
             pairs.sort(key=lambda x: (x[0], -Q[x[1], x[2]], x[1], x[2]))
         else:
             pairs.sort()
-        info, A, B, pp, pp2, ppf, ppf2, alpha, atoms = [], [], [], [], [], [], [], [], []
+        info, A, B, pp, pp2, ppf, ppf2, alpha, atoms, ppd = [], [], [], [], [], [], [], [], [], []
         s2 = math.sqrt(2 * math.pi ** 2.5)
         for cls, a, b in pairs:
             Ra, Rb = mol.xyz[atom[a]], mol.xyz[atom[b]]
@@ -279,6 +289,7 @@ class Problem:
                     pp2.append((kap, 0.5 / p))
                     ppf.append((*(-be / p * AB), p))
                     ppf2.append((*(al / p * AB), kap))
+                    ppd.append((*(-be / p * AB), *(al / p * AB), p, kap, 0.5 / p))
                     alpha.append(al)
         self.cls = np.array([x[0] for x in pairs])
         self.pair_shells = [(a, b) for _, a, b in pairs]
@@ -293,8 +304,19 @@ class Problem:
         self.ppf, self.ppf2, self.alpha = f(ppf, np.float32), f(ppf2, np.float32), f(alpha, np.float64)
         self.D = np.ascontiguousarray(D, dtype=np.float64)
         self.Df = self.D.astype(np.float32)
+        # double-float data as the runtime lays them out: 5 float4 per primitive pair
+        # ((P-A)x,(P-A)y | (P-A)z,(P-B)x | (P-B)y,(P-B)z | p,kappa | 1/2p,-), each value hi, lo
+        v = np.array(ppd, dtype=np.float64).reshape(-1, 9)
+        hl = np.zeros((v.shape[0], 20), dtype=np.float32)
+        hl[:, 0:18:2] = v.astype(np.float32)
+        hl[:, 1:18:2] = (v - v.astype(np.float32).astype(np.float64)).astype(np.float32)
+        self.ppd = np.ascontiguousarray(hl)
+        self.Ddf = np.ascontiguousarray(np.stack([self.Df, (self.D - self.Df.astype(np.float64)).astype(np.float32)],
+                                                 axis=-1))
         self.nbf = D.shape[0]
         self.boys, self.boysf = boys_tables(oracle)
+        bh = self.boys.astype(np.float32)
+        self.boysd = np.ascontiguousarray(np.stack([bh, (self.boys - bh.astype(np.float64)).astype(np.float32)], axis=-1))
 
     def rows(self, X, Y, items=True):
         """Rows (bra, first ket, quartet count) of class pair (X, Y) and their
@@ -317,10 +339,12 @@ class Problem:
         return a.ctypes.data_as(C.c_void_p)
 
     def jk(self, prec, tsmall=1.0, lists=False):
-        """J and K from the class kernels of one precision.  lists=True hands
-        every row's kets to the kernels as an explicit ket list (the form of
-        a mixed build's FP64 and demoted lists), in reversed order."""
+        """J and K from the class kernels of one precision (0 FP64, 1 FP32, 2 FP32
+        in Algorithm 1's order, 3 double-float).  lists=True hands every row's
+        kets to the kernels as an explicit ket list (the form of a mixed build's
+        FP64 and demoted lists), in reversed order."""
         lib = load(self.lmax, self.only)
+        lib.emu_set_df(self._p(self.ppd), self._p(self.boysd), self._p(self.Ddf))
         J = np.zeros((self.nbf, self.nbf))
         K = np.zeros((self.nbf, self.nbf))
         for X in range(len(self.pcs)):

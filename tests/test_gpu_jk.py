@@ -133,3 +133,31 @@ def test_all_fp32_kernels_against_oracle(g, seed, shells, natom, kmax):
     Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
     assert np.abs(J - Jo).max() <= 2e-6 * np.abs(Jo).max(), np.abs(J - Jo).max() / np.abs(Jo).max()
     assert np.abs(K - Ko).max() <= 2e-6 * np.abs(Ko).max(), np.abs(K - Ko).max() / np.abs(Ko).max()
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(44, [0, 1, 2], 3, 3), (45, [2, 2, 1], 2, 4)])
+def test_double_float_tier(g, seed, shells, natom, kmax):
+    """Every quartet through the double-float kernels (cutoff 0: every quartet
+    is FP64-selected, and the double-float tier takes them): the oracle's J, K
+    and E to FP64-like accuracy, far inside the FP32 kernels' 2e-6; with the
+    tier off the same quartets run in FP64 and the two agree to 1e-11."""
+    mol = molgen.random_molecule(500 + seed, natom, shells, 1, kmax, 0.05, 5e3, layout="lattice", spacing=2.2)
+    D = molgen.density(mol, 600 + seed)
+    tau, df = g.get_option("mixed_tau"), g.get_option("df_tier")
+    g.set_option("mixed_tau", 0.0)
+    try:
+        g.set_option("df_tier", 1)
+        pairs, J, K, E = _run(g, mol, D, None, "mixed")
+        n32, n64 = g.last_split(pairs)
+        g.set_option("df_tier", 0)
+        _, J64, K64, E64 = _run(g, mol, D, None, "mixed")
+    finally:
+        g.set_option("mixed_tau", tau)
+        g.set_option("df_tier", df)
+    assert n32 == 0 and n64 == pairs.nquartets
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    sJ, sK = max(1.0, np.abs(Jo).max()), max(1.0, np.abs(Ko).max())
+    assert np.abs(J - Jo).max() <= 1e-11 * sJ, np.abs(J - Jo).max() / sJ
+    assert np.abs(K - Ko).max() <= 1e-11 * sK, np.abs(K - Ko).max() / sK
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-11 * max(1.0, abs(E))
+    assert np.abs(J - J64).max() <= 1e-11 * sJ and np.abs(K - K64).max() <= 1e-11 * sK

@@ -108,6 +108,20 @@ def test_emulated_path_searched_r(monkeypatch):
         assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), prec
 
 
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(61, [0, 1, 2], 2, 3), (63, [0, 2, 2], 2, 2)])
+def test_emulated_double_float(seed, shells, natom, kmax):
+    """The double-float kernels (hi + lo float pairs, FP32 arithmetic only; the
+    mixed build runs its largest-bound quartets in them) against the oracle,
+    and far more accurate than the FP32 kernels."""
+    mol, D = _mol(seed, shells, natom, kmax)
+    pr = kernel_emu.Problem(mol, D, oracle)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    J, K = pr.jk(3)
+    sJ, sK = max(1.0, np.abs(Jo).max()), max(1.0, np.abs(Ko).max())
+    assert np.abs(J - Jo).max() <= 1e-11 * sJ, np.abs(J - Jo).max() / sJ
+    assert np.abs(K - Ko).max() <= 1e-11 * sK, np.abs(K - Ko).max() / sK
+
+
 def test_emulated_rpath_variants_of_the_library():
     """The FP32 range kernels the library also carries in Algorithm 1's
     recursion order ((dd|dd), (dd|dp), (dp|dp); launched under the R-path
