@@ -67,6 +67,8 @@ def _load():
             lib.orc_schwarz.argtypes = [C.POINTER(_Mol), dp]
             lib.orc_jk.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, dp, dp]
             lib.orc_jk.restype = C.c_longlong
+            lib.orc_jk_ld.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, dp, dp]
+            lib.orc_jk_ld.restype = C.c_longlong
             lib.orc_jk_rows.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, ip, dp, dp]
             lib.orc_jk_rows.restype = C.c_int
             lib.orc_jk_rows_ld.argtypes = [C.POINTER(_Mol), dp, C.c_double, C.c_int, ip, dp, dp]
@@ -166,14 +168,18 @@ def schwarz(mol) -> np.ndarray:
     return Q
 
 
-def jk(mol, D, thresh: float | None = None, mode: str = "unique"):
+def jk(mol, D, thresh: float | None = None, mode: str = "unique", extended: bool = False):
     """J, K (and the number of shell quartets kept).  mode "all" loops over
-    every quartet; "unique" over a>=b, c>=d, ab>=cd with explicit images."""
+    every quartet; "unique" over a>=b, c>=d, ab>=cd with explicit images.
+    ``extended``: every integral and sum in long double (an extended-precision
+    reference on x86, where long double has a 64-bit significand), rounded to
+    FP64 at the end."""
     v = _MolView(mol)
     D = np.ascontiguousarray(D, dtype=np.float64)
     J = np.zeros_like(D)
     K = np.zeros_like(D)
-    kept = _load().orc_jk(v.ref(), _dp(D), float(thresh or 0.0), 0 if mode == "all" else 1, _dp(J), _dp(K))
+    fn = _load().orc_jk_ld if extended else _load().orc_jk
+    kept = fn(v.ref(), _dp(D), float(thresh or 0.0), 0 if mode == "all" else 1, _dp(J), _dp(K))
     return J, K, int(kept)
 
 

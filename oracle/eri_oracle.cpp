@@ -356,6 +356,78 @@ int jk_rows_impl(const orc_mol* m, const double* D, double thresh, int nrows, co
     return 0;
 }
 
+// J and K over the screened quartets (mode 0 all, mode 1 unique with images),
+// in arithmetic type R; see orc_jk.
+template <class R>
+long long jk_impl(const orc_mol* m, const double* D, double thresh, int mode, double* J, double* K) {
+    const auto o = bf_offsets(*m);
+    const int S = m->nshell, N = o[S];
+    std::vector<double> Q;
+    if (thresh > 0) schwarz_table(*m, Q);
+    CompArrT<R> Jt((size_t)N * N), Kt((size_t)N * N);
+    long long kept = 0;
+#pragma omp parallel reduction(+ : kept)
+    {
+        WorkT<R> w;
+        std::vector<R> blk;
+        CompArrT<R> Jl((size_t)N * N), Kl((size_t)N * N);
+#pragma omp for schedule(dynamic)
+        for (int a = 0; a < S; ++a)
+            for (int b = 0; b < S; ++b) {
+                if (mode == 1 && b > a) continue;
+                for (int c = 0; c < S; ++c)
+                    for (int d = 0; d < S; ++d) {
+                        if (mode == 1) {
+                            if (d > c) continue;
+                            const long ab = (long)a * (a + 1) / 2 + b, cd = (long)c * (c + 1) / 2 + d;
+                            if (cd > ab) continue;
+                        }
+                        if (thresh > 0 && Q[(size_t)a * S + b] * Q[(size_t)c * S + d] < thresh) continue;
+                        ++kept;
+                        Shell A = shell_of(*m, a), B = shell_of(*m, b), C = shell_of(*m, c), Dd = shell_of(*m, d);
+                        const int na = ncart(A.l), nb = ncart(B.l), nc = ncart(C.l), nd = ncart(Dd.l);
+                        blk.resize((size_t)na * nb * nc * nd);
+                        eri_quartet(A, B, C, Dd, blk.data(), w);
+                        if (mode == 0) {
+                            for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
+                            for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
+                                const R v = blk[((i * nb + j) * nc + k) * nd + l];
+                                const int mu = o[a] + i, nu = o[b] + j, la = o[c] + k, si = o[d] + l;
+                                Jl.add((size_t)mu * N + nu, v * R(D[(size_t)la * N + si]));
+                                Kl.add((size_t)mu * N + la, v * R(D[(size_t)nu * N + si]));
+                            }
+                        } else {
+                            const long ab = (long)a * (a + 1) / 2 + b, cd = (long)c * (c + 1) / 2 + d;
+                            R s = 1;
+                            if (a == b) s *= 0.5;
+                            if (c == d) s *= 0.5;
+                            if (ab == cd) s *= 0.5;
+                            for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
+                            for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
+                                const R v = s * blk[((i * nb + j) * nc + k) * nd + l];
+                                const int p = o[a] + i, q = o[b] + j, r = o[c] + k, t = o[d] + l;
+                                // the eight images (pq|rt) (qp|rt) (pq|tr) (qp|tr) (rt|pq) (tr|pq) (rt|qp) (tr|qp)
+                                const int img[8][4] = {{p, q, r, t}, {q, p, r, t}, {p, q, t, r}, {q, p, t, r},
+                                                       {r, t, p, q}, {t, r, p, q}, {r, t, q, p}, {t, r, q, p}};
+                                for (int g = 0; g < 8; ++g) {
+                                    const int* x = img[g];
+                                    Jl.add((size_t)x[0] * N + x[1], v * R(D[(size_t)x[2] * N + x[3]]));
+                                    Kl.add((size_t)x[0] * N + x[2], v * R(D[(size_t)x[1] * N + x[3]]));
+                                }
+                            }
+                        }
+                    }
+            }
+#pragma omp critical
+        for (size_t i = 0; i < (size_t)N * N; ++i) {
+            Jt.add(i, Jl.s[i]); Jt.add(i, Jl.c[i]);
+            Kt.add(i, Kl.s[i]); Kt.add(i, Kl.c[i]);
+        }
+    }
+    for (size_t i = 0; i < (size_t)N * N; ++i) { J[i] = (double)Jt.get(i); K[i] = (double)Kt.get(i); }
+    return kept;
+}
+
 }  // namespace
 
 extern "C" {
@@ -434,72 +506,14 @@ void orc_schwarz(const orc_mol* m, double* Q) {
 // permutational images.  thresh <= 0 disables screening.  Returns the number
 // of unique shell quartets kept (mode 1) or of all quartets kept (mode 0).
 long long orc_jk(const orc_mol* m, const double* D, double thresh, int mode, double* J, double* K) {
-    const auto o = bf_offsets(*m);
-    const int S = m->nshell, N = o[S];
-    std::vector<double> Q;
-    if (thresh > 0) schwarz_table(*m, Q);
-    CompArr Jt((size_t)N * N), Kt((size_t)N * N);
-    long long kept = 0;
-#pragma omp parallel reduction(+ : kept)
-    {
-        Work w;
-        std::vector<double> blk;
-        CompArr Jl((size_t)N * N), Kl((size_t)N * N);
-#pragma omp for schedule(dynamic)
-        for (int a = 0; a < S; ++a)
-            for (int b = 0; b < S; ++b) {
-                if (mode == 1 && b > a) continue;
-                for (int c = 0; c < S; ++c)
-                    for (int d = 0; d < S; ++d) {
-                        if (mode == 1) {
-                            if (d > c) continue;
-                            const long ab = (long)a * (a + 1) / 2 + b, cd = (long)c * (c + 1) / 2 + d;
-                            if (cd > ab) continue;
-                        }
-                        if (thresh > 0 && Q[(size_t)a * S + b] * Q[(size_t)c * S + d] < thresh) continue;
-                        ++kept;
-                        Shell A = shell_of(*m, a), B = shell_of(*m, b), C = shell_of(*m, c), Dd = shell_of(*m, d);
-                        const int na = ncart(A.l), nb = ncart(B.l), nc = ncart(C.l), nd = ncart(Dd.l);
-                        blk.resize((size_t)na * nb * nc * nd);
-                        eri_quartet(A, B, C, Dd, blk.data(), w);
-                        if (mode == 0) {
-                            for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
-                            for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
-                                const double v = blk[((i * nb + j) * nc + k) * nd + l];
-                                const int mu = o[a] + i, nu = o[b] + j, la = o[c] + k, si = o[d] + l;
-                                Jl.add((size_t)mu * N + nu, v * D[(size_t)la * N + si]);
-                                Kl.add((size_t)mu * N + la, v * D[(size_t)nu * N + si]);
-                            }
-                        } else {
-                            const long ab = (long)a * (a + 1) / 2 + b, cd = (long)c * (c + 1) / 2 + d;
-                            double s = 1.0;
-                            if (a == b) s *= 0.5;
-                            if (c == d) s *= 0.5;
-                            if (ab == cd) s *= 0.5;
-                            for (int i = 0; i < na; ++i) for (int j = 0; j < nb; ++j)
-                            for (int k = 0; k < nc; ++k) for (int l = 0; l < nd; ++l) {
-                                const double v = s * blk[((i * nb + j) * nc + k) * nd + l];
-                                const int p = o[a] + i, q = o[b] + j, r = o[c] + k, t = o[d] + l;
-                                // the eight images (pq|rt) (qp|rt) (pq|tr) (qp|tr) (rt|pq) (tr|pq) (rt|qp) (tr|qp)
-                                const int img[8][4] = {{p, q, r, t}, {q, p, r, t}, {p, q, t, r}, {q, p, t, r},
-                                                       {r, t, p, q}, {t, r, p, q}, {r, t, q, p}, {t, r, q, p}};
-                                for (int g = 0; g < 8; ++g) {
-                                    const int* x = img[g];
-                                    Jl.add((size_t)x[0] * N + x[1], v * D[(size_t)x[2] * N + x[3]]);
-                                    Kl.add((size_t)x[0] * N + x[2], v * D[(size_t)x[1] * N + x[3]]);
-                                }
-                            }
-                        }
-                    }
-            }
-#pragma omp critical
-        for (size_t i = 0; i < (size_t)N * N; ++i) {
-            Jt.add(i, Jl.s[i]); Jt.add(i, Jl.c[i]);
-            Kt.add(i, Kl.s[i]); Kt.add(i, Kl.c[i]);
-        }
-    }
-    for (size_t i = 0; i < (size_t)N * N; ++i) { J[i] = Jt.get(i); K[i] = Kt.get(i); }
-    return kept;
+    return jk_impl<double>(m, D, thresh, mode, J, K);
+}
+
+// The same J and K with every integral and sum in long double (x86: 64-bit
+// significand): an extended-precision reference for the FP64 result (the
+// Schwarz screening, from the FP64 Q, is the same).
+long long orc_jk_ld(const orc_mol* m, const double* D, double thresh, int mode, double* J, double* K) {
+    return jk_impl<long double>(m, D, thresh, mode, J, K);
 }
 
 // J/K contributions of an explicit list of unique shell quartets

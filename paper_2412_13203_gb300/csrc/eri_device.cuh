@@ -208,6 +208,22 @@ __device__ __forceinline__ void boys_f64(double T, double* F, const double* __re
     }
 }
 
+// 1/(2m+1) as hi + lo floats (the downward recursions of boys_f32 and boys_df).
+// The FP32 roundings of these reciprocals are too large for 12 of the 13
+// m >= 1 (by up to 5e-8 relative): multiplying by them alone would bias F_m
+// of every FP32 quartet the same way, an error that adds up over quartets
+// instead of cancelling.
+static __constant__ dfl kInvOddDf[kLmaxBoys + 1] = {
+    df_const(1.0), df_const(1.0 / 3), df_const(1.0 / 5), df_const(1.0 / 7), df_const(1.0 / 9),
+    df_const(1.0 / 11), df_const(1.0 / 13), df_const(1.0 / 15), df_const(1.0 / 17), df_const(1.0 / 19),
+    df_const(1.0 / 21), df_const(1.0 / 23), df_const(1.0 / 25), df_const(1.0 / 27)};
+
+// Slot of a Taylor row of the FP32 table that holds the low part of the row's
+// leading coefficient (FP32 evaluation uses terms 0..4 only): the series is
+// summed smallest terms first and the leading term's hi part added last, so
+// the one rounding of F_m(T_k) to FP32 is not shared by every T of a bin.
+constexpr int kBoysLoSlot = 5;
+
 template <int L>
 __device__ __forceinline__ void boys_f32(float T, float* F, const float* __restrict__ tab) {
     if (T < (float)kBoysTmax) {
@@ -217,20 +233,26 @@ __device__ __forceinline__ void boys_f32(float T, float* F, const float* __restr
         // |d| <= 1/32: five terms reach FP32 rounding
         float f = __ldg(c + 4);
 #pragma unroll
-        for (int j = 3; j >= 0; --j) f = fmaf(f, d, __ldg(c + j));
-        F[L] = f;
+        for (int j = 3; j >= 1; --j) f = fmaf(f, d, __ldg(c + j));
+        F[L] = __ldg(c) + fmaf(f, d, __ldg(c + kBoysLoSlot));
         if (L > 0) {
             const float* e = tab + ((size_t)k * kBoysRows + kLmaxBoys + 1) * kBoysTaylor;
             float eT = __ldg(e + 4);
 #pragma unroll
-            for (int j = 3; j >= 0; --j) eT = fmaf(eT, d, __ldg(e + j));
+            for (int j = 3; j >= 1; --j) eT = fmaf(eT, d, __ldg(e + j));
+            eT = __ldg(e) + fmaf(eT, d, __ldg(e + kBoysLoSlot));
             const float t2 = 2.0f * T;
 #pragma unroll
-            for (int m = L - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], eT) * (1.0f / (2 * m + 1));
+            for (int m = L - 1; m >= 0; --m) {
+                const float y = fmaf(t2, F[m + 1], eT);
+                F[m] = m == 0 ? y : fmaf(y, kInvOddDf[m].hi, y * kInvOddDf[m].lo);  // one rounding of y (hi + lo)
+            }
         }
     } else {
-        const float r = rsqrtf(T);
-        F[0] = 0.886226925f * r;
+        // rsqrtf refined by one Newton step, sqrt(pi)/2 as hi + lo
+        const float r0 = rsqrtf(T);
+        const float r = fmaf(0.5f * r0, fmaf(-T * r0, r0, 1.0f), r0);
+        F[0] = fmaf(r, 0.886226952f, r * -2.66231996e-08f);
         const float h = 0.5f * r * r;
 #pragma unroll
         for (int m = 0; m < L; ++m) F[m + 1] = F[m] * ((2 * m + 1) * h);
@@ -240,12 +262,6 @@ __device__ __forceinline__ void boys_f32(float T, float* F, const float* __restr
 // Double-float evaluation (the double-float quartets of a mixed build): the
 // FP64 table's values split into hi + lo, the same Taylor series, downward
 // recursion and asymptotic form, every operation on the FP32 pipe.
-// 1/(2m+1) as double-float constants (the downward recursion of boys_df)
-static __constant__ dfl kInvOddDf[kLmaxBoys + 1] = {
-    df_const(1.0), df_const(1.0 / 3), df_const(1.0 / 5), df_const(1.0 / 7), df_const(1.0 / 9),
-    df_const(1.0 / 11), df_const(1.0 / 13), df_const(1.0 / 15), df_const(1.0 / 17), df_const(1.0 / 19),
-    df_const(1.0 / 21), df_const(1.0 / 23), df_const(1.0 / 25), df_const(1.0 / 27)};
-
 template <int L>
 __device__ __forceinline__ void boys_df(dfl T, dfl* F, const float2* __restrict__ tab) {
     if (T.hi < (float)kBoysTmax) {

@@ -257,6 +257,10 @@ __global__ void k_boys_fill(const double* raw, int nm, double* tab, float* tabf,
     tab[idx] = v;
     tabf[idx] = (float)v;
     tabd[idx] = make_float2((float)v, (float)(v - (double)(float)v));
+    if (j == gb::kBoysLoSlot) {  // FP32 table: the low part of the row's leading term (unused slot)
+        const double v0 = r <= gb::kLmaxBoys ? raw[k * nm + r] : exp(-(double)k / gb::kBoysPerUnit);
+        tabf[idx] = (float)(v0 - (double)(float)v0);
+    }
 }
 
 int ensure_boys(int dev, cudaStream_t st) {

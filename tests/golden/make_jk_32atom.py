@@ -5,9 +5,13 @@ basis functions, Schwarz threshold 1e-10, seeded density) to jk_32atom.npz.
 Only the CPU oracle runs here: Obara-Saika/HRR integrals over every unique
 shell quartet that passes Schwarz, each added to its eight permutational
 images with Neumaier-compensated sums (J_mn = sum_ls (mn|ls) D_ls,
-K_mn = sum_ls (ml|ns) D_ls, E = tr(DJ)/2 - tr(DK)/4).  The GPU parity test
-of the full-size build compares every element of its J and K and its E with
-these values.  About 45 minutes on 8 x86 cores.
+K_mn = sum_ls (ml|ns) D_ls, E = tr(DJ)/2 - tr(DK)/4), every integral and sum
+in long double (64-bit significand on x86) and rounded to FP64 at the end.
+The FP64 oracle's elements carry errors of a few 1e-11 (the FP64 rounding of
+the recursions), which add up to several 1e-10 in E, too close to the 1e-10
+target to judge an FP64 build by; the extended values are good to about
+1e-14.  The GPU parity test of the full-size build compares every element of
+its J and K and its E with these values.  About 2.5 hours on 8 x86 cores.
 
 Run:  python tests/golden/make_jk_32atom.py
 """
@@ -33,7 +37,7 @@ def main():
     mol, D = molgen.config(1)
     thresh = molgen.CONFIG_THRESH[1]
     t = time.time()
-    J, K, kept = oracle.jk(mol, D, thresh, mode="unique")
+    J, K, kept = oracle.jk(mol, D, thresh, mode="unique", extended=True)
     E = oracle.energy(D, J, K)
     dt = time.time() - t
     iu = np.triu_indices(mol.nbf)

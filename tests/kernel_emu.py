@@ -27,7 +27,7 @@ sys.path.insert(0, os.path.join(ROOT, "paper_2412_13203_gb300", "codegen"))
 import md_codegen as mg  # noqa: E402
 
 BUILD = os.path.join(HERE, "_emu_build")
-KBOYS_ROWS, KBOYS_TAYLOR, KBOYS_NGRID, KLMAX_BOYS = 15, 8, 1281, 13
+KBOYS_ROWS, KBOYS_TAYLOR, KBOYS_NGRID, KLMAX_BOYS, KBOYS_LO_SLOT = 15, 8, 1281, 13, 5
 
 
 def _sources(lmax, only=None, ntu=8):
@@ -237,7 +237,8 @@ def load(lmax=2, only=None):
 def boys_tables(oracle):
     """The Boys Taylor table in the library's layout: F_{m+j}(T_k)/j! for
     T_k = k/16, m = 0..13, and exp(-T_k)/j! in the last row (values from the
-    oracle's Boys function)."""
+    oracle's Boys function); the FP32 copy holds the low part of each row's
+    leading term in the slot the FP32 evaluation does not use."""
     tab = np.zeros((KBOYS_NGRID, KBOYS_ROWS, KBOYS_TAYLOR))
     fact = np.array([math.factorial(j) for j in range(KBOYS_TAYLOR)], dtype=float)
     for k in range(KBOYS_NGRID):
@@ -246,7 +247,10 @@ def boys_tables(oracle):
         for m in range(KLMAX_BOYS + 1):
             tab[k, m] = F[m:m + KBOYS_TAYLOR] / fact
         tab[k, KLMAX_BOYS + 1] = math.exp(-T) / fact
-    return tab.ravel(), tab.ravel().astype(np.float32)
+    tabf = tab.astype(np.float32)
+    # slot 5 of every FP32 row: the low part of its leading term
+    tabf[:, :, KBOYS_LO_SLOT] = (tab[:, :, 0] - tabf[:, :, 0].astype(np.float64)).astype(np.float32)
+    return tab.ravel(), tabf.ravel()
 
 
 class Problem:

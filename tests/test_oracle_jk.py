@@ -118,3 +118,22 @@ def test_extended_precision_rows():
         Jl, Kl = oracle.jk_rows(mol, D, shells, extended=True)
         for X, Y in ((Jl, Jd), (Kl, Kd), (Jl, J[rows]), (Kl, K[rows])):
             assert np.abs(X - Y).max() <= 1e-13 * np.abs(Y).max()
+
+
+def test_extended_precision_unique_build():
+    """The long-double unique-quartet J/K (what writes the full-size golden
+    values) agree with the FP64 unique and all-quartet builds to FP64
+    rounding, keep the same quartets, and with the long-double rows."""
+    mol = _mol(26, [0, 1, 2], natom=3, kmax=3)
+    D = molgen.density(mol, 10)
+    J, K, kept = oracle.jk(mol, D, 1e-12, mode="unique")
+    Jl, Kl, kept_l = oracle.jk(mol, D, 1e-12, mode="unique", extended=True)
+    Ja, Ka, _ = oracle.jk(mol, D, 1e-12, mode="all")
+    assert kept_l == kept
+    for X, Y in ((Jl, J), (Kl, K), (Jl, Ja), (Kl, Ka)):
+        assert np.abs(X - Y).max() <= 1e-13 * np.abs(Y).max()
+    assert np.abs(Jl - Jl.T).max() <= 1e-14 * np.abs(Jl).max()
+    rows = oracle.bf_shell_rows(mol, [2])
+    Jr, Kr = oracle.jk_rows(mol, D, [2], 1e-12, extended=True)
+    assert np.abs(Jr - Jl[rows]).max() <= 1e-14 * np.abs(Jl).max()
+    assert np.abs(Kr - Kl[rows]).max() <= 1e-14 * np.abs(Kl).max()
