@@ -168,7 +168,8 @@ def class_totals(records):
     launch, each covering all of its range kernels)."""
     tot = {}
     for r in records:
-        key = (r["cls"], r["prec"])
+        # the FP32 complement of a primitively split FP64 list runs the FP32 kernels
+        key = (r["cls"], "fp32" if r["prec"] == "fp32c" else r["prec"])
         tot[key] = tot.get(key, 0.0) + r["ms"]
     return tot
 
@@ -683,7 +684,8 @@ def main():
                        "primitive_quartets": pairs.nprimquartets, "l2": "flushed (256 MB write) between timed steps",
                        "pair_build_ms": round(pair_ms, 2), "mixed_tau": g.get_option("mixed_tau"),
                        "mixed_tsmall": g.get_option("mixed_tsmall"), "mixed_fp32_quartets": n32,
-                       "mixed_fp64_quartets": n64,
+                       "mixed_fp64_quartets": n64, "mixed_prim_tau": g.get_option("prim_tau"),
+                       "mixed_fp64_tier_primitive_quartets": sum(v["fp64"]["nprimq"] for v in split.values()),
                        "parallelism": f"one molecule split over {world} GPUs (cost-balanced quartet rows, "
                                       "one all-reduce of J and K per build)" if world > 1 else "1 GPU"},
             "mixed": {"ms_per_step": t_mx, "primitive_quartets_per_s": pairs.nprimquartets / (t_mx * 1e-3),

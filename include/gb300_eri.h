@@ -224,7 +224,7 @@ int jk_boys(int L, int n, const double* T, double* F, jk_precision prec, void* c
 
 /* Tunables (process-wide). */
 typedef enum {
-    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 1e-2) */
+    JK_OPT_MIXED_TAU = 0,        /* mixed path: FP32 iff Q_ab Q_cd max|D| < tau (default 5e-3) */
     JK_OPT_MIXED_TSMALL = 1,     /* mixed path: Boys of FP32 quartets in FP64 for T < tsmall (default 0:
                                   * measured to change no J/K/E error on the benchmark workloads, while
                                   * the FP64 branch kept the FP32 kernels' FP64 pipe busy) */
@@ -256,11 +256,19 @@ typedef enum {
                                   * for the quartets whose density-weighted bound (as for JK_OPT_MIXED_TAU)
                                   * is below this value, FP64 otherwise; every per-quartet gradient sum
                                   * is added to dE/dR in FP64 (default 3e-4) */
-    JK_OPT_DF_TIER = 9           /* mixed builds (single and batched): nonzero runs the quartets the
+    JK_OPT_DF_TIER = 9,          /* mixed builds (single and batched): nonzero runs the quartets the
                                   * density-weighted bound keeps out of FP32 (l <= 2 classes) in
                                   * double-float arithmetic -- every value an unevaluated sum of two
                                   * floats, ~44 significant bits, all on the FP32 pipe -- instead of
-                                  * FP64 (default 1); the FP64 build is unaffected */
+                                  * FP64 (default 0); the FP64 build is unaffected */
+    JK_OPT_PRIM_TAU = 10         /* mixed builds (single and batched): primitive split of the quartets kept
+                                  * out of FP32.  Each pair's primitive pairs carry their own Schwarz factor
+                                  * q_p (shellpairs_build); of such a quartet only the primitive quartets
+                                  * with q_p q_q max|D| >= this value (max|D| over the quartet's six D
+                                  * blocks, as for JK_OPT_MIXED_TAU) run in FP64 / double-float, the others
+                                  * in FP32, added into the same J and K.  0 turns the split off (every
+                                  * primitive quartet of such a quartet in FP64 / double-float); default
+                                  * 1e-4 */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);
@@ -301,12 +309,16 @@ int jk_class_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
  * max_rows rows of 8 int64: bra class, ket class, then for the FP32 quartets
  * and for the FP64 quartets each: shell quartets, primitive quartets and the
  * algorithmic operation count of the generated code (as jk_class_stats).
- * *nrows receives the number of classes with work. */
+ * With the primitive split (JK_OPT_PRIM_TAU) the FP64 quartets' primitive
+ * quartets and operations are the FP64 / double-float tier's share, and the
+ * FP32 columns add the FP32 complement (the shell-quartet counts are those of
+ * the quartet-level split).  *nrows receives the number of classes with work. */
 int jk_split_stats(jk_pairs pairs, int max_rows, int64_t* rows, int* nrows);
 
 /* Launch timings of the last jk_build with JK_OPT_PROFILE set (host,
  * synchronous): up to max_rows rows of 5 doubles: bra class, ket class,
- * precision (0 FP64, 1 FP32, 3 double-float), shell quartets, milliseconds
+ * precision (0 FP64, 1 FP32, 3 double-float, 4 the FP32 complement of a
+ * primitively split FP64 list), shell quartets, milliseconds
  * (CUDA events on the build's stream).  *nrows receives the number of launches. */
 int jk_profile(jk_pairs pairs, int max_rows, double* rows, int* nrows);
 

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgb300eri.so")
 
 JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3, "profile": 4, "density_screen": 5,
-          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8, "df_tier": 9}
+          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8, "df_tier": 9, "prim_tau": 10}
 _PREC = {"fp64": 0, "mixed": 1}
 
 _lib = None
@@ -479,7 +479,7 @@ def profile(pairs: ShellPairs):
     for k in range(min(n.value, 256)):
         r = buf[5 * k:5 * k + 5]
         out.append(dict(cls=PAIR_CLASS_NAMES[int(r[0])] + "|" + PAIR_CLASS_NAMES[int(r[1])], bra=int(r[0]),
-                        ket=int(r[1]), prec={0: "fp64", 3: "df"}.get(int(r[2]), "fp32"), nquartets=int(r[3]),
+                        ket=int(r[1]), prec={0: "fp64", 3: "df", 4: "fp32c"}.get(int(r[2]), "fp32"), nquartets=int(r[3]),
                         ms=r[4]))
     return out
 

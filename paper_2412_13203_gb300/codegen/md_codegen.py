@@ -347,6 +347,19 @@ def crange_groups(bra, ket):
 
 CRANGE_VALUES = 150
 
+# Resident blocks of 128 threads per SM the FP32 class kernels are compiled
+# for (__launch_bounds__ minimum; None: the compiler's choice, up to 255
+# registers a thread).
+F32_MIN_BLOCKS = None
+
+
+PRIM_CUT = (
+    "int jq0 = 0, jq1 = ik.z;\n"
+    "if (pmode) {  // primitive split of a mixed build's FP64 list (gb::prim_range)\n"
+    "  gb::prim_range(pairs.pq, ib.w + ip, ik.w, ik.z, pthr, pmode, jq0, jq1);\n"
+    "  if (jq0 >= jq1) continue;\n"
+    "}")
+
 
 def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
     """Device code computing acc[NAB*NCD] for one shell quartet (flat mode with
@@ -383,6 +396,7 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
         E(f"{real} Xl[{HAB * NCD}];")
         E(f"{real} Rc[{L1 * L1 * L1}];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
+    E(PRIM_CUT)
     if dfm:
         E("const float4* pd_ = pairs.ppd + 5 * (ib.w + ip);")
         E("const float4 u0 = pd_[0], u1 = pd_[1], u2 = pd_[2], u3 = pd_[3], u4 = pd_[4];")
@@ -409,7 +423,7 @@ def gen_quartet_body(bra, ket, real, mode_flat, cds=None, rpath=None):
                 E(f"{real} x{h}_{k} = 0;")
     else:
         E(f"for (int i = 0; i < {HAB * NCD}; ++i) Xl[i] = 0;")
-    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    E("for (int jq = jq0; jq < jq1; ++jq) {")
     if dfm:
         E("const float4* qd_ = pairs.ppd + 5 * (ik.w + jq);")
         E("const float4 w0 = qd_[0], w1 = qd_[1], w2 = qd_[2], w3 = qd_[3], w4 = qd_[4];")
@@ -648,6 +662,7 @@ def gen_quartet_body_chunk(bra, ket, real):
     E(f"{real} Ebp[{S_ab}];")
     E(f"const int cx = c_comp_{lc}[3 * ci], cy = c_comp_{lc}[3 * ci + 1], cz = c_comp_{lc}[3 * ci + 2];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
+    E(PRIM_CUT)
     if f32:
         E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
         E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
@@ -672,7 +687,7 @@ def gen_quartet_body_chunk(bra, ket, real):
     E(f"  Ebp[k] = ebxa[w & 255] * ebya[(w >> 8) & 255] * ebza[w >> 16]{' * kp' if f32 else ''};")
     E("}")
     E(f"for (int i = 0; i < {HAB * nd}; ++i) Xl[i] = 0;")
-    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    E("for (int jq = jq0; jq < jq1; ++jq) {")
     if f32:
         E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
         E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q);")
@@ -862,8 +877,15 @@ def gen_class_kernels(bra, ket):
         else:
             centres = "  const double4 A = pairs.A[bra], B = pairs.B[bra], C = pairs.A[ket], Dd = pairs.B[ket];"
             dmat = "Dm"
+        lbounds = f"128, {F32_MIN_BLOCKS}" if prec == "f32" and F32_MIN_BLOCKS else "128"
         for suffix, body, digest, nacc in variants:
             warpk = warp and ", ws);" in digest
+            # primitive mode 1: the bra and ket primitive pairs are sorted by their
+            # Schwarz factors, so an item whose first bra primitive pair misses the
+            # cut with the largest ket one has no primitive quartet to evaluate
+            early = ("" if warpk else
+                     "  if (pmode == 1 && __fmul_rn(__ldg(pairs.pq + ib.w + ipart), __ldg(pairs.pq + ik.w)) < pthr)\n"
+                     "    continue;  // nothing of this item reaches the cut: no digestion either\n")
             loop_head = (
                 "  const long long stride = (long long)gridDim.x * blockDim.x;\n"
                 "  for (long long t0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~(GB_WARP_SIZE - 1)); "
@@ -885,7 +907,7 @@ def gen_class_kernels(bra, ket):
                 "                                      act ? (unsigned)((qt - ipart) & 0x7fffffff) : 0x80000000u | (threadIdx.x & 31), act);"
                 if warpk else "")
             out.append(f"""
-__global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JKArgs args) {{
+__global__ void __launch_bounds__({lbounds}) eri_jk_{name}_{prec}{suffix}(const gb::JKArgs args) {{
   // persistent grid-stride loop over the quartets of this launch; the total is
   // read on the device (last entry of the row prefix) so launches need no host sync
   // Work items: rows.start is the prefix of items per row, a row's quartet
@@ -934,7 +956,9 @@ __global__ void __launch_bounds__(128) eri_jk_{name}_{prec}{suffix}(const gb::JK
   const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)
                                   : __ldg(args.rows.ket0 + row) + (int)qo;
   const int4 ik = pairs.info[ket];
-{centres}
+  const int pmode = args.pmode;
+  const float pthr = pmode ? __ldg(args.rows.kthr + __ldg(args.rows.kofs + row) + qo) : 0.f;
+{early}{centres}
 {indent(body)}
   {real} s = 1;
   if (ib.x == ib.y) s *= 0.5f;
@@ -980,6 +1004,9 @@ __global__ void __launch_bounds__(128) eri_schwarz_{la}{lb}(const gb::SchwarzArg
   const int nsplit = min(S, ib.z);
   if (ipart >= nsplit) return;
   const double4 A = pairs.A[bra], B = pairs.B[bra], C = A, Dd = B;
+  const int pmode = 0;  // every primitive quartet
+  const float pthr = 0.f;
+  (void)pthr;
 {indent(sbody)}
   double* dg = sa.diag + ((size_t)i * S + ipart) * {nab};
 {diag}

@@ -107,6 +107,11 @@ struct PairsView {
     // per primitive pair, double-float kernels: 5 float4 = (P-A)x,(P-A)y | (P-A)z,(P-B)x |
     // (P-B)y,(P-B)z | p, kappa | 1/(2p), - (each value as hi, lo; differences formed in FP64)
     const float4* ppd;
+    // per primitive pair: its Schwarz factor sqrt(max_i |(pp|pp)_ii|) (contraction
+    // coefficients included), the primitive pairs of every pair sorted by it,
+    // largest first, so that |(p|q)| <= pq[p] pq[q] for every primitive quartet
+    // and the primitive quartets above a cut form a prefix of every ket loop
+    const float* pq;
 };
 
 struct RowsView {
@@ -116,6 +121,10 @@ struct RowsView {
     const int* ket0;         // first ket pair of every row (kets are contiguous) ...
     const long long* kofs;   // ... or, if klist is set, the row's first entry in klist
     const int* klist;        // explicit ket pairs (rows of a mixed build's FP64 / demoted lists)
+    // per klist entry (primitive split of a mixed build's FP64 list): the cut
+    // on pq[p] pq[q] that separates the quartet's large primitive quartets (FP64
+    // tier) from the rest (FP32), tau_p / max|D| of the quartet's D blocks
+    const float* kthr;
 };
 
 // One molecule of a batched launch.
@@ -152,7 +161,25 @@ struct JKArgs {
     int nbf;
     const BatchMol* mols;     // batched launches: per-molecule data (nullptr: single molecule above)
     const int* row_mol;       // batched launches: molecule of every row
+    // primitive quartets a work item evaluates: 0 all; 1 those with
+    // pq[p] pq[q] >= rows.kthr[entry] (FP64 / double-float tier); 2 the others
+    // (their FP32 complement, launched over the same list)
+    int pmode;
 };
+
+// The ket primitive pairs [j0, j1) that one bra primitive pair `ip` of a work
+// item evaluates under primitive mode `mode` (see JKArgs::pmode).  The kets'
+// factors are sorted descending, so pq[ip] pq[k0 + j] >= thr holds on a prefix;
+// both tiers take the decision with the same FP32 product, so every primitive
+// quartet is evaluated exactly once.
+__device__ __forceinline__ void prim_range(const float* __restrict__ pq, int ip, int k0, int nk, float thr, int mode,
+                                           int& j0, int& j1) {
+    const float qb = __ldg(pq + ip);
+    int n = 0;
+    while (n < nk && __fmul_rn(qb, __ldg(pq + k0 + n)) >= thr) ++n;
+    j0 = mode == 1 ? 0 : n;
+    j1 = mode == 1 ? n : nk;
+}
 
 struct GradArgs {
     PairsView pairs;

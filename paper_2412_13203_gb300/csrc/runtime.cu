@@ -145,15 +145,18 @@ std::mutex g_boys_mu;
 BoysTables g_boys[64];
 
 struct Options {
-    double tau = 1e-2;  // meets 1e-6 Eh on J, K and E of the 32-atom workload and of the 64 batch molecules
+    double tau = 5e-3;  // with the primitive split: J, K and E of the 32-atom workload and of the batch
+                        // molecules measured within 3e-7 Eh of the FP64 build
     double eps = 0.0;  // density screening of mixed builds (0: off)
     double tsmall = 0.0;  // FP32 Boys everywhere in FP32 quartets (the FP64 branch buys no accuracy)
     int check_sym = 0;
     int graph = 1;
     int profile = 0;
     int rpath = 1;     // FP32 kernels of the classes emitted twice: Algorithm 1's R recursion order
-    int df_tier = 1;   // mixed builds: the FP64-selected quartets in double-float arithmetic
+    int df_tier = 0;   // mixed builds: the FP64-selected quartets in double-float arithmetic (off: FP64 is
+                       // faster once the primitive split leaves only their large primitive quartets)
     double grad_tau = 3e-4;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
+    double ptau = 1e-4;  // mixed builds: primitive quartets of the FP64 list below this bound run in FP32 (0: off)
 } g_opt;
 
 struct ProfRec {
@@ -173,6 +176,7 @@ struct jk_pairs_s {
     DevBuf info, A, B, pp, pp2, ppf, ppf2;          // sorted, kept pairs
     DevBuf Ahl;                                     // float4 x 2 per pair: centre of a as hi + lo floats
     DevBuf ppd;                                     // float4 x 5 per primitive pair: double-float data
+    DevBuf pq;                                      // float per primitive pair: primitive Schwarz factor
     DevBuf Ddf;                                     // double-float copy of the last mixed build's D
     DevBuf Df;                                      // FP32 copy of the last mixed build's D
     DevBuf alpha;                                   // per primitive pair: exponent of the a primitive
@@ -187,6 +191,8 @@ struct jk_pairs_s {
     std::vector<std::vector<double>> part_cost;     // per class: algorithmic cost of every part, then the
                                                     // largest single-row cost of the class
     DevBuf list64, listdem;                         // mixed: FP64 and demoted (FP32) ket lists
+    DevBuf thr64;                                   // mixed, primitive split: per FP64 list entry, its primitive cut
+    bool last_psplit = false;                       // the last mixed build split its FP64 list by primitives
     std::vector<long long> list_off64, list_offd;   // per class: first entry in list64 / listdem
     std::vector<int> last_r0, last_r1;              // per class: rows of the last mixed build (partial builds)
     DevBuf pair_lab;                                // int2 per pair: la, lb
@@ -657,6 +663,52 @@ __global__ void k_np_of(const int4* info, long long n, long long* np) {
     if (k < n) np[k] = info[k].z;
 }
 
+// One entry per primitive pair of the kept pairs (entry npre[i] + k for the
+// k-th primitive pair of pair i): a one-primitive-pair view of its pair, on
+// which the class's Schwarz kernel gives the primitive Schwarz factor.
+__global__ void k_prim_expand(const int4* info, const double4* A, const double4* B, const long long* npre, long long n,
+                              int4* finfo, double4* fA, double4* fB) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 ib = info[i];
+    const long long o = npre[i];
+    for (int k = 0; k < ib.z; ++k) {
+        finfo[o + k] = make_int4(ib.x, ib.y, 1, ib.w + k);
+        fA[o + k] = A[i];
+        fB[o + k] = B[i];
+    }
+}
+
+// The primitive pairs of every kept pair, sorted by primitive Schwarz factor
+// (largest first, ties in their previous order), gathered into compact
+// arrays at npre[i]; info[i].w is moved to the new first index.
+__global__ void k_prim_sort(int4* info, const long long* npre, long long n, const double* q, const double4* pp,
+                            const double2* pp2, const float4* ppf, const float4* ppf2, const float4* ppd,
+                            const double* alpha, double4* pp_o, double2* pp2_o, float4* ppf_o, float4* ppf2_o,
+                            float4* ppd_o, double* alpha_o, float* pq_o) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 ib = info[i];
+    const long long o = npre[i];
+    for (int k = 0; k < ib.z; ++k) {
+        const double qk = q[o + k];
+        int rank = 0;
+        for (int j = 0; j < ib.z; ++j) {
+            const double qj = q[o + j];
+            rank += (qj > qk || (qj == qk && j < k)) ? 1 : 0;
+        }
+        const long long src = (long long)ib.w + k, dst = o + rank;
+        pp_o[dst] = pp[src];
+        pp2_o[dst] = pp2[src];
+        ppf_o[dst] = ppf[src];
+        ppf2_o[dst] = ppf2[src];
+        for (int c = 0; c < 5; ++c) ppd_o[5 * dst + c] = ppd[5 * src + c];
+        alpha_o[dst] = alpha[src];
+        pq_o[dst] = (float)qk;
+    }
+    info[i].w = (int)o;
+}
+
 // Max |D| over every shell block (non-negative floats order like their bits).
 __global__ void k_dsh(const double* D, int n, const int* bf_shell, int nshell, unsigned int* dsh) {
     const long long n2 = (long long)n * n;
@@ -680,6 +732,37 @@ __global__ void k_list_primq(const long long* cnt, const long long* ofs, const i
     for (long long k = 0; k < c; ++k) kp += info[klist[ofs[r] + k]].z;
     atomicAdd(acc, (unsigned long long)(kp * info[rbra[r]].z));
     atomicAdd(acc + 1, (unsigned long long)(c * info[rbra[r]].z));
+}
+
+// k_list_primq over a primitively split FP64 list: the primitive quartets and
+// bra primitive-pair units of each listed quartet on either side of its cut
+// (the same FP32 products as gb::prim_range), FP64 tier into acc64, the FP32
+// complement into acc32.
+__global__ void k_list_primq_split(const long long* cnt, const long long* ofs, const int* klist, const float* thr,
+                                   const int* rbra, int nrows, const int4* info, const float* pq,
+                                   unsigned long long* acc32, unsigned long long* acc64) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long c = cnt[r];
+    if (c == 0) return;
+    const int4 ib = info[rbra[r]];
+    unsigned long long p64 = 0, u64 = 0, p32 = 0, u32 = 0;
+    for (long long k = 0; k < c; ++k) {
+        const int4 ik = info[klist[ofs[r] + k]];
+        const float t = thr[ofs[r] + k];
+        for (int ip = 0; ip < ib.z; ++ip) {
+            int j0, j1;
+            gb::prim_range(pq, ib.w + ip, ik.w, ik.z, t, 1, j0, j1);
+            p64 += j1;
+            u64 += j1 > 0;
+            p32 += ik.z - j1;
+            u32 += j1 < ik.z;
+        }
+    }
+    atomicAdd(acc64, p64);
+    atomicAdd(acc64 + 1, u64);
+    atomicAdd(acc32, p32);
+    atomicAdd(acc32 + 1, u32);
 }
 
 // Work items of every row: quartets x min(P, K_ab) (bra primitive pairs of the
@@ -904,6 +987,7 @@ gb::PairsView view_of(const jk_pairs_s* h) {
     v.alpha = h->alpha.as<double>();
     v.Ahl = h->Ahl.as<float4>();
     v.ppd = h->ppd.as<float4>();
+    v.pq = h->pq.as<float>();
     return v;
 }
 
@@ -1150,6 +1234,74 @@ int build_impl(const jk_atoms* atoms, const jk_shells* shells, double thresh, jk
     }
     if ((rc = scan_exclusive(d_npk.as<long long>(), d_npre.as<long long>(), kept + 1, d_tot.as<long long>() + 1, st)))
         return rc;
+    // ---- primitive Schwarz factors; primitive pairs of every kept pair sorted by
+    // them (largest first) into compact arrays (the dropped pairs' primitive
+    // pairs are released)
+    {
+        std::vector<long long> ncp(ncls + 1, 0);
+        for (int c = 0; c <= ncls; ++c)
+            CK(cudaMemcpyAsync(&ncp[c], d_npre.as<long long>() + h->cls_start[c], sizeof(long long),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const long long nkp = ncp[ncls];
+        if (nkp > (long long)INT32_MAX) return fail(JK_ERR_UNSUPPORTED, "more than 2^31 primitive pairs");
+        const long long nk1 = std::max(1LL, nkp);
+        DevBuf f_info, f_A, f_B, f_q;
+        if ((rc = f_info.alloc(sizeof(int4) * nk1))) return rc;
+        if ((rc = f_A.alloc(sizeof(double4) * nk1))) return rc;
+        if ((rc = f_B.alloc(sizeof(double4) * nk1))) return rc;
+        if ((rc = f_q.alloc(sizeof(double) * nk1))) return rc;
+        if (kept > 0) {
+            k_prim_expand<<<nblk(kept, 256), 256, 0, st>>>(h->info.as<int4>(), h->A.as<double4>(), h->B.as<double4>(),
+                                                            d_npre.as<long long>(), kept, f_info.as<int4>(),
+                                                            f_A.as<double4>(), f_B.as<double4>());
+            CKL();
+        }
+        gb::PairsView fv;
+        std::memset(&fv, 0, sizeof(fv));
+        fv.npair = (int)nkp;
+        fv.info = f_info.as<int4>();
+        fv.A = f_A.as<double4>();
+        fv.B = f_B.as<double4>();
+        fv.pp = h->pp.as<double4>();
+        fv.pp2 = h->pp2.as<double2>();
+        for (int c = 0; c < ncls; ++c) {
+            const int nab = pair_ncart(c);
+            const long long chunk = std::max<long long>(1, (long long)(diag_len / nab));
+            for (long long e0 = ncp[c]; e0 < ncp[c + 1]; e0 += chunk) {
+                const int cnt = (int)std::min(chunk, ncp[c + 1] - e0);
+                CK(cudaMemsetAsync(d_diag.p, 0, sizeof(double) * (size_t)cnt * nab * gb::kSchwarzSplit, st));
+                gb::SchwarzArgs sa{fv, (int)e0, cnt, boys, d_diag.as<double>(), f_q.as<double>() + e0};
+                if (gb_launch_schwarz(c, sa, st)) return fail(JK_ERR_CUDA, "primitive Schwarz kernel launch failed");
+                k_schwarz_finish<<<nblk(cnt, 256), 256, 0, st>>>(d_diag.as<double>(), nab, cnt, f_q.as<double>() + e0);
+                CKL();
+            }
+        }
+        DevBuf n_pp, n_pp2, n_ppf, n_ppf2, n_ppd, n_alpha;
+        if ((rc = n_pp.alloc(sizeof(double4) * nk1))) return rc;
+        if ((rc = n_pp2.alloc(sizeof(double2) * nk1))) return rc;
+        if ((rc = n_ppf.alloc(sizeof(float4) * nk1))) return rc;
+        if ((rc = n_ppf2.alloc(sizeof(float4) * nk1))) return rc;
+        if ((rc = n_ppd.alloc(sizeof(float4) * 5 * nk1))) return rc;
+        if ((rc = n_alpha.alloc(sizeof(double) * nk1))) return rc;
+        if ((rc = h->pq.alloc(sizeof(float) * nk1))) return rc;
+        if (kept > 0) {
+            k_prim_sort<<<nblk(kept, 128), 128, 0, st>>>(
+                h->info.as<int4>(), d_npre.as<long long>(), kept, f_q.as<double>(), h->pp.as<double4>(),
+                h->pp2.as<double2>(), h->ppf.as<float4>(), h->ppf2.as<float4>(), h->ppd.as<float4>(),
+                h->alpha.as<double>(), n_pp.as<double4>(), n_pp2.as<double2>(), n_ppf.as<float4>(),
+                n_ppf2.as<float4>(), n_ppd.as<float4>(), n_alpha.as<double>(), h->pq.as<float>());
+            CKL();
+        }
+        CK(cudaStreamSynchronize(st));  // the old arrays are released below
+        h->pp = std::move(n_pp);
+        h->pp2 = std::move(n_pp2);
+        h->ppf = std::move(n_ppf);
+        h->ppf2 = std::move(n_ppf2);
+        h->ppd = std::move(n_ppd);
+        h->alpha = std::move(n_alpha);
+        h->nprimpair = nkp;
+    }
     // Every class pair's rows are enumerated, scanned and counted in stream
     // order with shared scratch; the per-class totals land in one device array
     // that is read back with a single synchronisation at the end.
@@ -1247,7 +1399,7 @@ int grid_for(long long total, int block, int qpt, int nsm) {
 int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* start, const int* ket0,
                  long long total_hint, const double* D, double* J, double* K, cudaStream_t st,
                  int nrows = -1, const long long* kofs = nullptr, const int* klist = nullptr, int r0 = 0,
-                 double* Jlo = nullptr, double* Klo = nullptr) {
+                 double* Jlo = nullptr, double* Klo = nullptr, int pmode = 0, const float* kthr = nullptr) {
     if (total_hint <= 0) return 0;
     const int nr = nrows >= 0 ? nrows : cr.nrows - r0;
     if (nr <= 0) return 0;
@@ -1260,6 +1412,8 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
     a.rows.ket0 = ket0 ? ket0 + r0 : nullptr;
     a.rows.kofs = kofs ? kofs + r0 : nullptr;
     a.rows.klist = klist;
+    a.rows.kthr = kthr;
+    a.pmode = (klist && kthr) ? pmode : 0;
     a.Jlo = Jlo;
     a.Klo = Klo;
     a.boys = g_boys[h->device].tab.as<double>();
@@ -1283,7 +1437,7 @@ int launch_class(jk_pairs_s* h, const ClassRows& cr, int prec, const long long* 
         CK(cudaEventCreate(&pr->e1));
         pr->bra = cr.bra_cls;
         pr->ket = cr.ket_cls;
-        pr->prec = prec;
+        pr->prec = a.pmode == 2 ? 4 : prec;  // 4: FP32 complement of a primitive split
         pr->total = total_hint;
         CK(cudaEventRecord(pr->e0, st));
     }
@@ -1326,7 +1480,7 @@ int split_count(jk_pairs_s* h, ClassRows& cr, int r0, int r1, const double* dmax
 // split_tot[2..4]), list offsets (l64, ldem; totals into split_tot[5..6]) and
 // the list fill.  The prefixes start at 0 at row r0.
 int split_fill(jk_pairs_s* h, ClassRows& cr, int r0, int r1, long long* split_tot, int* list64, int* listdem,
-               cudaStream_t st, double tau, double eps) {
+               cudaStream_t st, double tau, double eps, float taup, float* thr64) {
     int rc;
     const long long n1 = r1 - r0 + 1;
     long long* scr = cr.scr.as<long long>();
@@ -1341,7 +1495,7 @@ int split_fill(jk_pairs_s* h, ClassRows& cr, int r0, int r1, long long* split_to
     k_rows_fill<<<nblk(nr, 256), 256, 0, st>>>(cr.bra.as<int>() + r0, cr.ket0.as<int>() + r0, cr.k32.as<int>() + r0, nr,
                                                h->A.as<double4>(), tau, eps, h->pair_sh.as<int2>(),
                                                h->Dsh.as<float>(), h->nshell, cr.l64.as<long long>() + r0,
-                                               cr.ldem.as<long long>() + r0, list64, listdem);
+                                               cr.ldem.as<long long>() + r0, list64, listdem, taup, thr64);
     CKL();
     h->launches += 1 + 5 * scan_launches(n1);
     return 0;
@@ -1512,18 +1666,27 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         }
         if ((rc = h->list64.alloc(sizeof(int) * std::max(1LL, off64[ncr])))) return rc;
         if ((rc = h->listdem.alloc(sizeof(int) * std::max(1LL, offd[ncr])))) return rc;
+        const bool psplit = g_opt.ptau > 0.0;
+        if (psplit && (rc = h->thr64.alloc(sizeof(float) * std::max(1LL, off64[ncr])))) return rc;
+        h->last_psplit = psplit;
         for (int k = 0; k < ncr; ++k) {
             ClassRows& cr = h->rows[k];
             const int r0 = R0[k], r1 = R1[k];
             if (cr.total <= 0 || r1 <= r0) continue;
             int* l64 = h->list64.as<int>() + off64[k];
             int* ldm = h->listdem.as<int>() + offd[k];
+            float* t64 = psplit ? h->thr64.as<float>() + off64[k] : nullptr;
             if ((rc = split_fill(h, cr, r0, r1, h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st, g_opt.tau,
-                                 g_opt.eps)))
+                                 g_opt.eps, (float)g_opt.ptau, t64)))
                 return rc;
-            // the largest-bound quartets: FP64, or double-float on the FP32 pipe (JK_OPT_DF_TIER)
+            // the largest-bound quartets: FP64, or double-float on the FP32 pipe (JK_OPT_DF_TIER); with
+            // the primitive split only their large primitive quartets, the rest in an FP32 launch over
+            // the same list
             if ((rc = launch_class(h, cr, g_opt.df_tier ? 3 : 0, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st,
-                                   r1 - r0, cr.l64.as<long long>(), l64, r0)))
+                                   r1 - r0, cr.l64.as<long long>(), l64, r0, nullptr, nullptr, 1, t64)))
+                return rc;
+            if (psplit && (rc = launch_class(h, cr, 1, cr.s64.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
+                                             cr.l64.as<long long>(), l64, r0, nullptr, nullptr, 2, t64)))
                 return rc;
             if ((rc = launch_class(h, cr, 1, cr.s32.as<long long>(), cr.k32.as<int>(), cr.itotal, D, J, K, st, r1 - r0,
                                    nullptr, nullptr, r0)))
@@ -1577,10 +1740,11 @@ struct BatchPlan {
     std::vector<const double*> D;
     std::vector<double*> J, K;
     int prec = 0, device = 0, max_n = 0, graph = 0, rpath = 0, df = 0;
-    double tau = 0.0, eps = 0.0, tsmall = 0.0;
+    double tau = 0.0, eps = 0.0, tsmall = 0.0, ptau = 0.0;
     long long nquartets = 0;
     DevBuf bm, dmax, split_tot;
     DevBuf list64, listdem;  // mixed: FP64 and demoted ket lists, one segment per class
+    DevBuf thr64;            // mixed, primitive split: per FP64 list entry, its primitive cut
     std::vector<BatchClass> cls;
     cudaStream_t cs = nullptr, ps[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr}, done = nullptr;
@@ -1793,7 +1957,8 @@ int build_plan(BatchPlan& P, cudaStream_t st) {
 }
 
 int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* start, const int* ket0,
-                       cudaStream_t s, const long long* kofs = nullptr, const int* klist = nullptr) {
+                       cudaStream_t s, const long long* kofs = nullptr, const int* klist = nullptr, int pmode = 0,
+                       const float* kthr = nullptr) {
     gb::JKArgs a;
     std::memset(&a, 0, sizeof(a));
     a.pairs = view_of(P.mols[0]);
@@ -1803,6 +1968,8 @@ int launch_batch_class(BatchPlan& P, BatchClass& bc, int prec, const long long* 
     a.rows.ket0 = ket0;
     a.rows.kofs = kofs;
     a.rows.klist = klist;
+    a.rows.kthr = kthr;
+    a.pmode = (klist && kthr) ? pmode : 0;
     a.boys = g_boys[P.device].tab.as<double>();
     a.boysf = g_boys[P.device].tabf.as<float>();
     a.boysd = g_boys[P.device].tabd.as<float2>();
@@ -1848,14 +2015,18 @@ int enqueue_batch(BatchPlan& P) {
             if ((rc = scan_into(bc.cdem.as<long long>(), bc.ldem.as<long long>(), n1, tot + 6, scr, s))) return rc;
             int* l64 = P.list64.as<int>() + bc.off64;
             int* ldm = P.listdem.as<int>() + bc.offdem;
+            float* t64 = P.ptau > 0.0 ? P.thr64.as<float>() + bc.off64 : nullptr;
             k_rows_fill_batched<<<nblk(bc.nrows, 256), 256, 0, s>>>(bc.bra.as<int>(), bc.ket0.as<int>(), bc.k32.as<int>(),
                                                                     bc.rowmol.as<int>(), bc.nrows, bm, P.tau, P.eps,
                                                                     bc.l64.as<long long>(), bc.ldem.as<long long>(),
-                                                                    l64, ldm);
+                                                                    l64, ldm, (float)P.ptau, t64);
             CKL();
             P.launches += 1 + 5 * scan_launches(n1);
             if ((rc = launch_batch_class(P, bc, P.df ? 3 : 0, bc.s64.as<long long>(), nullptr, s, bc.l64.as<long long>(),
-                                         l64)))
+                                         l64, 1, t64)))
+                return rc;
+            if (t64 && (rc = launch_batch_class(P, bc, 1, bc.s64.as<long long>(), nullptr, s, bc.l64.as<long long>(),
+                                                l64, 2, t64)))
                 return rc;
             if ((rc = launch_batch_class(P, bc, 1, bc.s32.as<long long>(), bc.k32.as<int>(), s))) return rc;
             if ((rc = launch_batch_class(P, bc, 1, bc.sdem.as<long long>(), nullptr, s, bc.ldem.as<long long>(), ldm)))
@@ -1923,6 +2094,7 @@ int batch_prepass(BatchPlan& P, bool* relaid) {
         int rc;
         if ((rc = P.list64.alloc(sizeof(int) * o64))) return rc;
         if ((rc = P.listdem.alloc(sizeof(int) * od))) return rc;
+        if (P.ptau > 0.0 && (rc = P.thr64.alloc(sizeof(float) * o64))) return rc;
         *relaid = true;
     }
     return 0;
@@ -1952,7 +2124,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
     CK(cudaGetDevice(&dev));
     bool same = g_plan && g_plan->device == dev && (int)g_plan->mols.size() == nmol && g_plan->prec == (int)prec &&
                 g_plan->tau == g_opt.tau && g_plan->eps == g_opt.eps && g_plan->tsmall == g_opt.tsmall && g_plan->graph == g_opt.graph &&
-                g_plan->rpath == g_opt.rpath && g_plan->df == g_opt.df_tier;
+                g_plan->rpath == g_opt.rpath && g_plan->df == g_opt.df_tier && g_plan->ptau == g_opt.ptau;
     for (int m = 0; same && m < nmol; ++m)
         same = g_plan->mols[m] == pairs[m] && g_plan->serial[m] == pairs[m]->serial && g_plan->D[m] == D[m] &&
                g_plan->J[m] == J[m] && g_plan->K[m] == K[m];
@@ -1973,6 +2145,7 @@ int batched_impl(int nmol, const jk_pairs* pairs, const double* const* D, double
         P.graph = g_opt.graph;
         P.rpath = g_opt.rpath;
         P.df = g_opt.df_tier;
+        P.ptau = g_opt.ptau;
         if ((rc = build_plan(P, st))) { g_plan.reset(); return rc; }
     }
     BatchPlan& P = *g_plan;
@@ -2324,13 +2497,14 @@ int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR
         int* l64 = h->list64.as<int>() + off64[k];
         int* ldm = h->listdem.as<int>() + offd[k];
         if ((rc = split_fill(h, cr, R0[k], R1[k], h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st,
-                             g_opt.grad_tau, 0.0)))
+                             g_opt.grad_tau, 0.0, 0.f, nullptr)))
             return rc;
         if ((rc = launch(k, 0, cr.s64.as<long long>(), nullptr, cr.l64.as<long long>(), l64))) return rc;
         if ((rc = launch(k, 1, cr.s32.as<long long>(), cr.k32.as<int>(), nullptr, nullptr))) return rc;
         if ((rc = launch(k, 1, cr.sdem.as<long long>(), nullptr, cr.ldem.as<long long>(), ldm))) return rc;
     }
     // the split diagnostics (jk_last_split, jk_split_stats) now describe this gradient
+    h->last_psplit = false;
     h->list_off64 = off64;
     h->list_offd = offd;
     h->last_r0 = R0;
@@ -2446,6 +2620,7 @@ int jk_set_option(jk_option opt, double v) {
             g_opt.grad_tau = v;
             return JK_OK;
         case JK_OPT_DF_TIER: g_opt.df_tier = v != 0.0; return JK_OK;
+        case JK_OPT_PRIM_TAU: if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "primitive tau"); g_opt.ptau = v; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2463,6 +2638,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_FAIL_ALLOC_AFTER: *v = (double)g_fail_alloc.load(); return JK_OK;
         case JK_OPT_GRAD_TAU: *v = g_opt.grad_tau; return JK_OK;
         case JK_OPT_DF_TIER: *v = g_opt.df_tier; return JK_OK;
+        case JK_OPT_PRIM_TAU: *v = g_opt.ptau; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2585,9 +2761,16 @@ int jk_split_stats(jk_pairs h, int max_rows, int64_t* rows, int* nrows) {
                 k_list_primq<<<nblk(nr, 256), 256>>>(cr.cdem.as<long long>() + r0, cr.ldem.as<long long>() + r0,
                                                      h->listdem.as<int>() + h->list_offd[ri], cr.bra.as<int>() + r0,
                                                      nr, h->info.as<int4>(), acc.as<unsigned long long>());
-                k_list_primq<<<nblk(nr, 256), 256>>>(cr.c64.as<long long>() + r0, cr.l64.as<long long>() + r0,
-                                                     h->list64.as<int>() + h->list_off64[ri], cr.bra.as<int>() + r0,
-                                                     nr, h->info.as<int4>(), acc.as<unsigned long long>() + 2);
+                if (h->last_psplit)
+                    k_list_primq_split<<<nblk(nr, 256), 256>>>(
+                        cr.c64.as<long long>() + r0, cr.l64.as<long long>() + r0,
+                        h->list64.as<int>() + h->list_off64[ri], h->thr64.as<float>() + h->list_off64[ri],
+                        cr.bra.as<int>() + r0, nr, h->info.as<int4>(), h->pq.as<float>(), acc.as<unsigned long long>(),
+                        acc.as<unsigned long long>() + 2);
+                else
+                    k_list_primq<<<nblk(nr, 256), 256>>>(cr.c64.as<long long>() + r0, cr.l64.as<long long>() + r0,
+                                                         h->list64.as<int>() + h->list_off64[ri], cr.bra.as<int>() + r0,
+                                                         nr, h->info.as<int4>(), acc.as<unsigned long long>() + 2);
                 CKL();
             }
             unsigned long long v[4];

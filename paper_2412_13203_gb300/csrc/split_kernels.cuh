@@ -56,16 +56,25 @@ __device__ __forceinline__ void split_row(const double4* A, int i, int s, int c,
     n32 = kend - lo;
 }
 
-// The prefix [s, lo) of one row into the FP64 and demoted lists.
+// The prefix [s, lo) of one row into the FP64 and demoted lists.  With a
+// primitive split (thr64 set), every FP64 entry also gets its primitive cut
+// taup / max|D| of its D blocks: its primitive quartets with pq[p] pq[q] at or
+// above the cut run in the FP64 tier, the others in FP32 (JKArgs::pmode).
 __device__ __forceinline__ void fill_row(const double4* A, int i, int s, int lo, double tau, double eps,
-                                         const int2* psh, const float* dsh, int nshell, int* list64, int* listdem) {
+                                         const int2* psh, const float* dsh, int nshell, int* list64, int* listdem,
+                                         float taup, float* thr64) {
     const double qi = A[i].w;
     const int2 ab = psh[i];
     int o64 = 0, od = 0;
     for (int j = s; j < lo; ++j) {
-        const double b = qi * A[j].w * (double)quartet_dmax(dsh, nshell, ab, psh[j]);
-        if (b >= tau) list64[o64++] = j;
-        else if (b >= eps) listdem[od++] = j;
+        const float dq = quartet_dmax(dsh, nshell, ab, psh[j]);
+        const double b = qi * A[j].w * (double)dq;
+        if (b >= tau) {
+            if (thr64) thr64[o64] = __fdiv_rn(taup, dq);
+            list64[o64++] = j;
+        } else if (b >= eps) {
+            listdem[od++] = j;
+        }
     }
 }
 
@@ -104,10 +113,11 @@ __global__ void k_rows_split(const long long* start, const int* rbra, const int*
 // at the row offsets l64 / ldem (exclusive prefixes of c64 / cdem).
 __global__ void k_rows_fill(const int* rbra, const int* rket0, const int* k32, int nrows, const double4* A, double tau,
                             double eps, const int2* psh, const float* dsh, int nshell, const long long* l64,
-                            const long long* ldem, int* list64, int* listdem) {
+                            const long long* ldem, int* list64, int* listdem, float taup, float* thr64) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
-    fill_row(A, rbra[r], rket0[r], k32[r], tau, eps, psh, dsh, nshell, list64 + l64[r], listdem + ldem[r]);
+    fill_row(A, rbra[r], rket0[r], k32[r], tau, eps, psh, dsh, nshell, list64 + l64[r], listdem + ldem[r], taup,
+             thr64 ? thr64 + l64[r] : nullptr);
 }
 
 // k_rows_split for batched rows (each row's molecule from rowmol; dmax holds
@@ -131,10 +141,10 @@ __global__ void k_rows_split_batched(const long long* start, const int* rbra, co
 // k_rows_fill for batched rows.
 __global__ void k_rows_fill_batched(const int* rbra, const int* rket0, const int* k32, const int* rowmol, int nrows,
                                     const gb::BatchMol* bm, double tau, double eps, const long long* l64,
-                                    const long long* ldem, int* list64, int* listdem) {
+                                    const long long* ldem, int* list64, int* listdem, float taup, float* thr64) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const gb::BatchMol& mol = bm[rowmol[r]];
     fill_row(mol.pairs.A, rbra[r], rket0[r], k32[r], tau, eps, mol.psh, mol.Dsh, mol.nshell, list64 + l64[r],
-             listdem + ldem[r]);
+             listdem + ldem[r], taup, thr64 ? thr64 + l64[r] : nullptr);
 }

@@ -47,6 +47,8 @@ inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v)
 }
 inline unsigned int atomicMax(unsigned int* p, unsigned int v) { const unsigned int o = *p; if (v > o) *p = v; return o; }
 inline float __fdividef(float a, float b) { return a / b; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fdiv_rn(float a, float b) { return a / b; }
 inline int __double2int_rn(double x) { return (int)std::nearbyint(x); }
 inline int __float2int_rn(float x) { return (int)std::nearbyint(x); }
 inline long long __double_as_longlong(double x) { long long r; std::memcpy(&r, &x, 8); return r; }

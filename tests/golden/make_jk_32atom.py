@@ -44,7 +44,8 @@ def main():
     # J and K are symmetric: the upper triangles hold every value
     np.savez_compressed(OUT, J_upper=J[iu], K_upper=K[iu], E=np.float64(E), kept=np.int64(kept),
                         nbf=np.int64(mol.nbf), thresh=np.float64(thresh),
-                        asymJ=np.float64(np.abs(J - J.T).max()), asymK=np.float64(np.abs(K - K.T).max()))
+                        asymJ=np.float64(np.abs(J - J.T).max()), asymK=np.float64(np.abs(K - K.T).max()),
+                        arith=np.str_("long double"), seconds=np.float64(dt))
     print(f"nbf={mol.nbf} kept={kept} E={E!r} |J|max={np.abs(J).max():.3f} |K|max={np.abs(K).max():.3f} "
           f"threads={oracle.num_threads()} {dt:.0f}s -> {OUT}")
 

@@ -89,6 +89,14 @@ static const gb::dfl* g_ddf = nullptr;
 extern "C" void emu_set_df(const float4* ppd, const float2* boysd, const void* ddf) {
     g_ppd = ppd; g_boysd = boysd; g_ddf = (const gb::dfl*)ddf;
 }
+// primitive split (emu_set_prim): primitive Schwarz factors of the next views,
+// per-list-entry cuts and the primitive mode of the next launches
+static const float* g_pq = nullptr;
+static const float* g_kthr = nullptr;
+static int g_pmode = 0;
+extern "C" void emu_set_prim(const float* pq, const float* kthr, int pmode) {
+    g_pq = pq; g_kthr = kthr; g_pmode = pmode;
+}
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
     gb::PairsView v;
@@ -104,6 +112,7 @@ static gb::PairsView pv(int npair, const int4* info, const double4* A, const dou
     }
     v.Ahl = g_ahl.back().data();
     v.ppd = g_ppd;
+    v.pq = g_pq;
     return v;
 }
 extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const double4* A, const double4* B,
@@ -117,6 +126,8 @@ extern "C" int emu_jk(int X, int Y, int prec, int npair, const int4* info, const
     a.pairs = pv(npair, info, A, B, pp, pp2, ppf, ppf2, alpha);
     a.rows.nrows = nrows; a.rows.start = start; a.rows.bra = bra; a.rows.ket0 = ket0;
     a.rows.kofs = kofs; a.rows.klist = klist;
+    a.rows.kthr = klist ? g_kthr : nullptr;
+    a.pmode = klist && g_kthr ? g_pmode : 0;
     a.boys = boys; a.boysf = boysf; a.tsmall = tsmall; a.D = D; a.Df = Df; a.J = J; a.K = K; a.nbf = nbf;
     a.boysd = g_boysd; a.Ddf = g_ddf;
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
@@ -258,7 +269,7 @@ class Problem:
     runtime lays them out (pairs canonicalised l_a >= l_b, grouped by class;
     for bra class = ket class only kets up to the bra)."""
 
-    def __init__(self, mol, D, oracle, lmax=2, own_classes=False, q_order=False):
+    def __init__(self, mol, D, oracle, lmax=2, own_classes=False, q_order=False, prim_sort=False):
         self.mol, self.lmax = mol, lmax
         c = oracle.normalize(mol)
         l, K, off, atom = mol.shell_l, mol.shell_nprim, mol.shell_prim_offset, mol.shell_atom
@@ -275,7 +286,7 @@ class Problem:
             pairs.sort(key=lambda x: (x[0], -Q[x[1], x[2]], x[1], x[2]))
         else:
             pairs.sort()
-        info, A, B, pp, pp2, ppf, ppf2, alpha, atoms, ppd = [], [], [], [], [], [], [], [], [], []
+        info, A, B, pp, pp2, ppf, ppf2, alpha, atoms, ppd, pq = [], [], [], [], [], [], [], [], [], [], []
         s2 = math.sqrt(2 * math.pi ** 2.5)
         for cls, a, b in pairs:
             Ra, Rb = mol.xyz[atom[a]], mol.xyz[atom[b]]
@@ -284,17 +295,31 @@ class Problem:
             A.append((*Ra, Q[a, b]))
             B.append((*Rb, 0.0))
             atoms.append((atom[a], atom[b]))
-            for u in range(K[a]):
-                for v in range(K[b]):
-                    al, be = mol.exps[off[a] + u], mol.exps[off[b] + v]
-                    p = al + be
-                    kap = s2 * math.exp(-al * be / p * (AB @ AB)) * c[off[a] + u] * c[off[b] + v] / p
-                    pp.append((*((al * Ra + be * Rb) / p), p))
-                    pp2.append((kap, 0.5 / p))
-                    ppf.append((*(-be / p * AB), p))
-                    ppf2.append((*(al / p * AB), kap))
-                    ppd.append((*(-be / p * AB), *(al / p * AB), p, kap, 0.5 / p))
-                    alpha.append(al)
+            order = [(u, v) for u in range(K[a]) for v in range(K[b])]
+            if prim_sort:
+                # as the pair build: each primitive pair's Schwarz factor (the oracle's
+                # diagonal (pp|pp) of the two one-primitive shells, normalised
+                # contraction coefficients included), largest first
+                qv = []
+                for u, v in order:
+                    sa = (Ra, int(l[a]), [mol.exps[off[a] + u]], [c[off[a] + u]])
+                    sb = (Rb, int(l[b]), [mol.exps[off[b] + v]], [c[off[b] + v]])
+                    e = oracle.eri_quartet([sa, sb, sa, sb])
+                    n2 = e.shape[0] * e.shape[1]
+                    qv.append(math.sqrt(float(np.abs(np.diag(e.reshape(n2, n2))).max())))
+                rank = sorted(range(len(order)), key=lambda k: (-qv[k], k))
+                order = [order[k] for k in rank]
+                pq += [qv[k] for k in rank]
+            for u, v in order:
+                al, be = mol.exps[off[a] + u], mol.exps[off[b] + v]
+                p = al + be
+                kap = s2 * math.exp(-al * be / p * (AB @ AB)) * c[off[a] + u] * c[off[b] + v] / p
+                pp.append((*((al * Ra + be * Rb) / p), p))
+                pp2.append((kap, 0.5 / p))
+                ppf.append((*(-be / p * AB), p))
+                ppf2.append((*(al / p * AB), kap))
+                ppd.append((*(-be / p * AB), *(al / p * AB), p, kap, 0.5 / p))
+                alpha.append(al)
         self.cls = np.array([x[0] for x in pairs])
         self.pair_shells = [(a, b) for _, a, b in pairs]
         present = sorted(set(self.cls.tolist()))
@@ -306,6 +331,7 @@ class Problem:
         self.info, self.atoms = f(info, np.int32), f(atoms, np.int32)
         self.A, self.B, self.pp, self.pp2 = f(A, np.float64), f(B, np.float64), f(pp, np.float64), f(pp2, np.float64)
         self.ppf, self.ppf2, self.alpha = f(ppf, np.float32), f(ppf2, np.float32), f(alpha, np.float64)
+        self.pq = f(pq, np.float32) if prim_sort else None
         self.D = np.ascontiguousarray(D, dtype=np.float64)
         self.Df = self.D.astype(np.float32)
         # double-float data as the runtime lays them out: 5 float4 per primitive pair
@@ -342,13 +368,30 @@ class Problem:
     def _p(self, a):
         return a.ctypes.data_as(C.c_void_p)
 
-    def jk(self, prec, tsmall=1.0, lists=False):
+    def prim_cuts(self, bra, klist, taup):
+        """Per list entry the primitive cut taup / max|D| over the quartet's six
+        D blocks, in FP32 (the runtime's list fill)."""
+        off = self.mol.shell_offsets()
+        nc = [(int(x) + 1) * (int(x) + 2) // 2 for x in self.mol.shell_l]
+        blk = lambda x, y: float(np.abs(self.Df[off[x]:off[x] + nc[x], off[y]:off[y] + nc[y]]).max())
+        a, b = self.pair_shells[bra]
+        out = []
+        for j in klist:
+            c, d = self.pair_shells[j]
+            dq = np.float32(max(blk(a, b), blk(c, d), blk(a, c), blk(a, d), blk(b, c), blk(b, d)))
+            out.append(np.float32(taup) / dq)
+        return out
+
+    def jk(self, prec, tsmall=1.0, lists=False, pmode=0, taup=0.0):
         """J and K from the class kernels of one precision (0 FP64, 1 FP32, 2 FP32
         in Algorithm 1's order, 3 double-float).  lists=True hands every row's
         kets to the kernels as an explicit ket list (the form of a mixed build's
-        FP64 and demoted lists), in reversed order."""
+        FP64 and demoted lists), in reversed order.  pmode 1 / 2 (with lists and
+        a primitive-sorted problem): only the primitive quartets at / below the
+        cut taup / max|D| of each quartet (JKArgs::pmode)."""
         lib = load(self.lmax, self.only)
         lib.emu_set_df(self._p(self.ppd), self._p(self.boysd), self._p(self.Ddf))
+        assert pmode == 0 or (lists and self.pq is not None)
         J = np.zeros((self.nbf, self.nbf))
         K = np.zeros((self.nbf, self.nbf))
         for X in range(len(self.pcs)):
@@ -364,6 +407,14 @@ class Problem:
                     kofs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
                     klist = np.concatenate([np.arange(k0, k0 + c)[::-1] for k0, c in zip(ket0, cnt)]).astype(np.int32)
                     ket0 = np.zeros_like(ket0)
+                kthr = None
+                if pmode:
+                    kthr = np.ascontiguousarray(np.concatenate(
+                        [self.prim_cuts(int(i), klist[kofs[k]:kofs[k + 1]], taup) for k, i in enumerate(bra)]),
+                        dtype=np.float32)
+                    lib.emu_set_prim(self._p(self.pq), self._p(kthr), pmode)
+                else:
+                    lib.emu_set_prim(None if self.pq is None else self._p(self.pq), None, 0)
                 rc = lib.emu_jk(X, Y, prec, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
                                 self._p(self.pp), self._p(self.pp2), self._p(self.ppf), self._p(self.ppf2),
                                 self._p(self.alpha), len(bra), self._p(start), self._p(bra), self._p(ket0),

@@ -66,4 +66,4 @@ int main(void) {
                     lib, "-o", str(exe), f"-Wl,-rpath,{os.path.dirname(lib)}"], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out
-    assert out.stdout.split() == ["3", "3", "0.01"]
+    assert out.stdout.split() == ["3", "3", "0.005"]

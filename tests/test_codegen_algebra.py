@@ -108,7 +108,11 @@ def _if_chain(line):
 
 
 def to_python(body):
-    """Translate a generated kernel body (C) into Python source."""
+    """Translate a generated kernel body (C) into Python source.  The bodies
+    run here with every primitive quartet (primitive mode 0): the primitive
+    split's block (mg.PRIM_CUT) is reduced to its mode-0 ket range; the split
+    itself is exercised by tests/test_kernel_emulation.py."""
+    body = body.replace(mg.PRIM_CUT, "int jq0 = 0, jq1 = ik.z;")
     out, ind, stack, pending = [], 0, [], 0
 
     def emit(s, extra=0):

@@ -143,8 +143,9 @@ def test_double_float_tier(g, seed, shells, natom, kmax):
     tier off the same quartets run in FP64 and the two agree to 1e-11."""
     mol = molgen.random_molecule(500 + seed, natom, shells, 1, kmax, 0.05, 5e3, layout="lattice", spacing=2.2)
     D = molgen.density(mol, 600 + seed)
-    tau, df = g.get_option("mixed_tau"), g.get_option("df_tier")
+    tau, df, ptau = g.get_option("mixed_tau"), g.get_option("df_tier"), g.get_option("prim_tau")
     g.set_option("mixed_tau", 0.0)
+    g.set_option("prim_tau", 0.0)  # every primitive quartet of every quartet in the tier
     try:
         g.set_option("df_tier", 1)
         pairs, J, K, E = _run(g, mol, D, None, "mixed")
@@ -154,6 +155,7 @@ def test_double_float_tier(g, seed, shells, natom, kmax):
     finally:
         g.set_option("mixed_tau", tau)
         g.set_option("df_tier", df)
+        g.set_option("prim_tau", ptau)
     assert n32 == 0 and n64 == pairs.nquartets
     Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
     sJ, sK = max(1.0, np.abs(Jo).max()), max(1.0, np.abs(Ko).max())
@@ -161,3 +163,42 @@ def test_double_float_tier(g, seed, shells, natom, kmax):
     assert np.abs(K - Ko).max() <= 1e-11 * sK, np.abs(K - Ko).max() / sK
     assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-11 * max(1.0, abs(E))
     assert np.abs(J - J64).max() <= 1e-11 * sJ and np.abs(K - K64).max() <= 1e-11 * sK
+
+
+@pytest.mark.parametrize("df", [1, 0])
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(46, [0, 1, 2], 3, 4), (47, [2, 1], 3, 3)])
+def test_primitive_split(g, df, seed, shells, natom, kmax):
+    """The primitive split of the FP64-selected quartets (JK_OPT_PRIM_TAU) with
+    every quartet FP64-selected (tau 0): a vanishing cut leaves every primitive
+    quartet in the FP64 / double-float tier (the unsplit result); an
+    unreachable cut sends every primitive quartet to the FP32 complement (the
+    all-FP32 result, to FP32 rounding of the oracle); a cut in between splits
+    the work and stays within FP32 rounding of the part below it."""
+    mol = molgen.random_molecule(500 + seed, natom, shells, 1, kmax, 0.05, 5e3, layout="lattice", spacing=2.2)
+    D = molgen.density(mol, 600 + seed)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    sJ, sK = max(1.0, np.abs(Jo).max()), max(1.0, np.abs(Ko).max())
+    old = {k: g.get_option(k) for k in ("mixed_tau", "df_tier", "prim_tau")}
+    res = {}
+    try:
+        g.set_option("mixed_tau", 0.0)
+        g.set_option("df_tier", df)
+        for ptau in (0.0, 1e-300, 1e300, 1e-3):
+            g.set_option("prim_tau", ptau)
+            pairs, J, K, E = _run(g, mol, D, None, "mixed")
+            st = g.split_stats(pairs)
+            res[ptau] = (J, K, sum(s["fp64"]["nprimq"] for s in st), sum(s["fp32"]["nprimq"] for s in st))
+    finally:
+        for k, v in old.items():
+            g.set_option(k, v)
+    J0, K0, p64, p32 = res[0.0]
+    assert p32 == 0 and p64 == pairs.nprimquartets
+    J, K, q64, q32 = res[1e-300]
+    assert (q64, q32) == (p64, 0)
+    assert np.abs(J - J0).max() <= 1e-12 * sJ and np.abs(K - K0).max() <= 1e-12 * sK
+    J, K, q64, q32 = res[1e300]
+    assert (q64, q32) == (0, p64)
+    assert np.abs(J - Jo).max() <= 2e-6 * np.abs(Jo).max() and np.abs(K - Ko).max() <= 2e-6 * np.abs(Ko).max()
+    J, K, q64, q32 = res[1e-3]
+    assert q64 > 0 and q32 > 0 and q64 + q32 == p64
+    assert np.abs(J - Jo).max() <= 2e-6 * sJ and np.abs(K - Ko).max() <= 2e-6 * sK

@@ -30,7 +30,8 @@ def _one_s_shell(nprim=1):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nprim", [1, 3])
 def test_one_basis_function(g, prec, nprim):
-    """nbf = 1: one pair, one quartet, J = K = (ss|ss) D."""
+    """nbf = 1: one pair, one quartet, J = K = (ss|ss) D (a mixed build runs
+    the quartet's small primitive quartets in FP32: the mixed target, 1e-6 Eh)."""
     mol = _one_s_shell(nprim)
     pairs = g.ShellPairs(mol)
     assert (pairs.nbf, pairs.npairs, pairs.nquartets) == (1, 1, 1)
@@ -39,9 +40,10 @@ def test_one_basis_function(g, prec, nprim):
     J, K = g.jk_build(pairs, Dt, prec)
     E = g.jk_energy(Dt, J, K)
     Jo, Ko, _ = oracle.jk(mol, D, mode="all")
-    assert abs(float(J[0, 0]) - Jo[0, 0]) <= 1e-10 * Jo[0, 0]
-    assert abs(float(K[0, 0]) - Ko[0, 0]) <= 1e-10 * Ko[0, 0]
-    assert abs(E - oracle.energy(D, Jo, Ko)) <= 1e-10 * abs(E)
+    tol = 1e-10 * Jo[0, 0] if prec == "fp64" else 1e-6
+    assert abs(float(J[0, 0]) - Jo[0, 0]) <= tol
+    assert abs(float(K[0, 0]) - Ko[0, 0]) <= tol
+    assert abs(E - oracle.energy(D, Jo, Ko)) <= (1e-10 * abs(E) if prec == "fp64" else 1e-6)
     gr = g.jk_grad(pairs, Dt, "fp64").cpu().numpy()
     assert np.abs(gr).max() <= 1e-12 * abs(E)  # one centre: no geometry dependence
 
@@ -80,7 +82,8 @@ def test_zero_density_mixed(g):
 def test_batch_with_degenerate_molecules(g, prec):
     """One launch sequence over an ordinary molecule, a one-function molecule
     and a molecule with no surviving pair: each result equals its own
-    single-molecule build."""
+    single-molecule build (a mixed build's FP32 sums are grouped over other
+    warp lanes in a batch: FP32 rounding)."""
     mol0, D0 = molgen.config(0)
     mol1 = _one_s_shell(3)
     D1 = np.array([[0.6]])
@@ -89,9 +92,9 @@ def test_batch_with_degenerate_molecules(g, prec):
     Js, Ks = g.jk_build_batched(plist, Ds, precision=prec)
     for p, D, Jb, Kb in zip(plist, Ds, Js, Ks):
         J, K = g.jk_build(p, D, prec)
-        scale = max(1.0, float(J.abs().max()))
-        assert float((Jb - J).abs().max()) <= 1e-10 * scale
-        assert float((Kb - K).abs().max()) <= 1e-10 * scale
+        scale = max(1.0, float(J.abs().max())) * (1e-10 if prec == "fp64" else 1e-6)
+        assert float((Jb - J).abs().max()) <= scale
+        assert float((Kb - K).abs().max()) <= scale
     assert int(torch.count_nonzero(Js[2])) == 0 and int(torch.count_nonzero(Ks[2])) == 0
 
 

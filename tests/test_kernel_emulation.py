@@ -149,3 +149,35 @@ def test_emulated_batched_mode():
             Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
             assert np.abs(J - Jo).max() <= tol * max(1.0, np.abs(Jo).max()), prec
             assert np.abs(K - Ko).max() <= tol * max(1.0, np.abs(Ko).max()), prec
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(81, [0, 1, 2], 2, 4), (82, [2, 1], 3, 3)])
+def test_emulated_primitive_split(seed, shells, natom, kmax):
+    """The primitive split of a mixed build's FP64 list: with each pair's
+    primitive pairs sorted by their Schwarz factor, the kernels' primitive
+    mode 1 (quartets at or above the cut) and mode 2 (below it) together
+    evaluate every primitive quartet exactly once -- FP64 mode 1 + FP64 mode 2
+    equals the unsplit FP64 build -- and mode 2 in FP32 beside mode 1 in FP64
+    or double-float stays within FP32 rounding of the cut part."""
+    mol, D = _mol(seed, shells, natom, kmax)
+    pr = kernel_emu.Problem(mol, D, oracle, prim_sort=True)
+    Jo, Ko, _ = oracle.jk(mol, D, mode="unique")
+    J0, K0 = pr.jk(0, lists=True)
+    assert np.abs(J0 - Jo).max() <= 1e-10 * max(1.0, np.abs(Jo).max())
+    taup = 1e-3
+    J1, K1 = pr.jk(0, lists=True, pmode=1, taup=taup)
+    J2, K2 = pr.jk(0, lists=True, pmode=2, taup=taup)
+    scale = max(1.0, np.abs(J0).max(), np.abs(K0).max())
+    # a real split: both modes carry work
+    assert np.abs(J1).max() > 1e-3 * scale and np.abs(J2).max() > 0.0
+    assert np.abs(J1 + J2 - J0).max() <= 1e-12 * scale and np.abs(K1 + K2 - K0).max() <= 1e-12 * scale
+    # the cut part in FP32: its error is FP32 rounding of that part alone
+    J2f, K2f = pr.jk(1, lists=True, pmode=2, taup=taup)
+    part = max(np.abs(J2).max(), np.abs(K2).max())
+    assert np.abs(J2f - J2).max() <= 2e-6 * part and np.abs(K2f - K2).max() <= 2e-6 * part
+    J1d, K1d = pr.jk(3, lists=True, pmode=1, taup=taup)
+    assert np.abs(J1d + J2f - Jo).max() <= 2e-6 * part + 1e-10 * scale
+    assert np.abs(K1d + K2f - Ko).max() <= 2e-6 * part + 1e-10 * scale
+    # a cut of zero keeps everything in mode 1 (and nothing in mode 2)
+    Jz, Kz = pr.jk(0, lists=True, pmode=2, taup=0.0)
+    assert np.abs(Jz).max() == 0.0 and np.abs(Kz).max() == 0.0

@@ -22,7 +22,12 @@ def _excl(x):
     return np.concatenate([[0], np.cumsum(x)]).astype(np.int64)
 
 
-def _mixed_build(pr, tau, eps):
+def _mixed_build(pr, tau, eps, taup=0.0):
+    """A mixed build as the runtime runs it: split counts, list fill, then the
+    FP64 list, the FP32 suffix and the demoted list through the class kernels;
+    with taup > 0 (a primitive-sorted problem) the FP64 list runs its large
+    primitive quartets in FP64 (primitive mode 1) and the rest in FP32 over the
+    same list (mode 2)."""
     lib = kernel_emu.load(pr.lmax, pr.only)
     split = build_split_lib()
     mol, D, n = pr.mol, pr.D, pr.nbf
@@ -59,13 +64,18 @@ def _mixed_build(pr, tau, eps):
             l64, ldem = _excl(cnt["c64"][:nr]), _excl(cnt["cdem"][:nr])
             list64 = np.zeros(max(1, l64[-1]), np.int32)
             listdem = np.zeros(max(1, ldem[-1]), np.int32)
+            thr64 = np.zeros(max(1, l64[-1]), np.float32)
             split.emu_fill(bra.ctypes.data, ket0.ctypes.data, k32.ctypes.data, nr, pr.A.ctypes.data, tau, eps,
                            psh.ctypes.data, dsh.ctypes.data, S, l64.ctypes.data, ldem.ctypes.data,
-                           list64.ctypes.data, listdem.ctypes.data)
-            for prec, st, k0, ko, kl in ((0, s64, None, l64, list64), (1, s32, k32, None, None),
-                                         (1, sdem, None, ldem, listdem)):
+                           list64.ctypes.data, listdem.ctypes.data, taup, thr64.ctypes.data if taup > 0 else None)
+            launches = [(0, s64, None, l64, list64, 1 if taup > 0 else 0), (1, s32, k32, None, None, 0),
+                        (1, sdem, None, ldem, listdem, 0)]
+            if taup > 0:
+                launches.append((1, s64, None, l64, list64, 2))
+            for prec, st, k0, ko, kl, pmode in launches:
                 if st[-1] == 0:
                     continue
+                lib.emu_set_prim(None if pr.pq is None else p(pr.pq), p(thr64) if pmode else None, pmode)
                 rc = lib.emu_jk(X, Y, prec, *common(), nr, p(st), p(bra), None if k0 is None else p(k0),
                                 None if ko is None else p(ko), None if kl is None else p(kl), *tail())
                 assert rc == 0
@@ -91,14 +101,18 @@ def _mixed_build(pr, tau, eps):
     return J + J.T, K + K.T, np.array(quartets, np.int32), parts
 
 
-@pytest.mark.parametrize("seed,shells,scale,tau,eps", [(81, [0, 1, 2], 1.0, 1e-2, 0.0), (82, [0, 1, 2], 1e-2, 1e-2, 1e-7),
-                                                       (83, [2, 0, 1], 1e-3, 0.0, 1e-8), (84, [0, 1, 3], 1e-2, 1e-3, 1e-7)])
-def test_mixed_build_with_screening_matches_oracle(seed, shells, scale, tau, eps):
+@pytest.mark.parametrize("seed,shells,scale,tau,eps,taup", [(81, [0, 1, 2], 1.0, 1e-2, 0.0, 0.0),
+                                                            (82, [0, 1, 2], 1e-2, 1e-2, 1e-7, 0.0),
+                                                            (83, [2, 0, 1], 1e-3, 0.0, 1e-8, 0.0),
+                                                            (84, [0, 1, 3], 1e-2, 1e-3, 1e-7, 0.0),
+                                                            (81, [0, 1, 2], 1.0, 1e-2, 0.0, 1e-3),
+                                                            (84, [0, 1, 3], 1e-2, 1e-3, 1e-7, 1e-5)])
+def test_mixed_build_with_screening_matches_oracle(seed, shells, scale, tau, eps, taup):
     mol = molgen.random_molecule(1000 + seed, 3, shells, 1, 3, 0.1, 50.0, layout="lattice", spacing=2.2)
     D = molgen.density(mol, 1100 + seed) * scale
     lmax = max(shells)
-    pr = kernel_emu.Problem(mol, D, oracle, lmax=lmax, own_classes=True, q_order=True)
-    J, K, q, parts = _mixed_build(pr, tau, eps)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=lmax, own_classes=True, q_order=True, prim_sort=taup > 0)
+    J, K, q, parts = _mixed_build(pr, tau, eps, taup)
     if tau == 0.0:  # FP64 build with screening: every kept quartet in the FP64 list
         assert parts["fp32"] == parts["dem"] == 0 and parts["fp64"] == len(q)
     elif seed in (81, 84):  # all three launch forms run

@@ -43,12 +43,12 @@ extern "C" void emu_split(const long long* start, const int* rbra, const int* rk
 }
 extern "C" void emu_fill(const int* rbra, const int* rket0, const int* k32, int nrows, const double* A4, double tau,
                          double eps, const int* psh2, const float* dsh, int nshell, const long long* l64,
-                         const long long* ldem, int* list64, int* listdem) {
+                         const long long* ldem, int* list64, int* listdem, float taup, float* thr64) {
     blockDim = {1, 1, 1}; gridDim = {(unsigned)nrows, 1, 1}; threadIdx = {0, 0, 0};
     for (int r = 0; r < nrows; ++r) {
         blockIdx = {(unsigned)r, 0, 0};
         k_rows_fill(rbra, rket0, k32, nrows, reinterpret_cast<const double4*>(A4), tau, eps,
-                    reinterpret_cast<const int2*>(psh2), dsh, nshell, l64, ldem, list64, listdem);
+                    reinterpret_cast<const int2*>(psh2), dsh, nshell, l64, ldem, list64, listdem, taup, thr64);
     }
 }
 """
@@ -75,7 +75,8 @@ def build_split_lib():
     vp = C.c_void_p
     L.emu_split.argtypes = ([vp, vp, vp, C.c_int, vp, C.c_double, C.c_double, C.c_double, vp, vp, vp, C.c_int, C.c_int]
                             + [vp] * 8)
-    L.emu_fill.argtypes = [vp, vp, vp, C.c_int, vp, C.c_double, C.c_double, vp, vp, C.c_int, vp, vp, vp, vp]
+    L.emu_fill.argtypes = [vp, vp, vp, C.c_int, vp, C.c_double, C.c_double, vp, vp, C.c_int, vp, vp, vp, vp,
+                           C.c_float, vp]
     return L
 
 
@@ -133,9 +134,11 @@ def test_split_and_fill_follow_the_rule(lib, seed, tau, eps):
     ldem = np.concatenate([[0], np.cumsum(out["cdem"][:n])]).astype(np.int64)
     list64 = np.full(max(1, l64[-1]), -1, np.int32)
     listdem = np.full(max(1, ldem[-1]), -1, np.int32)
+    thr64 = np.full(max(1, l64[-1]), -1.0, np.float32)
+    taup = np.float32(tau / 10)
     lib.emu_fill(rbra.ctypes.data, rket0.ctypes.data, k32.ctypes.data, n, A.ctypes.data, tau, eps,
                  psh.ctypes.data, dsh.ctypes.data, dsh.shape[0], l64.ctypes.data, ldem.ctypes.data,
-                 list64.ctypes.data, listdem.ctypes.data)
+                 list64.ctypes.data, listdem.ctypes.data, taup, thr64.ctypes.data)
     tot = {"fp64": 0, "dem": 0, "fp32": 0, "skip": 0}
     for r in range(n):
         i, s, c = int(rbra[r]), int(rket0[r]), int(start[r + 1] - start[r])
@@ -152,6 +155,12 @@ def test_split_and_fill_follow_the_rule(lib, seed, tau, eps):
         assert want32 == list(range(int(k32[r]), int(k32[r]) + len(want32)))
         assert list(list64[l64[r]:l64[r + 1]]) == want64
         assert list(listdem[ldem[r]:ldem[r + 1]]) == wantdem
+        # primitive cut of every FP64 entry: taup over the largest |D| of the quartet's six blocks, in FP32
+        (a, b) = psh[i]
+        for e, j in zip(range(l64[r], l64[r + 1]), want64):
+            (c, d) = psh[j]
+            dq = np.float32(max(dsh[a, b], dsh[c, d], dsh[a, c], dsh[a, d], dsh[b, c], dsh[b, d]))
+            assert thr64[e] == np.float32(taup / dq), (thr64[e], taup / dq)
     assert int(qtot[0]) == tot["fp32"] + tot["dem"] and int(qtot[1]) == tot["fp64"] and int(qtot[7]) == tot["dem"]
     if eps == 0.0:
         assert tot["skip"] == 0
