@@ -261,7 +261,7 @@ typedef enum {
                                   * double-float arithmetic -- every value an unevaluated sum of two
                                   * floats, ~44 significant bits, all on the FP32 pipe -- instead of
                                   * FP64 (default 0); the FP64 build is unaffected */
-    JK_OPT_PRIM_TAU = 10         /* mixed builds (single and batched): primitive split of the quartets kept
+    JK_OPT_PRIM_TAU = 10,        /* mixed builds (single and batched): primitive split of the quartets kept
                                   * out of FP32.  Each pair's primitive pairs carry their own Schwarz factor
                                   * q_p (shellpairs_build); of such a quartet only the primitive quartets
                                   * with q_p q_q max|D| >= this value (max|D| over the quartet's six D
@@ -269,6 +269,10 @@ typedef enum {
                                   * in FP32, added into the same J and K.  0 turns the split off (every
                                   * primitive quartet of such a quartet in FP64 / double-float); default
                                   * 1e-4 */
+    JK_OPT_GRAD_PRIM_TAU = 11    /* mixed gradient: the same primitive split of the quartets whose bound
+                                  * reaches JK_OPT_GRAD_TAU -- their derivative integrals of primitive
+                                  * quartets with q_p q_q max|D| below this value by the FP32 derivative
+                                  * kernels, the others in FP64; 0 turns it off; default 1e-6 */
 } jk_option;
 int jk_set_option(jk_option opt, double value);
 int jk_get_option(jk_option opt, double* value);

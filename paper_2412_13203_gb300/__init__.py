@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgb300eri.so")
 
 JK_OPT = {"mixed_tau": 0, "mixed_tsmall": 1, "check_symmetry": 2, "graph": 3, "profile": 4, "density_screen": 5,
-          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8, "df_tier": 9, "prim_tau": 10}
+          "rpath": 6, "fail_alloc_after": 7, "grad_tau": 8, "df_tier": 9, "prim_tau": 10, "grad_prim_tau": 11}
 _PREC = {"fp64": 0, "mixed": 1}
 
 _lib = None

@@ -1130,6 +1130,10 @@ def gen_grad_kernel(bra, ket, prec="f64"):
     E("const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)")
     E("                                : __ldg(args.rows.ket0 + row) + (int)qo;")
     E("const int4 ik = pairs.info[ket];")
+    E("const int pmode = args.pmode;")
+    E("const float pthr = pmode ? __ldg(args.rows.kthr + __ldg(args.rows.kofs + row) + qo) : 0.f;")
+    E("if (pmode == 1 && __fmul_rn(__ldg(pairs.pq + ib.w + ipart), __ldg(pairs.pq + ik.w)) < pthr)")
+    E("  continue;  // primitive mode 1: nothing of this item reaches the cut")
     if f32:
         E("const float4 ah = pairs.Ahl[2 * bra], al = pairs.Ahl[2 * bra + 1];")
         E("const float4 ch = pairs.Ahl[2 * ket], cl = pairs.Ahl[2 * ket + 1];")
@@ -1157,6 +1161,7 @@ def gen_grad_kernel(bra, ket, prec="f64"):
     E(f"{real} XC[{3 * H0 * NCDx}];")
     E(f"{real} Rc[{S * S * S}];")
     E("for (int ip = ipart; ip < ib.z; ip += nsplit) {")
+    E(PRIM_CUT)
     if f32:
         E("const float4 pa = pairs.ppf[ib.w + ip]; const float4 pb = pairs.ppf2[ib.w + ip];")
         E("const float p = pa.w, kp = pb.w, inv2p = __fdividef(0.5f, p);")
@@ -1175,7 +1180,7 @@ def gen_grad_kernel(bra, ket, prec="f64"):
         _store_axis_array(E, em, f"eb{ax}", la + 1, lb + 1, Eb, real)
     E(f"for (int i = 0; i < {H1 * NCDx}; ++i) X[i] = 0;")
     E(f"for (int i = 0; i < {3 * H0 * NCDx}; ++i) XC[i] = 0;")
-    E("for (int jq = 0; jq < ik.z; ++jq) {")
+    E("for (int jq = jq0; jq < jq1; ++jq) {")
     if f32:
         E("const float4 qa = pairs.ppf[ik.w + jq]; const float4 qb = pairs.ppf2[ik.w + jq];")
         E("const float q = qa.w, kq = qb.w, inv2q = __fdividef(0.5f, q), gam2 = 2.0f * (float)pairs.alpha[ik.w + jq];")

@@ -191,6 +191,7 @@ struct GradArgs {
     int nbf;
     const int2* atoms;        // per pair: atoms of shells a and b
     double* grad;             // [natom * 3], accumulated
+    int pmode;                // primitive split of a mixed gradient's FP64 list (as JKArgs::pmode)
 };
 
 // Schwarz kernels spread the bra primitive pairs of a pair over up to this

@@ -157,6 +157,7 @@ struct Options {
                        // faster once the primitive split leaves only their large primitive quartets)
     double grad_tau = 3e-4;  // mixed gradient: FP32 derivative integrals iff the quartet's bound is below this
     double ptau = 1e-4;  // mixed builds: primitive quartets of the FP64 list below this bound run in FP32 (0: off)
+    double grad_ptau = 1e-6;  // mixed gradient: the same split of its FP64 list (0: off)
 } g_opt;
 
 struct ProfRec {
@@ -2426,7 +2427,8 @@ int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR
     h->launches = 0;
     // one launch over rows [r0, r1) of a class: per-row item prefix `start`,
     // contiguous kets from ket0 or explicit ones (kofs/klist)
-    auto launch = [&](int k, int kp, const long long* start, const int* ket0, const long long* kofs, const int* klist) {
+    auto launch = [&](int k, int kp, const long long* start, const int* ket0, const long long* kofs, const int* klist,
+                      int pmode = 0, const float* kthr = nullptr) {
         const ClassRows& cr = h->rows[k];
         const int r0 = R0[k], nr = R1[k] - R0[k];
         gb::GradArgs a;
@@ -2438,6 +2440,8 @@ int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR
         a.rows.ket0 = ket0 ? ket0 + r0 : nullptr;
         a.rows.kofs = kofs ? kofs + r0 : nullptr;
         a.rows.klist = klist;
+        a.rows.kthr = kthr;
+        a.pmode = (klist && kthr) ? pmode : 0;
         a.boys = g_boys[h->device].tab.as<double>();
         a.boysf = g_boys[h->device].tabf.as<float>();
         a.tsmall = (float)g_opt.tsmall;
@@ -2491,20 +2495,27 @@ int jk_grad_part(jk_pairs h, int part, int nparts, const double* D, double* dEdR
     }
     if ((rc = h->list64.alloc(sizeof(int) * std::max(1LL, off64[ncr])))) return rc;
     if ((rc = h->listdem.alloc(sizeof(int) * std::max(1LL, offd[ncr])))) return rc;
+    const bool psplit = g_opt.grad_ptau > 0.0;
+    if (psplit && (rc = h->thr64.alloc(sizeof(float) * std::max(1LL, off64[ncr])))) return rc;
     for (int k = 0; k < ncr; ++k) {
         ClassRows& cr = h->rows[k];
         if (cr.total <= 0 || R1[k] <= R0[k]) continue;
         int* l64 = h->list64.as<int>() + off64[k];
         int* ldm = h->listdem.as<int>() + offd[k];
+        float* t64 = psplit ? h->thr64.as<float>() + off64[k] : nullptr;
         if ((rc = split_fill(h, cr, R0[k], R1[k], h->split_tot.as<long long>() + kSplitSlots * k, l64, ldm, st,
-                             g_opt.grad_tau, 0.0, 0.f, nullptr)))
+                             g_opt.grad_tau, 0.0, (float)g_opt.grad_ptau, t64)))
             return rc;
-        if ((rc = launch(k, 0, cr.s64.as<long long>(), nullptr, cr.l64.as<long long>(), l64))) return rc;
+        // the large-bound quartets in FP64 (with the primitive split: their large primitive
+        // quartets, the rest by the FP32 derivative kernels over the same list)
+        if ((rc = launch(k, 0, cr.s64.as<long long>(), nullptr, cr.l64.as<long long>(), l64, 1, t64))) return rc;
+        if (psplit && (rc = launch(k, 1, cr.s64.as<long long>(), nullptr, cr.l64.as<long long>(), l64, 2, t64)))
+            return rc;
         if ((rc = launch(k, 1, cr.s32.as<long long>(), cr.k32.as<int>(), nullptr, nullptr))) return rc;
         if ((rc = launch(k, 1, cr.sdem.as<long long>(), nullptr, cr.ldem.as<long long>(), ldm))) return rc;
     }
     // the split diagnostics (jk_last_split, jk_split_stats) now describe this gradient
-    h->last_psplit = false;
+    h->last_psplit = psplit;
     h->list_off64 = off64;
     h->list_offd = offd;
     h->last_r0 = R0;
@@ -2621,6 +2632,10 @@ int jk_set_option(jk_option opt, double v) {
             return JK_OK;
         case JK_OPT_DF_TIER: g_opt.df_tier = v != 0.0; return JK_OK;
         case JK_OPT_PRIM_TAU: if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "primitive tau"); g_opt.ptau = v; return JK_OK;
+        case JK_OPT_GRAD_PRIM_TAU:
+            if (!(v >= 0) || !std::isfinite(v)) return fail(JK_ERR_INVALID, "gradient primitive tau");
+            g_opt.grad_ptau = v;
+            return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }
@@ -2639,6 +2654,7 @@ int jk_get_option(jk_option opt, double* v) {
         case JK_OPT_GRAD_TAU: *v = g_opt.grad_tau; return JK_OK;
         case JK_OPT_DF_TIER: *v = g_opt.df_tier; return JK_OK;
         case JK_OPT_PRIM_TAU: *v = g_opt.ptau; return JK_OK;
+        case JK_OPT_GRAD_PRIM_TAU: *v = g_opt.grad_ptau; return JK_OK;
     }
     return fail(JK_ERR_INVALID, "unknown option");
 }

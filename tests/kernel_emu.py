@@ -97,6 +97,10 @@ static int g_pmode = 0;
 extern "C" void emu_set_prim(const float* pq, const float* kthr, int pmode) {
     g_pq = pq; g_kthr = kthr; g_pmode = pmode;
 }
+// explicit ket lists of the next emu_grad call (nullptr: contiguous kets)
+static const long long* g_gkofs = nullptr;
+static const int* g_gklist = nullptr;
+extern "C" void emu_set_grad_lists(const long long* kofs, const int* klist) { g_gkofs = kofs; g_gklist = klist; }
 static gb::PairsView pv(int npair, const int4* info, const double4* A, const double4* B, const double4* pp,
                         const double2* pp2, const float4* ppf, const float4* ppf2, const double* alpha) {
     gb::PairsView v;
@@ -195,6 +199,9 @@ extern "C" int emu_grad(int X, int Y, int prec, int npair, const int4* info, con
     std::memset(&g, 0, sizeof(g));
     g.pairs = pv(npair, info, A, B, pp, pp2, ppf, ppf2, alpha);
     g.rows.nrows = nrows; g.rows.start = start; g.rows.bra = bra; g.rows.ket0 = ket0;
+    g.rows.kofs = g_gkofs; g.rows.klist = g_gklist;
+    g.rows.kthr = g_gklist ? g_kthr : nullptr;
+    g.pmode = g_gklist && g_kthr ? g_pmode : 0;
     g.boys = boys; g.boysf = boysf; g.tsmall = tsmall; g.D = D; g.nbf = nbf; g.atoms = atoms; g.grad = grad;
     blockIdx = {0, 0, 0}; threadIdx = {0, 0, 0}; blockDim = {1, 1, 1}; gridDim = {1, 1, 1};
     switch (X * 16 + Y) {
@@ -439,9 +446,12 @@ class Problem:
             assert rc == 0
         return Q
 
-    def grad(self, prec=0, tsmall=0.0):
-        """dE/dR from the derivative kernels of one precision (0 FP64, 1 FP32)."""
+    def grad(self, prec=0, tsmall=0.0, lists=False, pmode=0, taup=0.0):
+        """dE/dR from the derivative kernels of one precision (0 FP64, 1 FP32);
+        lists / pmode / taup as for jk() (the mixed gradient's FP64 list and its
+        primitive split)."""
         lib = load(self.lmax, self.only)
+        assert pmode == 0 or (lists and self.pq is not None)
         g = np.zeros((self.mol.xyz.shape[0], 3))
         for X in range(len(self.pcs)):
             for Y in range(X + 1):
@@ -449,11 +459,26 @@ class Problem:
                 if r is None:
                     continue
                 bra, ket0, start = r
+                kofs = klist = kthr = None
+                if lists:
+                    cnt = np.array([(i - ket0[k] + 1) if X == Y else int((self.cls == Y).sum())
+                                    for k, i in enumerate(bra)], dtype=np.int64)
+                    kofs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+                    klist = np.concatenate([np.arange(k0, k0 + c)[::-1] for k0, c in zip(ket0, cnt)]).astype(np.int32)
+                    if pmode:
+                        kthr = np.ascontiguousarray(np.concatenate(
+                            [self.prim_cuts(int(i), klist[kofs[k]:kofs[k + 1]], taup) for k, i in enumerate(bra)]),
+                            dtype=np.float32)
+                lib.emu_set_prim(None if self.pq is None else self._p(self.pq),
+                                 None if kthr is None else self._p(kthr), pmode)
+                lib.emu_set_grad_lists(None if kofs is None else self._p(kofs),
+                                       None if klist is None else self._p(klist))
                 rc = lib.emu_grad(X, Y, prec, len(self.info), self._p(self.info), self._p(self.A), self._p(self.B),
                                   self._p(self.pp), self._p(self.pp2), self._p(self.ppf), self._p(self.ppf2),
                                   self._p(self.alpha), len(bra), self._p(start), self._p(bra), self._p(ket0),
                                   self._p(self.boys), self._p(self.boysf), C.c_float(tsmall), self._p(self.D),
                                   self.nbf, self._p(self.atoms), self._p(g))
+                lib.emu_set_grad_lists(None, None)
                 assert rc == 0
         return g
 

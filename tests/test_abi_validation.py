@@ -146,8 +146,10 @@ def test_options_round_trip_and_validation(lib):
     tau0 = v.value
     assert tau0 == pytest.approx(5e-3)
     assert lib.jk_get_option(10, C.byref(v)) == JK_OK and v.value == pytest.approx(1e-4)  # JK_OPT_PRIM_TAU
+    assert lib.jk_get_option(11, C.byref(v)) == JK_OK and v.value == pytest.approx(1e-6)  # JK_OPT_GRAD_PRIM_TAU
     for bad in (-1e-3, math.nan, math.inf):
         assert lib.jk_set_option(10, bad) == JK_ERR_INVALID
+        assert lib.jk_set_option(11, bad) == JK_ERR_INVALID
     try:
         assert lib.jk_set_option(OPT_TAU, 3e-3) == JK_OK
         assert lib.jk_get_option(OPT_TAU, C.byref(v)) == JK_OK and v.value == 3e-3

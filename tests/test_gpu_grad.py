@@ -120,3 +120,33 @@ def test_mixed_gradient_24_atoms(g):
     gs = sum(g.jk_grad_part(pairs, Dt, p, 2, "mixed") for p in range(2))
     assert float((gs - gm).abs().max()) <= 1e-9 * float(gm.abs().max())
     pairs.free()
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(6, [0, 1, 2], 3, 4), (7, [1, 3], 2, 2)])
+def test_gradient_primitive_split(g, seed, shells, natom, kmax):
+    """The primitive split of the mixed gradient's FP64 list (JK_OPT_GRAD_PRIM_TAU)
+    with every quartet FP64-selected (grad_tau 0): a vanishing cut gives the
+    unsplit FP64 gradient, an unreachable one the FP32 derivative kernels
+    alone (FP32 rounding of the oracle), the default cut the oracle to 1e-6."""
+    mol = molgen.random_molecule(300 + seed, natom, shells, 1, kmax, 0.1, 50.0, layout="lattice", spacing=1.8)
+    D = molgen.density(mol, 400 + seed)
+    pairs = g.ShellPairs(mol)
+    Dt = torch.from_numpy(D).cuda()
+    go = oracle.grad(mol, D, mode="unique")
+    scale = max(1.0, np.abs(go).max())
+    old = {k: g.get_option(k) for k in ("grad_tau", "grad_prim_tau")}
+    out = {}
+    try:
+        g.set_option("grad_tau", 0.0)
+        for pt in (0.0, 1e-300, 1e300, old["grad_prim_tau"]):
+            g.set_option("grad_prim_tau", pt)
+            out[pt] = g.jk_grad(pairs, Dt, "mixed").cpu().numpy()
+            assert g.last_split(pairs)[1] == pairs.nquartets
+    finally:
+        for k, v in old.items():
+            g.set_option(k, v)
+    assert np.abs(out[0.0] - go).max() <= 1e-10 * scale
+    assert np.abs(out[1e-300] - out[0.0]).max() <= 1e-12 * scale
+    assert np.abs(out[1e300] - go).max() <= 2e-6 * scale
+    assert np.abs(out[old["grad_prim_tau"]] - go).max() <= 1e-6
+    pairs.free()

@@ -181,3 +181,24 @@ def test_emulated_primitive_split(seed, shells, natom, kmax):
     # a cut of zero keeps everything in mode 1 (and nothing in mode 2)
     Jz, Kz = pr.jk(0, lists=True, pmode=2, taup=0.0)
     assert np.abs(Jz).max() == 0.0 and np.abs(Kz).max() == 0.0
+
+
+@pytest.mark.parametrize("seed,shells,natom,kmax", [(83, [0, 1, 2], 2, 3), (84, [1, 3], 2, 2)])
+def test_emulated_gradient_primitive_split(seed, shells, natom, kmax):
+    """The derivative kernels' primitive modes (the mixed gradient's FP64 list
+    split at a primitive cut): FP64 mode 1 + FP64 mode 2 equals the unsplit
+    FP64 gradient, and FP64 mode 1 + FP32 mode 2 stays within FP32 rounding of
+    the part below the cut."""
+    mol, D = _mol(seed, shells, natom, kmax)
+    pr = kernel_emu.Problem(mol, D, oracle, lmax=max(shells), prim_sort=True)
+    go = oracle.grad(mol, D, mode="unique")
+    g0 = pr.grad(0, lists=True)
+    scale = max(1.0, np.abs(go).max())
+    assert np.abs(g0 - go).max() <= 1e-10 * scale
+    taup = 1e-4
+    g1 = pr.grad(0, lists=True, pmode=1, taup=taup)
+    g2 = pr.grad(0, lists=True, pmode=2, taup=taup)
+    assert np.abs(g1).max() > 1e-3 * scale and np.abs(g2).max() > 0.0
+    assert np.abs(g1 + g2 - g0).max() <= 1e-12 * scale
+    g2f = pr.grad(1, lists=True, pmode=2, taup=taup)
+    assert np.abs(g2f - g2).max() <= 2e-6 * max(np.abs(g2).max(), 1e-300)
