@@ -798,6 +798,15 @@ def cd_table(lc, ld):
     return f"static __device__ __constant__ int c_cd_tab_{lc}{ld}[{len(rows)}] = {{{', '.join(map(str, rows))}}};"
 
 
+def item_split(P, z):
+    """Work items of one quartet (gb::item_split): the largest divisor of the
+    bra pair's primitive-pair count z not above P."""
+    d = min(P, z)
+    while d > 1 and z % d:
+        d -= 1
+    return max(d, 1)
+
+
 def split_of(bra, ket):
     """Most threads one shell quartet's bra primitive pairs are spread over:
     heavy classes are split so that the launch balances over quartets of very
@@ -911,7 +920,7 @@ __global__ void __launch_bounds__({lbounds}) eri_jk_{name}_{prec}{suffix}(const 
   // persistent grid-stride loop over the quartets of this launch; the total is
   // read on the device (last entry of the row prefix) so launches need no host sync
   // Work items: rows.start is the prefix of items per row, a row's quartet
-  // being split into min({P}, K_ab) items over its bra primitive pairs; each
+  // being split into gb::item_split({P}, K_ab) items over its bra primitive pairs; each
   // item runs as {nch} thread(s) (one per Cartesian component of the ket's
   // first shell).  Items are taken from the end: the rows are ordered by
   // ascending ket primitive count, so the heaviest work goes first and the
@@ -950,7 +959,7 @@ __global__ void __launch_bounds__({lbounds}) eri_jk_{name}_{prec}{suffix}(const 
     Jlm = bm.Jlo; Klm = bm.Klo;
   }}
   const int4 ib = pairs.info[bra];
-  const int nsplit = min({P}, ib.z);
+  const int nsplit = gb::item_split({P}, ib.z);
   const long long qo = li / nsplit;
   const int ipart = (int)(li - qo * nsplit);
   const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)
@@ -1105,7 +1114,7 @@ def gen_grad_kernel(bra, ket, prec="f64"):
     E(f"const long long total = (args.rows.start[args.rows.nrows] - base) * {nthr};")
     E("for (long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x; gt < total;")
     E("     gt += (long long)gridDim.x * blockDim.x) {")
-    # work items as in the J/K kernels: a quartet split into min(P, K_ab) items
+    # work items as in the J/K kernels: a quartet split into item_split(P, K_ab) items
     # over its bra primitive pairs, heaviest rows (largest ket primitive count,
     # at the end of the range) first so that the launch tail is light
     E("const long long rt = total - 1 - gt;")
@@ -1124,7 +1133,7 @@ def gen_grad_kernel(bra, ket, prec="f64"):
     E("const double* __restrict__ Dm = args.D;")
     E("const int n = args.nbf;")
     E("const int4 ib = pairs.info[bra];")
-    E(f"const int nsplit = min({P}, ib.z);")
+    E(f"const int nsplit = gb::item_split({P}, ib.z);")
     E("const long long qo = li / nsplit;")
     E("const int ipart = (int)(li - qo * nsplit);")
     E("const int ket = args.rows.klist ? __ldg(args.rows.klist + __ldg(args.rows.kofs + row) + qo)")

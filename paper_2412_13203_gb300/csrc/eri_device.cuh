@@ -167,6 +167,17 @@ struct JKArgs {
     int pmode;
 };
 
+// Work items of one shell quartet whose bra pair has z primitive pairs, in a
+// class whose quartets spread over at most P threads: the largest divisor of z
+// not above P, so that every item of the quartet loops over the same number of
+// bra primitive pairs (the lanes of a warp, items of the same quartets, stay
+// in step).
+__host__ __device__ __forceinline__ int item_split(int P, int z) {
+    int d = P < z ? P : z;
+    while (d > 1 && z % d != 0) --d;
+    return d < 1 ? 1 : d;
+}
+
 // The ket primitive pairs [j0, j1) that one bra primitive pair `ip` of a work
 // item evaluates under primitive mode `mode` (see JKArgs::pmode).  The kets'
 // factors are sorted descending, so pq[ip] pq[k0 + j] >= thr holds on a prefix;

@@ -124,7 +124,7 @@ struct ClassRows {
     long long nprimq = 0;
     long long nbrap = 0;
     DevBuf start, bra, ket0;
-    DevBuf istart;      // prefix of work items per row (a quartet splits into min(P, K_ab) items)
+    DevBuf istart;      // prefix of work items per row (a quartet splits into gb::item_split(P, K_ab) items)
     long long itotal = 0;
     // mixed-precision split (filled on the device by jk_build).  Per row: the
     // kets of the global-bound FP64 prefix are listed explicitly -- FP64 ones
@@ -766,14 +766,14 @@ __global__ void k_list_primq_split(const long long* cnt, const long long* ofs, c
     atomicAdd(acc32 + 1, u32);
 }
 
-// Work items of every row: quartets x min(P, K_ab) (bra primitive pairs of the
+// Work items of every row: quartets x gb::item_split(P, K_ab) (bra primitive pairs of the
 // row's bra pair; batched rows look the pair up in their molecule).
 __global__ void k_row_items(const long long* start, const int* rbra, int nrows, const int4* info,
                             const gb::BatchMol* bm, const int* rowmol, int P, long long* w) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     const int4* inf = bm ? bm[rowmol[r]].pairs.info : info;
-    w[r] = (start[r + 1] - start[r]) * (long long)min(P, inf[rbra[r]].z);
+    w[r] = (start[r + 1] - start[r]) * (long long)gb::item_split(P, inf[rbra[r]].z);
 }
 
 // max |x| (as the bit pattern of a non-negative double) and, if xf is not

@@ -106,7 +106,7 @@ __global__ void k_rows_split(const long long* start, const int* rbra, const int*
     long long n64, nd, n32;
     int lo;
     split_row(A, i, rket0[r], (int)(start[r + 1] - start[r]), *dmax, tau, eps, psh, dsh, nshell, n64, nd, n32, lo);
-    store_split(r, n64, nd, n32, lo, min(P, info[i].z), c64, cdem, c32, k32, w64, wdem, w32, qtot);
+    store_split(r, n64, nd, n32, lo, gb::item_split(P, info[i].z), c64, cdem, c32, k32, w64, wdem, w32, qtot);
 }
 
 // Second pass: the kets of every row's prefix into the FP64 and demoted lists,
@@ -135,7 +135,7 @@ __global__ void k_rows_split_batched(const long long* start, const int* rbra, co
     split_row(mol.pairs.A, i, rket0[r], (int)(start[r + 1] - start[r]),
               __longlong_as_double((long long)dmax[rowmol[r]]), tau, eps, mol.psh, mol.Dsh, mol.nshell, n64, nd, n32,
               lo);
-    store_split(r, n64, nd, n32, lo, min(P, mol.pairs.info[i].z), c64, cdem, c32, k32, w64, wdem, w32, qtot);
+    store_split(r, n64, nd, n32, lo, gb::item_split(P, mol.pairs.info[i].z), c64, cdem, c32, k32, w64, wdem, w32, qtot);
 }
 
 // k_rows_fill for batched rows.

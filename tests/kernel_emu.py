@@ -357,7 +357,7 @@ class Problem:
 
     def rows(self, X, Y, items=True):
         """Rows (bra, first ket, quartet count) of class pair (X, Y) and their
-        prefix: of work items (min(P, K_ab) per quartet) or of quartets."""
+        prefix: of work items (item_split(P, K_ab) per quartet) or of quartets."""
         bras = np.where(self.cls == X)[0]
         kets = np.where(self.cls == Y)[0]
         if len(bras) == 0 or len(kets) == 0:
@@ -368,7 +368,7 @@ class Problem:
             n = (i - kets[0] + 1) if X == Y else len(kets)
             bra.append(i)
             ket0.append(kets[0])
-            cnt.append(n * (min(P, self.info[i, 2]) if items else 1))
+            cnt.append(n * (mg.item_split(P, int(self.info[i, 2])) if items else 1))
         start = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
         return np.array(bra, np.int32), np.array(ket0, np.int32), start
 

@@ -17,6 +17,8 @@ import os
 import numpy as np
 import pytest
 
+import kernel_emu
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(ROOT, "paper_2412_13203_gb300", "csrc")
@@ -145,7 +147,7 @@ def test_split_and_fill_follow_the_rule(lib, seed, tau, eps):
         cls = [_classify(A, psh, dsh, i, j, dmax, tau, eps) for j in range(s, s + c)]
         for k in cls:
             tot[k] += 1
-        m = min(P, int(info[i, 2]))
+        m = kernel_emu.mg.item_split(P, int(info[i, 2]))
         want64 = [j for j, k in zip(range(s, s + c), cls) if k == "fp64"]
         wantdem = [j for j, k in zip(range(s, s + c), cls) if k == "dem"]
         want32 = [j for j, k in zip(range(s, s + c), cls) if k == "fp32"]
