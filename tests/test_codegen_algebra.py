@@ -384,3 +384,17 @@ def test_path_searched_r_emission(monkeypatch, lam):
         got = _run(body, bra, ket, sh).reshape(na * nb, len(cds))
         want = ref.reshape(na * nb, nc * nd)[:, cds]
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+
+
+def test_item_split_divides_the_bra_primitive_pairs():
+    """Work items per quartet: a divisor of K_ab (every item of a quartet runs
+    the same number of bra primitive pairs), the largest one not above the
+    class's split P; K_ab <= P keeps one item per bra primitive pair."""
+    for P in (1, 4, 8):
+        for z in range(1, 65):
+            d = mg.item_split(P, z)
+            assert 1 <= d <= min(P, z) and z % d == 0
+            assert not any(z % e == 0 for e in range(d + 1, min(P, z) + 1))
+            if z <= P:
+                assert d == z
+    assert [mg.item_split(8, z) for z in (9, 10, 12, 15, 18, 25, 36)] == [3, 5, 6, 5, 6, 5, 6]
