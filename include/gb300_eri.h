@@ -120,8 +120,10 @@ int shellpairs_info(jk_pairs pairs, int* nbf, int64_t* npairs, int64_t* nquartet
  * (jk_set_option) run in FP32 -- primitive arithmetic, contracted block and
  * the digestion dot products, from centre differences formed in FP64 --
  * and each digested sum is added to J and K in FP64 (split accumulation);
- * the other quartets, the Schwarz factors and the final J/K symmetrisation
- * stay FP64, and the Boys function of FP32 quartets can be evaluated in FP64
+ * of the other quartets, the primitive quartets whose primitive Schwarz bound
+ * q_p q_q max|D| reaches JK_OPT_PRIM_TAU run in FP64 and the rest in FP32
+ * (JK_OPT_PRIM_TAU = 0: those quartets wholly FP64); the Schwarz factors and
+ * the final J/K symmetrisation stay FP64, and the Boys function of FP32 quartets can be evaluated in FP64
  * below T = tsmall (JK_OPT_MIXED_TSMALL; default 0: the FP32 evaluation,
  * table and downward recursion, is as accurate there).  JK_FP64 accumulates J' and K'
  * with compensation (each update split into a multiple of 2^-32, summed

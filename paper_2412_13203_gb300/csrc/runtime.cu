@@ -218,11 +218,17 @@ struct jk_pairs_s {
     DevBuf sph_coef;                                // Cartesian-to-pure coefficient tables
     bool sph_ready = false;
     std::vector<ProfRec> prof;
+    // forked streams of a build's class launches (created on first use, on the handle's device)
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
     ~jk_pairs_s() {
         for (auto& r : prof) {
             if (r.e0) cudaEventDestroy(r.e0);
             if (r.e1) cudaEventDestroy(r.e1);
         }
+        for (auto& x : side) if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
+        if (fork) cudaEventDestroy(fork);
+        for (auto& e : join) if (e) cudaEventDestroy(e);
     }
 };
 
@@ -1577,6 +1583,35 @@ int ensure_partition(jk_pairs_s* h, int nparts, cudaStream_t st) {
 }
 
 // J and K of the rows of part `part` of `nparts` (nparts = 1: the whole build).
+// The class launches of one build are spread over the caller's stream and three
+// forked ones (launch tails of one class overlap the next class's work; J and
+// K take atomic updates from all of them), then joined back into the caller's
+// stream.  With JK_OPT_PROFILE set everything stays on the caller's stream, so
+// that the per-launch event times do not overlap.
+int fork_streams(jk_pairs_s* h, cudaStream_t st, std::vector<cudaStream_t>& out) {
+    out.assign(1, st);
+    if (g_opt.profile) return 0;
+    if (!h->fork) {
+        for (auto& x : h->side) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+        for (auto& e : h->join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(h->fork, st));
+    for (auto& x : h->side) {
+        CK(cudaStreamWaitEvent(x, h->fork, 0));
+        out.push_back(x);
+    }
+    return 0;
+}
+
+int join_streams(jk_pairs_s* h, cudaStream_t st, const std::vector<cudaStream_t>& ss) {
+    for (size_t i = 1; i < ss.size(); ++i) {
+        CK(cudaEventRecord(h->join[i - 1], ss[i]));
+        CK(cudaStreamWaitEvent(st, h->join[i - 1], 0));
+    }
+    return 0;
+}
+
 int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_precision prec, cudaStream_t st,
                   int part = 0, int nparts = 1) {
     const int n = h->nbf;
@@ -1620,15 +1655,19 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         Klo = h->Klo.as<double>();
         CK(cudaMemsetAsync(Jlo, 0, sizeof(double) * n2, st));
         CK(cudaMemsetAsync(Klo, 0, sizeof(double) * n2, st));
-        for (size_t k = 0; k < h->rows.size(); ++k) {
+        std::vector<cudaStream_t> ss;
+        if ((rc = fork_streams(h, st, ss))) return rc;
+        int rcl = 0;
+        for (size_t k = 0; k < h->rows.size() && rcl == 0; ++k) {
             const ClassRows& cr = h->rows[k];
             int r0, r1;
             range(k, r0, r1);
             const long long items = nparts > 1 ? h->part_items[k][part + 1] - h->part_items[k][part] : cr.itotal;
-            if ((rc = launch_class(h, cr, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), items, D, J, K, st, r1 - r0,
-                                   nullptr, nullptr, r0, Jlo, Klo)))
-                return rc;
+            rcl = launch_class(h, cr, 0, cr.istart.as<long long>(), cr.ket0.as<int>(), items, D, J, K,
+                               ss[k % ss.size()], r1 - r0, nullptr, nullptr, r0, Jlo, Klo);
         }
+        if ((rc = join_streams(h, st, ss))) return rc;
+        if (rcl) return rcl;
     } else {
         const int ncr = (int)h->rows.size();
         const size_t nst = (size_t)kSplitSlots * std::max(1, ncr);
@@ -1670,10 +1709,15 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
         const bool psplit = g_opt.ptau > 0.0;
         if (psplit && (rc = h->thr64.alloc(sizeof(float) * std::max(1LL, off64[ncr])))) return rc;
         h->last_psplit = psplit;
-        for (int k = 0; k < ncr; ++k) {
+        std::vector<cudaStream_t> ss;
+        if ((rc = fork_streams(h, st, ss))) return rc;
+        const cudaStream_t st0 = st;
+        auto one_class = [&](int k) -> int {
             ClassRows& cr = h->rows[k];
             const int r0 = R0[k], r1 = R1[k];
-            if (cr.total <= 0 || r1 <= r0) continue;
+            if (cr.total <= 0 || r1 <= r0) return 0;
+            // this class's list fill and launches on one of the forked streams
+            cudaStream_t st = ss[k % ss.size()];
             int* l64 = h->list64.as<int>() + off64[k];
             int* ldm = h->listdem.as<int>() + offd[k];
             float* t64 = psplit ? h->thr64.as<float>() + off64[k] : nullptr;
@@ -1695,7 +1739,13 @@ int jk_build_impl(jk_pairs_s* h, const double* D, double* J, double* K, jk_preci
             if ((rc = launch_class(h, cr, 1, cr.sdem.as<long long>(), nullptr, cr.itotal, D, J, K, st, r1 - r0,
                                    cr.ldem.as<long long>(), ldm, r0)))
                 return rc;
-        }
+            return 0;
+        };
+        int rcl = 0;
+        for (int k = 0; k < ncr && rcl == 0; ++k) rcl = one_class(k);
+        // joined also after a failed launch, so that no forked work outlives the call's ordering
+        if ((rc = join_streams(h, st0, ss))) return rc;
+        if (rcl) return rcl;
         h->list_off64 = off64;
         h->list_offd = offd;
         h->last_r0 = R0;
