@@ -67,3 +67,14 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out
     assert out.stdout.split() == ["3", "3", "0.005"]
+
+
+def test_binding_option_names_match_the_header():
+    """The Python binding's option table names every jk_option of the header
+    with its value (a renumbered or added option cannot drift apart)."""
+    import re
+    import paper_2412_13203_gb300 as g
+    text = open(os.path.join(ROOT, "include", "gb300_eri.h")).read()
+    body = text[text.index("typedef enum {", text.index("JK_OPT_MIXED_TAU") - 200):text.index("} jk_option;")]
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"JK_OPT_(\w+) = (\d+)", body)}
+    assert enum and enum == g.JK_OPT
